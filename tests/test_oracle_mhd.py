@@ -1,0 +1,204 @@
+"""Pins of the oracle's MHD right-hand side (Eqs. A1-A4) and RK3 step (Sec. 3.3).
+
+Each case chooses fields for which every derivative is a closed form (single sine modes, so
+each stencil returns its discrete Fourier symbol times the mode), so the expected RHS follows
+from Eqs. A1-A4 by hand.  Together the cases exercise every term with its sign and constant:
+advection, the pressure term with cs^2(lnrho, s), the Lorentz force j x B / rho with
+j = grad div A - lap A, viscosity with the 1/3 grad div u and 2 S.grad lnrho terms, bulk
+viscosity, viscous/ohmic/bulk heating over rho T, and the induction term u x B + eta lap A.
+
+RK3: for a force-free (Beltrami) vector potential with u = 0 the system is linear in A, and
+one step multiplies A by the 3-stage, 3rd-order stability polynomial 1 + z + z^2/2 + z^3/6
+with z = eta lam2 dt.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import MhdParams
+from paper_2406_08923_gb300 import synth
+from symbols import grid, lam1, lam2, mu
+
+N = 16
+LNRHO, UX, UY, UZ, AX, AY, AZ, SS = range(8)
+
+
+def _par(**kw):
+    base = dict(cs0=1.3, gamma=5.0 / 3.0, cp=1.7, lnrho0=0.3, nu=0.02, eta=0.03, zeta=0.05, mu0=1.5)
+    base.update(kw)
+    return MhdParams.for_grid(N, **base)
+
+
+def _temp(p, lnrho, ss):
+    cs2 = p.cs0 ** 2 * np.exp(p.gamma * ss / p.cp + (p.gamma - 1) * (lnrho - p.lnrho0))
+    return cs2, cs2 / (p.cp * (p.gamma - 1))
+
+
+def _check(got, exp, tol=1e-12):
+    for q in range(8):
+        e = np.broadcast_to(exp[q], got[q].shape)
+        np.testing.assert_allclose(got[q], e, rtol=0, atol=tol, err_msg=f"field {q}")
+
+
+def test_uniform_state_has_zero_rhs():
+    p = _par()
+    f = np.empty((8, N, N, N))
+    for q, v in enumerate((0.2, 0.5, -0.3, 0.1, 1.0, -2.0, 0.7, 0.4)):
+        f[q] = v
+    rhs = oracle.mhd_rhs(f, p)
+    assert np.abs(rhs).max() < 1e-13
+
+
+def test_sound_wave_pressure_term():
+    p = _par()
+    (Z, Y, X), h = grid(N)
+    k, eps = 2, 1e-2
+    f = np.zeros((8, N, N, N))
+    f[LNRHO] = eps * np.sin(k * X)
+    cs2, _ = _temp(p, f[LNRHO], 0.0)
+    exp = np.zeros_like(f)
+    exp[UX] = -cs2 * lam1(k, h) * eps * np.cos(k * X)
+    _check(oracle.mhd_rhs(f, p), exp)
+
+
+def test_entropy_gradient_pressure_term():
+    p = _par()
+    (Z, Y, X), h = grid(N)
+    k, eps = 3, 2e-2
+    f = np.zeros((8, N, N, N))
+    f[SS] = eps * np.sin(k * Y)
+    cs2, _ = _temp(p, 0.0, f[SS])
+    exp = np.zeros_like(f)
+    exp[UY] = -cs2 * lam1(k, h) * eps * np.cos(k * Y) / p.cp
+    _check(oracle.mhd_rhs(f, p), exp)
+
+
+def test_shear_with_density_gradient():
+    p = _par()
+    (Z, Y, X), h = grid(N)
+    k, q, eps, dl = 2, 3, 1e-2, 3e-2
+    f = np.zeros((8, N, N, N))
+    f[UY] = eps * np.sin(k * X)
+    f[LNRHO] = dl * np.sin(q * Y)
+    g = lam1(k, h) * eps * np.cos(k * X)     # d uy / dx
+    G = lam1(q, h) * dl * np.cos(q * Y)      # d lnrho / dy
+    cs2, T = _temp(p, f[LNRHO], 0.0)
+    exp = np.zeros_like(f)
+    exp[LNRHO] = -f[UY] * G
+    exp[UX] = p.nu * g * G                   # nu * 2 S_xy dlnrho/dy, S_xy = g/2
+    exp[UY] = -cs2 * G + p.nu * lam2(k, h) * f[UY]
+    exp[SS] = p.nu * g * g / T               # 2 rho nu S:S / (rho T), S:S = g^2/2
+    _check(oracle.mhd_rhs(f, p), exp)
+
+
+def test_compressive_flow_and_bulk_viscosity():
+    p = _par()
+    (Z, Y, X), h = grid(N)
+    k, eps = 2, 1e-2
+    f = np.zeros((8, N, N, N))
+    f[UX] = eps * np.sin(k * X)
+    g = lam1(k, h) * eps * np.cos(k * X)     # div u
+    l2 = lam2(k, h) * f[UX]                  # d2 ux / dx2 = d/dx div u
+    cs2, T = _temp(p, 0.0, 0.0)
+    exp = np.zeros_like(f)
+    exp[LNRHO] = -g
+    exp[UX] = -f[UX] * g + p.nu * (l2 + l2 / 3.0) + p.zeta * l2
+    exp[SS] = (2 * p.nu * (2.0 / 3.0) * g * g + p.zeta * g * g) / T
+    _check(oracle.mhd_rhs(f, p), exp)
+
+
+def test_grad_div_u_uses_mixed_derivatives():
+    p = _par()
+    (Z, Y, X), h = grid(N)
+    k, eps = 2, 1e-2
+    th = k * (X + Y)
+    f = np.zeros((8, N, N, N))
+    f[UX] = eps * np.sin(th)
+    dxu = lam1(k, h) * eps * np.cos(th)
+    dyu = dxu
+    l2 = lam2(k, h) * f[UX]
+    m = mu(k, k, h, h) * f[UX]
+    cs2, T = _temp(p, 0.0, 0.0)
+    exp = np.zeros_like(f)
+    exp[LNRHO] = -dxu
+    exp[UX] = -f[UX] * dxu + p.nu * (2 * l2 + l2 / 3.0) + p.zeta * l2
+    exp[UY] = p.nu * m / 3.0 + p.zeta * m
+    # S: Sxx = dxu - dxu/3, Syy = Szz = -dxu/3, Sxy = dyu/2
+    SS2 = (2 * dxu / 3) ** 2 + 2 * (dxu / 3) ** 2 + 2 * (dyu / 2) ** 2
+    exp[SS] = (2 * p.nu * SS2 + p.zeta * dxu * dxu) / T
+    _check(oracle.mhd_rhs(f, p), exp)
+
+
+def test_lorentz_force_ohmic_heating_and_induction():
+    p = _par()
+    (Z, Y, X), h = grid(N)
+    k, eps, U, l0 = 3, 1e-2, 0.4, 0.2
+    f = np.zeros((8, N, N, N))
+    f[AZ] = eps * np.sin(k * X)
+    f[UX] = U
+    f[LNRHO] = l0
+    By = -lam1(k, h) * eps * np.cos(k * X)
+    jz = -lam2(k, h) * f[AZ] / p.mu0
+    rho = np.exp(l0)
+    cs2, T = _temp(p, l0, 0.0)
+    exp = np.zeros_like(f)
+    exp[UX] = -jz * By / rho                 # (j x B)_x = jy Bz - jz By
+    exp[SS] = p.eta * p.mu0 * jz * jz / (rho * T)
+    exp[AZ] = U * By + p.eta * lam2(k, h) * f[AZ]   # (u x B)_z = ux By - uy Bx
+    _check(oracle.mhd_rhs(f, p), exp)
+
+
+def test_grad_div_A_in_current():
+    p = _par()
+    (Z, Y, X), h = grid(N)
+    k, eps = 2, 1e-2
+    th = k * (X + Y)
+    f = np.zeros((8, N, N, N))
+    f[AX] = eps * np.sin(th)
+    l2 = lam2(k, h) * f[AX]
+    m = mu(k, k, h, h) * f[AX]
+    jx = (l2 - 2 * l2) / p.mu0               # grad div A - lap A
+    jy = m / p.mu0
+    Bz = -lam1(k, h) * eps * np.cos(th)      # dAy/dx - dAx/dy
+    _, T = _temp(p, 0.0, 0.0)
+    exp = np.zeros_like(f)
+    exp[UX] = jy * Bz
+    exp[UY] = -jx * Bz
+    exp[SS] = p.eta * p.mu0 * (jx * jx + jy * jy) / T
+    exp[AX] = p.eta * 2 * l2
+    _check(oracle.mhd_rhs(f, p), exp)
+
+
+@pytest.mark.parametrize("dt", [0.1, 0.3])
+def test_rk3_stability_polynomial_on_beltrami_field(dt):
+    p = _par(eta=0.5)
+    (Z, Y, X), h = grid(N)
+    k, eps = 3, 1e-2
+    f = np.zeros((8, N, N, N))
+    f[AX] = eps * np.sin(k * Z)
+    f[AY] = eps * np.cos(k * Z)
+    out = oracle.mhd_rk3(f, p, dt, 1)
+    z = p.eta * lam2(k, h) * dt
+    P = 1 + z + z * z / 2 + z ** 3 / 6
+    np.testing.assert_allclose(out[AX], P * f[AX], atol=1e-14)
+    np.testing.assert_allclose(out[AY], P * f[AY], atol=1e-14)
+    assert np.abs(out[[LNRHO, UX, UY, UZ, AZ]]).max() < 1e-14
+    # entropy is heated uniformly (ohmic heating of a spatially uniform |j|)
+    assert np.ptp(out[SS]) < 1e-14 and out[SS].mean() > 0
+    # the polynomial differs from exp(z) at 4th order: the test can see a wrong scheme
+    assert abs(P - np.exp(z)) > 1e-5
+
+
+def test_box_step_matches_periodic_step():
+    n = 12
+    p = MhdParams.for_grid(n)
+    f = synth.mhd_fields(n, seed=3) * 30.0
+    dt = p.dt_default()
+    ref = oracle.mhd_rk3(f, p, dt, 1)
+    c = (4, 7, 2)
+    m = 2 * 9 + 1
+    idx = [np.arange(ci - 9, ci + 10) % n for ci in c]
+    box = f[:, idx[0]][:, :, idx[1]][:, :, :, idx[2]]
+    out = oracle.mhd_rk3_box(box, p, dt, 3)
+    np.testing.assert_allclose(out[:, 9, 9, 9], ref[:, c[0], c[1], c[2]], rtol=1e-13, atol=1e-16)
+    assert out.shape[1] == m
