@@ -1,0 +1,500 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 stencil engine.
+
+Headline workload: the 3D heat equation with the 6th-order 19-point Laplacian, 256^3 cells,
+FP64, periodic halos, forward Euler dt = 0.1 dx^2, 100 steps (Sec. 3.2, Eqs. 4-7).  One bench
+step is one whole job: stencil_step(plan, in, out, 100) -- the input halo fill and 100 fused
+Euler passes, each writing its output's periodic halo.  The metric is Mcell-updates/s
+(cells x Euler steps / time).  The two 145 MB padded FP64 fields the passes stream between
+exceed the 126 MB L2, so no flush is needed between iterations.
+
+The JSON line also carries, per the other stencil workloads (1D cross-correlation, FP32 heat,
+fused 8-field MHD in FP64 and in FP32/BF16 storage), their own throughput and roofline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-extras]
+
+Under torchrun (N > 1) every rank solves its own independent grid (weak scaling, no
+data-path collective); the time is the max over ranks.  --impl reference times the FP64 CPU
+oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+HEAT_N, HEAT_STEPS = 256, 100
+MHD_N, MHD_N_LOWP, MHD_STEPS = 256, 384, 20
+XC_N, XC_SWEEPS = 1 << 20, 10
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# FP64 vector FMA rate of GB300 (nominal 1.25 TFLOP/s dense, recipe table); FP32 from the
+# unit count: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz boost.
+FP64_PEAK_TFLOPS = 1.25
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax = float(f[2])
+                except ValueError:
+                    continue
+                for n, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+            os.unlink(self.path)
+        except OSError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------- helpers
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, None
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl")
+    return rank, ws, dist
+
+
+def _barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def _max_over_ranks(v, dist):
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _timed(fn, reps, stream):
+    """Average ms of fn() over reps, CUDA events on `stream`, synchronised on both sides."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _roof(bound, achieved, peak, unit, traffic=None, note=""):
+    return {"bound": bound, "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": unit,
+            "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": note}
+
+
+# ----------------------------------------------------------------------------- workloads
+
+
+def heat_job(L, synth, dtype, n, steps, warmup, reps, stream, with_e2e=False):
+    """Time stencil_step(n^3 heat, `steps` Euler steps) and its per-kernel average."""
+    import torch
+    par = L.heat_params(n)
+    p = L.Plan(3, (n, n, n), 3, 1, L.STENCIL_BC_PERIODIC, L.STENCIL_DIFFUSION, dtype, dtype, params=par)
+    a, b = p.alloc(), p.alloc()
+    p.upload(a, [synth.heat_field(n)])
+    p.halo_fill(a)
+    torch.cuda.synchronize()
+    p.autotune(a, b, nsteps=4, reps=2, stream=stream)
+    for _ in range(warmup):
+        p.step(a, b, steps, stream)
+    res = {"plan": p, "fields": (a, b), "variant": p.variant()[2]}
+    res["ms_job"] = _timed(lambda: p.step(a, b, steps, stream), reps, stream)
+    ms_halo = _timed(lambda: p.halo_fill(a, stream), max(reps, 10), stream)
+    res["ms_kernel"] = (res["ms_job"] - ms_halo) / steps
+    res["ms_halo"] = ms_halo
+    res["launches_per_job"] = steps + 1
+    if with_e2e:
+        nbytes = p.bytes_per_field
+        h_in = torch.empty(nbytes // a[0].element_size(), dtype=a[0].dtype, pin_memory=True)
+        h_out = torch.empty_like(h_in, pin_memory=True)
+        h_in.copy_(a[0].cpu())
+        d_in = p.alloc()
+
+        def e2e():
+            d_in[0].copy_(h_in, non_blocking=True)
+            p.step(d_in, b, steps, stream)
+            h_out.copy_(b[0], non_blocking=True)
+
+        for _ in range(max(1, warmup // 2)):
+            e2e()
+        res["ms_e2e"] = _timed(e2e, reps, stream)
+        res["e2e_bytes"] = (nbytes, nbytes)
+    return res
+
+
+def mhd_job(L, synth, storage, n, steps, warmup, reps, stream):
+    import torch
+    par = L.mhd_params(n)
+    compute = L.STENCIL_F64 if storage == L.STENCIL_F64 else L.STENCIL_F32
+    p = L.Plan(3, (n, n, n), 3, 8, L.STENCIL_BC_PERIODIC, L.STENCIL_MHD8, storage, compute, params=par)
+    a, b = p.alloc(), p.alloc()
+    seed = synth.SEED_MHD if storage == L.STENCIL_F64 else synth.SEED_MHD_LOWP
+    p.upload(a, synth.mhd_fields(n, seed=seed))
+    torch.cuda.synchronize()
+    p.autotune(a, b, nsteps=1, reps=1, stream=stream)
+    for _ in range(warmup):
+        p.step(a, b, steps, stream)
+    ms_job = _timed(lambda: p.step(a, b, steps, stream), reps, stream)
+    ms_halo = _timed(lambda: p.halo_fill(a, stream), 5, stream)
+    ms_sub = (ms_job - ms_halo) / (3 * steps)
+    norms = p.norms(b)
+    return {"plan": p, "ms_job": ms_job, "ms_substep": ms_sub, "variant": p.variant()[2],
+            "mass": float(norms[-1]), "finite": bool(np.all(np.isfinite(norms)))}
+
+
+def xcorr_job(L, synth, dtype, warmup, reps, stream):
+    import torch
+    n = XC_N
+    if dtype == L.STENCIL_I32:
+        data, g = synth.xcorr_int32(n)
+    else:
+        data = synth.xcorr_f64(n)
+        g = np.array([1 / 90, -3 / 20, 3 / 2, -49 / 18, 3 / 2, -3 / 20, 1 / 90])
+    p = L.Plan(1, (n,), 3, 1, L.STENCIL_BC_PERIODIC, L.STENCIL_XCORR, dtype, dtype, coeffs=g)
+    a, b = p.alloc(), p.alloc()
+    p.upload(a, [data])
+    torch.cuda.synchronize()
+    for _ in range(warmup):
+        p.step(a, b, XC_SWEEPS, stream)
+    ms = _timed(lambda: p.step(a, b, XC_SWEEPS, stream), reps, stream)
+    return {"ms_job": ms}
+
+
+def cpu_baseline(seconds_target=10.0):
+    """The FP64 oracle, as it stands, on the host cores: a bounded sample of the headline
+    workload (256^3 heat field, a number of Euler steps chosen to take ~10 s)."""
+    import oracle
+    from paper_2406_08923_gb300 import synth
+    n = HEAT_N
+    f = synth.heat_field(n)
+    h = 2 * np.pi / n
+    t0 = time.perf_counter()
+    oracle.diffusion(f, 0.1 * h * h, 1.0, (h, h, h), 1)
+    t1 = time.perf_counter() - t0
+    k = max(1, min(HEAT_STEPS, int(seconds_target / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.diffusion(f, 0.1 * h * h, 1.0, (h, h, h), k)
+    dt = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    threads = int(os.environ.get("OMP_NUM_THREADS", cores))
+    return {"value": round(n ** 3 * k / dt / 1e6, 3), "unit": "Mcell-updates/s", "cores": threads,
+            "kind": "oracle", "sample": f"256^3 FP64 heat field, {k} forward-Euler steps (of 100), "
+                                        f"{dt:.1f} s wall on {threads} OpenMP threads"}
+
+
+# ----------------------------------------------------------------------------- arms
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2406_08923_gb300 import synth
+    n = HEAT_N
+    f = synth.heat_field(n)
+    h = 2 * np.pi / n
+    per_step = 4  # Euler steps of the oracle per bench step (bounded sample of the 100-step job)
+    for _ in range(args.warmup):
+        oracle.diffusion(f, 0.1 * h * h, 1.0, (h, h, h), 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.diffusion(f, 0.1 * h * h, 1.0, (h, h, h), per_step)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = n ** 3 * per_step / dt / 1e6
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    threads = int(os.environ.get("OMP_NUM_THREADS", cores))
+    line = {
+        "impl": "reference", "metric": "heat3d_256_fp64_mcell_updates_per_s", "value": round(value, 3),
+        "unit": "Mcell-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "heat3d_r3_256^3_fp64_periodic_euler_dt0.1dx2_100steps",
+                   "sample": f"{per_step} of the 100 Euler steps per bench step"},
+        "cpu_baseline": {"value": round(value, 3), "unit": "Mcell-updates/s", "cores": threads, "kind": "oracle",
+                         "sample": f"256^3 FP64 heat field, {per_step} Euler steps per bench step"},
+        "e2e": {"value": round(value, 3), "unit": "Mcell-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2406_08923_gb300 import _lib as L
+    from paper_2406_08923_gb300 import synth
+
+    rank, world, dist = _dist()
+    L.load()
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.current_stream()
+    hbm_peak, hbm_src = _peaks()
+
+    # ---- headline: 256^3 FP64 heat, 100 steps per bench step
+    n = HEAT_N
+    cells = n ** 3
+    head = heat_job(L, synth, L.STENCIL_F64, n, HEAT_STEPS, args.warmup, 1, stream, with_e2e=False)
+    p = head["plan"]
+    a, b = head["fields"]
+    _barrier(dist)
+    torch.cuda.synchronize()
+    with Clocks(dev) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            p.step(a, b, HEAT_STEPS, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    _barrier(dist)
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = _max_over_ranks(ms, dist)
+    clocks = clk.summary()
+    value = world * cells * HEAT_STEPS / (ms / 1e3) / 1e6
+
+    # per-kernel average: job time minus the one input halo fill, over 100 passes
+    ms_halo = _timed(lambda: p.halo_fill(a, stream), 20, stream)
+    ms_kernel = (ms - ms_halo) / HEAT_STEPS
+    flops_cell, bytes_cell = 38.0, 16.0
+    achieved_tf = cells * flops_cell / (ms_kernel / 1e3) / 1e12
+    achieved_gbs = cells * bytes_cell / (ms_kernel / 1e3) / 1e9
+
+    # e2e through the public API with host buffers: pinned H2D of the padded input,
+    # the 100-step job, D2H of the padded result, every step.
+    nbytes = p.bytes_per_field
+    h_in = torch.empty(a[0].numel(), dtype=a[0].dtype, pin_memory=True)
+    h_out = torch.empty_like(h_in, pin_memory=True)
+    h_in.copy_(a[0].cpu())
+    d_in = p.alloc()
+
+    def e2e():
+        d_in[0].copy_(h_in, non_blocking=True)
+        p.step(d_in, b, HEAT_STEPS, stream)
+        h_out.copy_(b[0], non_blocking=True)
+
+    e2e()
+    ms_e2e = _max_over_ranks(_timed(e2e, max(3, args.steps // 2), stream), dist)
+
+    extras = {}
+    if not args.no_extras:
+        extras = run_extras(L, synth, stream, hbm_peak, args)
+
+    line = {
+        "metric": "heat3d_256_fp64_mcell_updates_per_s",
+        "value": round(value, 3), "unit": "Mcell-updates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "heat3d_r3_256^3_fp64_periodic_euler_dt0.1dx2_100steps",
+                   "cells": cells, "euler_steps_per_bench_step": HEAT_STEPS,
+                   "kernel_variant": head["variant"],
+                   "l2": "inputs larger than L2 (2 x 145 MB padded FP64 fields streamed per pass)",
+                   "parallelism": f"{world} independent grids (one per GPU)"},
+        "roofline": _roof("alu", achieved_tf, FP64_PEAK_TFLOPS, "TFLOP/s",
+                          note="FP64 nominal 1.25 TFLOP/s (recipe table); 38 flop/cell-update"),
+        "roofline_hbm": {"achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                         "frac": round(achieved_gbs / hbm_peak, 4), "peak_source": hbm_src,
+                         "bytes_per_cell": bytes_cell},
+        "kernel_ms_avg": round(ms_kernel, 5), "halo_fill_ms": round(ms_halo, 5),
+        "e2e": {"value": round(world * cells * HEAT_STEPS / (ms_e2e / 1e3) / 1e6, 3), "unit": "Mcell-updates/s",
+                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "gpu_launches": args.steps * (HEAT_STEPS + 1),
+        "clocks": clocks,
+        "per_stencil": extras,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_extras(L, synth, stream, hbm_peak, args):
+    out = {}
+    w, r = 1, 3
+    # config 1: 1D cross-correlation, 2^20 cells, 10 sweeps (L2-resident: no HBM claim)
+    for name, dt in (("xcorr1d_int32_2^20_10sweeps", L.STENCIL_I32), ("xcorr1d_fp64_2^20_10sweeps", L.STENCIL_F64)):
+        res = xcorr_job(L, synth, dt, w, 20, stream)
+        out[name] = {"ms_per_job": round(res["ms_job"], 4),
+                     "mcell_updates_per_s": round(XC_N * XC_SWEEPS / (res["ms_job"] / 1e3) / 1e6, 1),
+                     "launches_per_job": 1, "bound": "l2 + launch latency (4-8 MiB working set)"}
+    # config 2, FP32 variant
+    res = heat_job(L, synth, L.STENCIL_F32, HEAT_N, HEAT_STEPS, w, r, stream)
+    cells = HEAT_N ** 3
+    gbs = cells * 8.0 / (res["ms_kernel"] / 1e3) / 1e9
+    out["heat3d_256_fp32_100steps"] = {
+        "ms_per_job": round(res["ms_job"], 4), "kernel_ms_avg": round(res["ms_kernel"], 5),
+        "mcell_updates_per_s": round(cells * HEAT_STEPS / (res["ms_job"] / 1e3) / 1e6, 1),
+        "variant": res["variant"],
+        "roofline": _roof("hbm", gbs, hbm_peak, "GB/s", note="8 B/cell-update algorithmic")}
+    res["plan"].close()
+    # config 3: fused 8-field MHD, 256^3 FP64, 20 RK3 steps
+    cells = MHD_N ** 3
+    res = mhd_job(L, synth, L.STENCIL_F64, MHD_N, MHD_STEPS, w, 1, stream)
+    out["mhd8_256_fp64_20steps"] = {
+        "ms_per_job": round(res["ms_job"], 3), "ms_per_substep": round(res["ms_substep"], 4),
+        "mcell_substep_updates_per_s": round(cells / (res["ms_substep"] / 1e3) / 1e6, 1),
+        "variant": res["variant"], "finite": res["finite"], "mass": res["mass"],
+        "paper_ideal_hbm_frac": round(cells * 128.0 / (res["ms_substep"] / 1e3) / 1e9 / hbm_peak, 4)}
+    res["plan"].close()
+    # config 4: 384^3 FP32 / BF16 storage, Kahan-compensated RK
+    cells = MHD_N_LOWP ** 3
+    for name, st, bpc in (("mhd8_384_fp32_20steps", L.STENCIL_F32, 4), ("mhd8_384_bf16_20steps", L.STENCIL_BF16, 2)):
+        res = mhd_job(L, synth, st, MHD_N_LOWP, MHD_STEPS, w, 1, stream)
+        # per cell-substep: f_in, f_out, w r/w, c r/w over 8 fields (avg over the 3 substeps)
+        avg_vals = 8 * (1 + 1 + (1 + 2 + 1) / 3.0 + 2)
+        gbs = cells * avg_vals * bpc / (res["ms_substep"] / 1e3) / 1e9
+        out[name] = {"ms_per_job": round(res["ms_job"], 3), "ms_per_substep": round(res["ms_substep"], 4),
+                     "mcell_substep_updates_per_s": round(cells / (res["ms_substep"] / 1e3) / 1e6, 1),
+                     "variant": res["variant"], "finite": res["finite"], "mass": res["mass"],
+                     "roofline": _roof("hbm", gbs, hbm_peak, "GB/s",
+                                       note=f"{avg_vals:.1f} values x {bpc} B per cell-substep")}
+        res["plan"].close()
+    return out
+
+
+CASES = {
+    # name: (kind, storage, default n, steps per job)
+    "heat_f64": ("heat", 1, HEAT_N, HEAT_STEPS),
+    "heat_f32": ("heat", 2, HEAT_N, HEAT_STEPS),
+    "mhd_f64": ("mhd", 1, MHD_N, 1),
+    "mhd_f32": ("mhd", 2, MHD_N_LOWP, 1),
+    "mhd_bf16": ("mhd", 3, MHD_N_LOWP, 1),
+    "xcorr_i32": ("xcorr", 0, XC_N, XC_SWEEPS),
+}
+
+
+def run_case(args):
+    """One workload, fixed kernel variant, `warmup` + `steps` jobs; prints one short JSON line."""
+    import torch
+
+    from paper_2406_08923_gb300 import _lib as L
+    from paper_2406_08923_gb300 import synth
+    kind, storage, n0, steps = CASES[args.case]
+    n = args.n or n0
+    stream = torch.cuda.current_stream()
+    if kind == "heat":
+        par = L.heat_params(n)
+        p = L.Plan(3, (n, n, n), 3, 1, L.STENCIL_BC_PERIODIC, L.STENCIL_DIFFUSION, storage, storage, params=par)
+        a, b = p.alloc(), p.alloc()
+        p.upload(a, [synth.heat_field(n)])
+    elif kind == "mhd":
+        par = L.mhd_params(n)
+        compute = L.STENCIL_F64 if storage == L.STENCIL_F64 else L.STENCIL_F32
+        p = L.Plan(3, (n, n, n), 3, 8, L.STENCIL_BC_PERIODIC, L.STENCIL_MHD8, storage, compute, params=par)
+        a, b = p.alloc(), p.alloc()
+        p.upload(a, synth.mhd_fields(n))
+    else:
+        data, g = synth.xcorr_int32(n)
+        p = L.Plan(1, (n,), 3, 1, L.STENCIL_BC_PERIODIC, L.STENCIL_XCORR, storage, storage, coeffs=g)
+        a, b = p.alloc(), p.alloc()
+        p.upload(a, [data])
+    p.set_variant(args.variant)
+    for _ in range(args.warmup):
+        p.step(a, b, steps, stream)
+    ms = _timed(lambda: p.step(a, b, steps, stream), args.steps, stream)
+    p.sync()
+    print(json.dumps({"case": args.case, "n": n, "steps_per_job": steps, "variant": p.variant()[2],
+                      "ms_per_job": round(ms, 4)}), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--no-extras", action="store_true", help="headline workload only")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--case", default=None, choices=sorted(CASES),
+                    help="run one workload only (no autotune), e.g. for an ncu capture")
+    ap.add_argument("--n", type=int, default=None, help="grid size for --case")
+    ap.add_argument("--variant", type=int, default=0, help="kernel variant for --case")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.case:
+        return run_case(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,216 @@
+/*
+ * stencil.h -- C ABI of the GB300 stencil engine (libstencil.so).
+ *
+ * The engine sweeps stencil functions over padded 1D/3D arrays on one NVIDIA GB300 GPU
+ * (sm_103a).  It implements the computations of "Stencil Computations on AMD and Nvidia
+ * Graphics Processors: Performance and Tuning Strategies" (Pekkila et al., arXiv 2406.08923):
+ *
+ *   STENCIL_XCORR      1D cross-correlation f'_i = sum_{j=-r..r} g_j f^_{i+j}       (Sec. 3.1, Eq. 3)
+ *   STENCIL_DIFFUSION  forward-Euler step of df/dt = alpha lap f with the 6th-order
+ *                      central 2nd-derivative stencil per axis, folded into one
+ *                      19-point cross-correlation                                  (Sec. 3.2, Eqs. 4-7)
+ *   STENCIL_MHD8       one 3-stage Runge-Kutta step of the 8-field non-ideal MHD system
+ *                      in non-conservative form, 6th-order central 1st, 2nd and mixed
+ *                      derivatives fused with the nonlinear right-hand side          (Sec. 3.3, Eqs. 8-9,
+ *                                                                                   Appendix A, Eqs. A1-A4)
+ *
+ * Arrays are "augmented" arrays f^ (Sec. 2.4, Eq. 2): the interior is surrounded by a halo of
+ * width r whose values are the boundary function beta.  With STENCIL_BC_PERIODIC the library
+ * fills the halo with the periodic image of the interior; with STENCIL_BC_CALLER the caller
+ * fills it and the library only reads it.
+ *
+ * Conventions for every entry point:
+ *   - Device pointers are plain CUDA device addresses (e.g. torch tensor data_ptr()), owned
+ *     by the caller and at least 16-byte aligned.  `stream` is a cudaStream_t passed as
+ *     void* (NULL = the legacy default stream).  Work is enqueued on `stream` and returns
+ *     before it completes unless stated otherwise.
+ *   - Host pointers are owned by the caller and only read/written during the call.
+ *   - Errors are returned as stencil_status; nothing aborts, exits or throws across the ABI.
+ *     stencil_last_error_detail() gives a human-readable reason for the last failure.
+ *   - A plan belongs to the CUDA device that was current when it was created; calls with a
+ *     different current device return STENCIL_EINVAL.
+ *   - Calls on one plan must not overlap in host threads; separate plans are independent.
+ */
+#ifndef STENCIL_H
+#define STENCIL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define STENCIL_ABI_VERSION 1
+
+typedef struct stencil_plan *stencil_t;
+
+typedef enum stencil_status {
+    STENCIL_OK = 0,
+    STENCIL_EINVAL = 1,       /* an argument is out of range, inconsistent or misaligned */
+    STENCIL_ENOMEM = 2,       /* a device or host allocation failed */
+    STENCIL_ECUDA = 3,        /* a CUDA call failed (detail string names it) */
+    STENCIL_EUNSUPPORTED = 4, /* a valid combination this build does not implement */
+    STENCIL_ETIMEOUT = 5      /* a bounded device-side wait expired; the kernel gave up */
+} stencil_status;
+
+typedef enum stencil_dtype {
+    STENCIL_I32 = 0,  /* int32 storage, arithmetic modulo 2^32 (XCORR only) */
+    STENCIL_F64 = 1,
+    STENCIL_F32 = 2,
+    STENCIL_BF16 = 3  /* bfloat16 storage; arithmetic in FP32 */
+} stencil_dtype;
+
+typedef enum stencil_bc {
+    STENCIL_BC_PERIODIC = 0, /* beta(f, i) = f_{i mod n}: library fills the halo */
+    STENCIL_BC_CALLER = 1    /* caller fills the halo; one pass per stencil_step call */
+} stencil_bc;
+
+typedef enum stencil_kind {
+    STENCIL_XCORR = 0,     /* Eq. 3, ndim = 1, radius 0..4, caller weights g_{-r..r} */
+    STENCIL_DIFFUSION = 1, /* Eqs. 4-7, ndim = 3, radius 3 */
+    STENCIL_MHD8 = 2       /* Eqs. A1-A4 + RK3, ndim = 3, radius 3, 8 fields */
+} stencil_kind;
+
+/* Physical constants.  Unused members are ignored by kinds that do not need them. */
+typedef struct stencil_params {
+    double dt;     /* time step (DIFFUSION, MHD8) */
+    double alpha;  /* diffusion coefficient (DIFFUSION) */
+    double dx[3];  /* grid spacing along x, y, z (DIFFUSION, MHD8) */
+    double cs0;    /* MHD8: reference sound speed */
+    double gamma;  /* MHD8: adiabatic index */
+    double cp;     /* MHD8: specific heat at constant pressure */
+    double lnrho0; /* MHD8: reference log-density */
+    double nu;     /* MHD8: kinematic viscosity */
+    double eta;    /* MHD8: magnetic diffusivity */
+    double zeta;   /* MHD8: bulk viscosity */
+    double mu0;    /* MHD8: vacuum permeability */
+} stencil_params;
+
+/* Field order of STENCIL_MHD8 (Table A1 symbols). */
+enum { STENCIL_MHD_LNRHO = 0, STENCIL_MHD_UX, STENCIL_MHD_UY, STENCIL_MHD_UZ,
+       STENCIL_MHD_AX, STENCIL_MHD_AY, STENCIL_MHD_AZ, STENCIL_MHD_SS, STENCIL_MHD_NFIELDS };
+
+/*
+ * stencil_create -- validate a problem and build a plan (Sec. 2.4 Eq. 2 for the layout).
+ *
+ *   ndim     1 (XCORR) or 3 (DIFFUSION, MHD8).
+ *   dims     interior extents (nx, ny, nz); entries beyond ndim are ignored.  With periodic
+ *            boundaries each used extent must be >= 2*radius + 1.
+ *   radius   stencil radius r: 0..4 for XCORR, 3 for DIFFUSION and MHD8.
+ *   coeffs   XCORR only: 2r+1 weights g_{-r..r}, int32_t for STENCIL_I32, double otherwise
+ *            (rounded to FP32 for STENCIL_F32).  Copied; may be freed after the call.
+ *            NULL for the other kinds.
+ *   ncoeffs  2r+1 for XCORR, 0 otherwise.
+ *   nfields  1 for XCORR and DIFFUSION, 8 for MHD8.
+ *   storage  element type of the caller's arrays; compute = arithmetic type:
+ *              XCORR:     I32/I32, F64/F64, F32/F32
+ *              DIFFUSION: F64/F64, F32/F32
+ *              MHD8:      F64/F64, F32/F32, BF16/F32 (F32 and BF16 storage use
+ *                         Kahan-compensated RK accumulation)
+ *   params   physical constants (may be NULL for XCORR).
+ *   out      receives the plan.
+ *
+ * The only call that allocates device memory: library-owned scratch (one extra field set for
+ * ping-pong, the RK register and Kahan compensation arrays for MHD8, reduction buffers).
+ * Returns EINVAL on invalid arguments, EUNSUPPORTED on valid but unimplemented
+ * combinations, ENOMEM/ECUDA if the scratch allocation fails (nothing is leaked).
+ */
+stencil_status stencil_create(int ndim, const int64_t dims[3], int radius, const void *coeffs,
+                              int ncoeffs, int nfields, stencil_bc bc, stencil_kind kind,
+                              stencil_dtype storage, stencil_dtype compute,
+                              const stencil_params *params, stencil_t *out);
+
+/* Release a plan and its scratch (synchronises the device first).  NULL is a no-op. */
+void stencil_destroy(stencil_t plan);
+
+/*
+ * stencil_layout -- how the caller must allocate each field (Eq. 2 augmented array).
+ *
+ * A field is a dense array of padded[0] * padded[1] * padded[2] elements of the storage
+ * type, x fastest.  Interior cell (i, j, k) lives at linear element index
+ *     (origin[0] + i) + pitch[1] * (origin[1] + j) + pitch[2] * (origin[2] + k),
+ * with pitch = {1, padded[0], padded[0] * padded[1]}.  The halo of width r surrounds the
+ * interior on every used axis; origin[0] >= r is rounded up so that interior rows start on a
+ * 16-byte boundary, and padded[0] is a multiple of 32 bytes.  Any output pointer may be NULL.
+ */
+stencil_status stencil_layout(stencil_t plan, int64_t padded[3], int64_t pitch[3],
+                              int64_t origin[3], int64_t *bytes_per_field);
+
+/*
+ * stencil_step -- advance `nsteps` iterations (Sec. 2.4: f'_i = zeta(f^, i) for all i).
+ *
+ *   XCORR      nsteps sweeps of Eq. 3 (each sweep feeds the next).
+ *   DIFFUSION  nsteps forward-Euler steps of Eqs. 4-7.
+ *   MHD8       nsteps RK3 steps (3 substeps each) of Eqs. A1-A4.
+ *
+ * fields_in / fields_out: nfields device pointers each, laid out per stencil_layout, in
+ * the plan's storage type; in and out must not alias.  The result is in fields_out; the
+ * interior of fields_in is not modified.  With STENCIL_BC_PERIODIC the halo of fields_in
+ * is (re)filled first and the halo of fields_out is valid on return; with
+ * STENCIL_BC_CALLER the halo of fields_in must be filled by the caller, nsteps must be 1
+ * and the kind must be XCORR or DIFFUSION.  Asynchronous on `stream`: no host sync, no
+ * allocation, safe to capture in a CUDA graph.  Bounded device waits that expire are
+ * reported by the next stencil_sync / stencil_field_norms on the plan.
+ */
+stencil_status stencil_step(stencil_t plan, void *const *fields_in, void *const *fields_out,
+                            int nsteps, void *stream);
+
+/* stencil_halo_fill -- fill the halo of each field with the periodic image of its interior
+ * (Eq. 2 with periodic beta).  No-op for STENCIL_BC_CALLER.  Asynchronous on `stream`. */
+stencil_status stencil_halo_fill(stencil_t plan, void *const *fields, void *stream);
+
+/*
+ * stencil_mhd_rhs -- evaluate only the MHD right-hand side phi(gamma(psi(f))) (Sec. 3.3,
+ * Eqs. 8-9; Eqs. A1-A4) without time integration.  MHD8 plans only.
+ *
+ * fields: 8 device pointers in the plan's layout with a valid halo (periodic plans refill
+ * it first).  rhs: 8 device pointers to DENSE interior arrays (nx * ny * nz, x fastest) of
+ * the plan's compute type (double for F64, float otherwise).  Asynchronous on `stream`.
+ */
+stencil_status stencil_mhd_rhs(stencil_t plan, void *const *fields, void *const *rhs,
+                               void *stream);
+
+/*
+ * stencil_field_norms -- per-field reductions over the interior, accumulated in FP64 on
+ * the device: out[3*f + 0] = sum f, out[3*f + 1] = sum f^2, out[3*f + 2] = max |f|.  For
+ * MHD8 plans out[3*nfields] additionally receives the mass sum exp(lnrho) * dx*dy*dz.
+ * `out` is a host array of 3*nfields (+1 for MHD8) doubles.  Synchronises `stream`; returns
+ * STENCIL_ETIMEOUT if an earlier kernel on this plan reported an expired wait.
+ */
+stencil_status stencil_field_norms(stencil_t plan, void *const *fields, double *out,
+                                   void *stream);
+
+/* stencil_sync -- synchronise `stream` and report (then clear) any expired device wait
+ * recorded by this plan's kernels since the last check. */
+stencil_status stencil_sync(stencil_t plan, void *stream);
+
+/*
+ * Kernel variants and runtime autotuning.  Each kind has a small table of kernel variants
+ * (tile shape, pipeline depth, z-chunk length).  As in the paper's automated tuning of the
+ * thread-block decomposition (Sec. 5.1), stencil_autotune times every variant on the
+ * caller's buffers (one warm-up call, then `reps` timed calls of stencil_step(nsteps) with
+ * CUDA events on `stream`), discards variants that fail to launch, and keeps the fastest.
+ * It overwrites fields_out and synchronises `stream`.  stencil_get_variant reports the
+ * current variant, the number of variants and the current variant's name (static string);
+ * any output pointer may be NULL.  stencil_set_variant selects one (EINVAL if out of range).
+ */
+stencil_status stencil_get_variant(stencil_t plan, int *variant, int *count, const char **name);
+stencil_status stencil_set_variant(stencil_t plan, int variant);
+stencil_status stencil_autotune(stencil_t plan, void *const *fields_in, void *const *fields_out,
+                                int nsteps, int reps, void *stream);
+
+/* Human-readable name of a status code (static string). */
+const char *stencil_strerror(stencil_status status);
+
+/* Detail of the last failure on `plan` (or of the last failed stencil_create when plan is
+ * NULL, per host thread).  Valid until the next call on the plan. */
+const char *stencil_last_error_detail(stencil_t plan);
+
+/* ABI version of the loaded library (STENCIL_ABI_VERSION at build time). */
+int stencil_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STENCIL_H */

@@ -1,0 +1,307 @@
+"""ctypes binding of libstencil.so (include/stencil.h).
+
+Argument marshalling only: every step of the stencil path runs in the library's CUDA
+kernels.  The functions keep the C names (stencil_create, stencil_step, ...); ``Plan`` is a
+small convenience wrapper that owns a handle and allocates fields with PyTorch according to
+``stencil_layout``.  PyTorch provides device memory and streams, nothing else.
+
+There is no fallback: if libstencil.so is missing or fails to load, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libstencil.so")
+
+# enums (include/stencil.h)
+STENCIL_OK, STENCIL_EINVAL, STENCIL_ENOMEM, STENCIL_ECUDA, STENCIL_EUNSUPPORTED, STENCIL_ETIMEOUT = range(6)
+STENCIL_I32, STENCIL_F64, STENCIL_F32, STENCIL_BF16 = range(4)
+STENCIL_BC_PERIODIC, STENCIL_BC_CALLER = range(2)
+STENCIL_XCORR, STENCIL_DIFFUSION, STENCIL_MHD8 = range(3)
+
+EXPORTED = (
+    "stencil_create", "stencil_destroy", "stencil_layout", "stencil_step", "stencil_halo_fill",
+    "stencil_mhd_rhs", "stencil_field_norms", "stencil_sync", "stencil_strerror",
+    "stencil_last_error_detail", "stencil_abi_version", "stencil_get_variant",
+    "stencil_set_variant", "stencil_autotune",
+)
+
+
+class stencil_params(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("alpha", ctypes.c_double), ("dx", ctypes.c_double * 3),
+                ("cs0", ctypes.c_double), ("gamma", ctypes.c_double), ("cp", ctypes.c_double),
+                ("lnrho0", ctypes.c_double), ("nu", ctypes.c_double), ("eta", ctypes.c_double),
+                ("zeta", ctypes.c_double), ("mu0", ctypes.c_double)]
+
+
+class StencilError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        self.status = status
+        super().__init__(f"{where}: status {status} ({_strerror(status)}): {detail}")
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load():
+    """Load libstencil.so (raises if it is missing: there is no CPU fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libstencil.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        P, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        PP = ctypes.POINTER(ctypes.c_void_p)
+        sigs = {
+            "stencil_create": (I, [I, ctypes.POINTER(I64), I, P, I, I, I, I, I, I,
+                                   ctypes.POINTER(stencil_params), ctypes.POINTER(P)]),
+            "stencil_destroy": (None, [P]),
+            "stencil_layout": (I, [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64),
+                                   ctypes.POINTER(I64)]),
+            "stencil_step": (I, [P, PP, PP, I, P]),
+            "stencil_halo_fill": (I, [P, PP, P]),
+            "stencil_mhd_rhs": (I, [P, PP, PP, P]),
+            "stencil_field_norms": (I, [P, PP, ctypes.POINTER(D), P]),
+            "stencil_sync": (I, [P, P]),
+            "stencil_strerror": (ctypes.c_char_p, [I]),
+            "stencil_last_error_detail": (ctypes.c_char_p, [P]),
+            "stencil_abi_version": (I, []),
+            "stencil_get_variant": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(ctypes.c_char_p)]),
+            "stencil_set_variant": (I, [P, I]),
+            "stencil_autotune": (I, [P, PP, PP, I, I, P]),
+        }
+        for name, (res, args) in sigs.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _strerror(status: int) -> str:
+    try:
+        return load().stencil_strerror(status).decode()
+    except Exception:  # noqa: BLE001 -- only used to format an error message
+        return "?"
+
+
+def _check(status: int, where: str, handle=None):
+    if status != STENCIL_OK:
+        detail = load().stencil_last_error_detail(handle).decode()
+        raise StencilError(status, where, detail)
+
+
+def _ptrs(tensors):
+    arr = (ctypes.c_void_p * len(tensors))(*[int(t.data_ptr()) for t in tensors])
+    return ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p)), arr
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+
+
+# ----------------------------------------------------------------- raw C-named calls
+
+
+def stencil_create(ndim, dims, radius, coeffs, nfields, bc, kind, storage, compute, params=None):
+    lib = load()
+    d = (ctypes.c_int64 * 3)(*(list(dims) + [1, 1, 1])[:3])
+    keep = None
+    cptr, ncoeffs = None, 0
+    if coeffs is not None:
+        keep = np.ascontiguousarray(coeffs, dtype=np.int32 if storage == STENCIL_I32 else np.float64)
+        cptr, ncoeffs = keep.ctypes.data_as(ctypes.c_void_p), keep.size
+    h = ctypes.c_void_p()
+    st = lib.stencil_create(ndim, d, radius, cptr, ncoeffs, nfields, bc, kind, storage, compute,
+                            ctypes.byref(params) if params is not None else None, ctypes.byref(h))
+    _check(st, "stencil_create", None)
+    return h
+
+
+def stencil_layout(h):
+    pad, pitch, origin = (ctypes.c_int64 * 3)(), (ctypes.c_int64 * 3)(), (ctypes.c_int64 * 3)()
+    nbytes = ctypes.c_int64()
+    _check(load().stencil_layout(h, pad, pitch, origin, ctypes.byref(nbytes)), "stencil_layout", h)
+    return tuple(pad), tuple(pitch), tuple(origin), nbytes.value
+
+
+def stencil_step(h, fields_in, fields_out, nsteps, stream=None):
+    pi, ki = _ptrs(fields_in)
+    po, ko = _ptrs(fields_out)
+    _check(load().stencil_step(h, pi, po, nsteps, _stream(stream)), "stencil_step", h)
+
+
+def stencil_halo_fill(h, fields, stream=None):
+    p, k = _ptrs(fields)
+    _check(load().stencil_halo_fill(h, p, _stream(stream)), "stencil_halo_fill", h)
+
+
+def stencil_mhd_rhs(h, fields, rhs, stream=None):
+    p, k = _ptrs(fields)
+    r, kr = _ptrs(rhs)
+    _check(load().stencil_mhd_rhs(h, p, r, _stream(stream)), "stencil_mhd_rhs", h)
+
+
+def stencil_field_norms(h, fields, nvalues, stream=None):
+    p, k = _ptrs(fields)
+    out = (ctypes.c_double * nvalues)()
+    _check(load().stencil_field_norms(h, p, out, _stream(stream)), "stencil_field_norms", h)
+    return np.array(out[:], dtype=np.float64)
+
+
+def stencil_sync(h, stream=None):
+    _check(load().stencil_sync(h, _stream(stream)), "stencil_sync", h)
+
+
+def stencil_get_variant(h):
+    v, n, name = ctypes.c_int(), ctypes.c_int(), ctypes.c_char_p()
+    _check(load().stencil_get_variant(h, ctypes.byref(v), ctypes.byref(n), ctypes.byref(name)),
+           "stencil_get_variant", h)
+    return v.value, n.value, name.value.decode()
+
+
+def stencil_set_variant(h, variant):
+    _check(load().stencil_set_variant(h, variant), "stencil_set_variant", h)
+
+
+def stencil_autotune(h, fields_in, fields_out, nsteps=1, reps=3, stream=None):
+    pi, ki = _ptrs(fields_in)
+    po, ko = _ptrs(fields_out)
+    _check(load().stencil_autotune(h, pi, po, nsteps, reps, _stream(stream)), "stencil_autotune", h)
+
+
+def stencil_destroy(h):
+    if h:
+        load().stencil_destroy(h)
+
+
+# ----------------------------------------------------------------- convenience wrapper
+
+_TORCH_DT = {STENCIL_I32: "int32", STENCIL_F64: "float64", STENCIL_F32: "float32", STENCIL_BF16: "bfloat16"}
+_NP_DT = {STENCIL_I32: np.int32, STENCIL_F64: np.float64, STENCIL_F32: np.float32}
+
+
+class Plan:
+    """Owns one stencil plan; allocates fields in its padded layout with PyTorch."""
+
+    def __init__(self, ndim, dims, radius, nfields, bc, kind, storage, compute, coeffs=None,
+                 params=None):
+        self.ndim, self.radius, self.nfields = ndim, radius, nfields
+        self.dims = tuple(dims) + (1,) * (3 - len(dims))
+        self.kind, self.storage, self.compute, self.bc = kind, storage, compute, bc
+        self.params = params
+        self.h = stencil_create(ndim, self.dims, radius, coeffs, nfields, bc, kind, storage,
+                                compute, params)
+        self.padded, self.pitch, self.origin, self.bytes_per_field = stencil_layout(self.h)
+
+    def close(self):
+        if self.h:
+            stencil_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 -- interpreter shutdown
+            pass
+
+    # -- memory
+    @property
+    def torch_dtype(self):
+        import torch
+        return getattr(torch, _TORCH_DT[self.storage])
+
+    def alloc(self, device="cuda", fill=0):
+        """nfields flat tensors of padded[0]*padded[1]*padded[2] elements."""
+        import torch
+        n = self.padded[0] * self.padded[1] * self.padded[2]
+        return [torch.full((n,), fill, dtype=self.torch_dtype, device=device) for _ in range(self.nfields)]
+
+    def view3(self, t):
+        """(z, y, x) view of a whole padded field."""
+        return t.view(self.padded[2], self.padded[1], self.padded[0])
+
+    def interior(self, t):
+        """(nz, ny, nx) view of the interior (1D: (nx,))."""
+        v = self.view3(t)
+        ox, oy, oz = self.origin
+        nx, ny, nz = self.dims
+        v = v[oz:oz + nz, oy:oy + ny, ox:ox + nx]
+        return v[0, 0] if self.ndim == 1 else v
+
+    def upload(self, fields, arrays):
+        """Copy host arrays (interior shape) into the interior of device fields."""
+        import torch
+        for t, a in zip(fields, arrays):
+            src = torch.from_numpy(np.ascontiguousarray(a))
+            self.interior(t).copy_(src.to(self.torch_dtype))
+
+    def download(self, fields, dtype=np.float64):
+        """Interiors of device fields as one host array (nfields, ...)."""
+        import torch
+        out = [self.interior(t).to(torch.float64 if dtype == np.float64 else self.torch_dtype).cpu().numpy()
+               for t in fields]
+        return np.stack(out)
+
+    # -- calls
+    def step(self, fin, fout, nsteps=1, stream=None):
+        stencil_step(self.h, fin, fout, nsteps, stream)
+
+    def halo_fill(self, fields, stream=None):
+        stencil_halo_fill(self.h, fields, stream)
+
+    def mhd_rhs(self, fields, rhs, stream=None):
+        stencil_mhd_rhs(self.h, fields, rhs, stream)
+
+    def norms(self, fields, stream=None):
+        n = 3 * self.nfields + (1 if self.kind == STENCIL_MHD8 else 0)
+        return stencil_field_norms(self.h, fields, n, stream)
+
+    def sync(self, stream=None):
+        stencil_sync(self.h, stream)
+
+    def variant(self):
+        return stencil_get_variant(self.h)
+
+    def set_variant(self, v):
+        stencil_set_variant(self.h, v)
+
+    def autotune(self, fin, fout, nsteps=1, reps=3, stream=None):
+        stencil_autotune(self.h, fin, fout, nsteps, reps, stream)
+        return self.variant()
+
+
+def mhd_params(n, dt=None, **kw) -> stencil_params:
+    """stencil_params for the 8-field system on a periodic (2 pi)^3 box of n^3 (or (nz,ny,nx))."""
+    nz, ny, nx = (n, n, n) if np.isscalar(n) else tuple(n)
+    p = stencil_params()
+    tau = 2.0 * np.pi
+    p.dx[0], p.dx[1], p.dx[2] = tau / nx, tau / ny, tau / nz
+    vals = dict(cs0=1.0, gamma=5.0 / 3.0, cp=1.0, lnrho0=0.0, nu=5e-3, eta=5e-3, zeta=0.0, mu0=1.0)
+    vals.update(kw)
+    for k, v in vals.items():
+        setattr(p, k, v)
+    p.dt = 0.1 * min(p.dx[0], p.dx[1], p.dx[2]) if dt is None else dt
+    return p
+
+
+def heat_params(n, alpha=1.0, dt=None) -> stencil_params:
+    """stencil_params for the heat equation on a periodic (2 pi)^3 box; dt = 0.1 dx^2."""
+    nz, ny, nx = (n, n, n) if np.isscalar(n) else tuple(n)
+    p = stencil_params()
+    tau = 2.0 * np.pi
+    p.dx[0], p.dx[1], p.dx[2] = tau / nx, tau / ny, tau / nz
+    p.alpha = alpha
+    p.dt = 0.1 * min(p.dx[0], p.dx[1], p.dx[2]) ** 2 if dt is None else dt
+    return p

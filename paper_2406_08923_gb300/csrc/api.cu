@@ -1,0 +1,642 @@
+// api.cu -- the C ABI of include/stencil.h: plans, layout, validation, scratch ownership,
+// pass scheduling (ping-pong), TMA descriptor encoding and error reporting.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/stencil.h"
+#include "internal.h"
+
+using namespace stn;
+
+namespace {
+
+thread_local std::string g_create_detail;
+
+struct TmaEntry {
+    const void *ptr;
+    int box[3];
+    CUtensorMap map;
+};
+
+int esize_of(stencil_dtype t) {
+    switch (t) {
+    case STENCIL_I32: return 4;
+    case STENCIL_F64: return 8;
+    case STENCIL_F32: return 4;
+    case STENCIL_BF16: return 2;
+    }
+    return 0;
+}
+
+const char *dtype_name(stencil_dtype t) {
+    switch (t) {
+    case STENCIL_I32: return "i32";
+    case STENCIL_F64: return "f64";
+    case STENCIL_F32: return "f32";
+    case STENCIL_BF16: return "bf16";
+    }
+    return "?";
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+}  // namespace
+
+struct stencil_plan {
+    int device = 0;
+    int ndim = 0, radius = 0, nfields = 0;
+    stencil_kind kind = STENCIL_XCORR;
+    stencil_bc bc = STENCIL_BC_PERIODIC;
+    stencil_dtype storage = STENCIL_F64, compute = STENCIL_F64;
+    stencil_params par{};
+    Geom geom{};
+    int esize = 0;
+    int64_t bytes_per_field = 0;
+    // coefficients
+    int32_t gi[9] = {};
+    double gd[9] = {};
+    float gf[9] = {};
+    DiffCoef dcoef{};
+    MhdConst mconst{};
+    // library-owned scratch
+    void *tmp[8] = {};  // second field set for ping-pong (padded layout)
+    void *w[8] = {};    // RK register (dense interior, storage type)
+    void *kc[8] = {};   // Kahan compensation (dense interior, storage type)
+    double *partials = nullptr;
+    double *red_out = nullptr;
+    unsigned *err = nullptr;
+    int variant = 0;
+    std::vector<TmaEntry> tma;
+    std::string detail;
+};
+
+static stencil_status fail(stencil_t p, stencil_status st, const std::string &msg) {
+    if (p) p->detail = msg;
+    else g_create_detail = msg;
+    return st;
+}
+
+static stencil_status cuda_fail(stencil_t p, cudaError_t e, const char *what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    cudaGetLastError();  // clear the sticky non-fatal error state
+    return fail(p, e == cudaErrorMemoryAllocation ? STENCIL_ENOMEM : STENCIL_ECUDA, m);
+}
+
+#define CK(p, call, what)                                   \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(p, e_, what); \
+    } while (0)
+
+static stencil_status check_device(stencil_t p) {
+    int d = -1;
+    cudaError_t e = cudaGetDevice(&d);
+    if (e != cudaSuccess) return cuda_fail(p, e, "cudaGetDevice");
+    if (d != p->device)
+        return fail(p, STENCIL_EINVAL, "plan belongs to device " + std::to_string(p->device) +
+                                           " but device " + std::to_string(d) + " is current");
+    return STENCIL_OK;
+}
+
+static int storage_code(stencil_dtype t) {
+    switch (t) {
+    case STENCIL_I32: return 0;
+    case STENCIL_F64: return 1;
+    case STENCIL_F32: return 2;
+    case STENCIL_BF16: return 3;
+    }
+    return -1;
+}
+
+static void free_scratch(stencil_t p) {
+    for (int q = 0; q < 8; ++q) {
+        if (p->tmp[q]) cudaFree(p->tmp[q]);
+        if (p->w[q]) cudaFree(p->w[q]);
+        if (p->kc[q]) cudaFree(p->kc[q]);
+        p->tmp[q] = p->w[q] = p->kc[q] = nullptr;
+    }
+    if (p->partials) cudaFree(p->partials);
+    if (p->red_out) cudaFree(p->red_out);
+    if (p->err) cudaFree(p->err);
+    p->partials = p->red_out = nullptr;
+    p->err = nullptr;
+}
+
+// Encode (or fetch from the per-plan cache) the TMA descriptor of a field for a box shape.
+static stencil_status tma_map(stencil_t p, const void *ptr, const int box[3], CUtensorMap *out) {
+    for (auto &e : p->tma)
+        if (e.ptr == ptr && e.box[0] == box[0] && e.box[1] == box[1] && e.box[2] == box[2]) {
+            *out = e.map;
+            return STENCIL_OK;
+        }
+    auto fn = encode_fn();
+    if (!fn) return fail(p, STENCIL_ECUDA, "cuTensorMapEncodeTiled entry point unavailable");
+    CUtensorMapDataType dt;
+    switch (p->storage) {
+    case STENCIL_F64: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT64; break;
+    case STENCIL_F32: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32; break;
+    case STENCIL_BF16: dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16; break;
+    default: dt = CU_TENSOR_MAP_DATA_TYPE_INT32; break;
+    }
+    const Geom &g = p->geom;
+    cuuint64_t dims[3] = {(cuuint64_t)g.pad[0], (cuuint64_t)g.pad[1], (cuuint64_t)g.pad[2]};
+    cuuint64_t strides[2] = {(cuuint64_t)(g.pad[0] * p->esize), (cuuint64_t)(g.pad[0] * g.pad[1] * p->esize)};
+    cuuint32_t bx[3] = {(cuuint32_t)box[0], (cuuint32_t)box[1], (cuuint32_t)box[2]};
+    cuuint32_t es[3] = {1, 1, 1};
+    TmaEntry ent;
+    ent.ptr = ptr;
+    std::memcpy(ent.box, box, sizeof(ent.box));
+    CUresult r = fn(&ent.map, dt, 3, const_cast<void *>(ptr), dims, strides, bx, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return fail(p, STENCIL_ECUDA, "cuTensorMapEncodeTiled failed with CUresult " + std::to_string((int)r));
+    if (p->tma.size() >= 96) p->tma.erase(p->tma.begin());
+    p->tma.push_back(ent);
+    *out = ent.map;
+    return STENCIL_OK;
+}
+
+static stencil_status check_ptrs(stencil_t p, void *const *f, const char *what) {
+    if (!f) return fail(p, STENCIL_EINVAL, std::string(what) + " is NULL");
+    for (int q = 0; q < p->nfields; ++q) {
+        if (!f[q]) return fail(p, STENCIL_EINVAL, std::string(what) + "[" + std::to_string(q) + "] is NULL");
+        if (reinterpret_cast<uintptr_t>(f[q]) % 16 != 0)
+            return fail(p, STENCIL_EINVAL, std::string(what) + "[" + std::to_string(q) + "] is not 16-byte aligned");
+    }
+    return STENCIL_OK;
+}
+
+static Ptrs8 ptrs(void *const *f, int n) {
+    Ptrs8 r{};
+    for (int q = 0; q < n; ++q) r.p[q] = f[q];
+    return r;
+}
+
+extern "C" {
+
+int stencil_abi_version(void) { return STENCIL_ABI_VERSION; }
+
+const char *stencil_strerror(stencil_status s) {
+    switch (s) {
+    case STENCIL_OK: return "STENCIL_OK";
+    case STENCIL_EINVAL: return "STENCIL_EINVAL: invalid argument";
+    case STENCIL_ENOMEM: return "STENCIL_ENOMEM: out of memory";
+    case STENCIL_ECUDA: return "STENCIL_ECUDA: CUDA error";
+    case STENCIL_EUNSUPPORTED: return "STENCIL_EUNSUPPORTED: combination not implemented";
+    case STENCIL_ETIMEOUT: return "STENCIL_ETIMEOUT: bounded device wait expired";
+    }
+    return "unknown stencil_status";
+}
+
+const char *stencil_last_error_detail(stencil_t p) {
+    return p ? p->detail.c_str() : g_create_detail.c_str();
+}
+
+stencil_status stencil_create(int ndim, const int64_t dims[3], int radius, const void *coeffs,
+                              int ncoeffs, int nfields, stencil_bc bc, stencil_kind kind,
+                              stencil_dtype storage, stencil_dtype compute,
+                              const stencil_params *params, stencil_t *out) {
+    g_create_detail.clear();
+    if (!out) return fail(nullptr, STENCIL_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!dims) return fail(nullptr, STENCIL_EINVAL, "dims is NULL");
+    if ((int)kind < 0 || (int)kind > 2) return fail(nullptr, STENCIL_EINVAL, "unknown kind");
+    if ((int)bc < 0 || (int)bc > 1) return fail(nullptr, STENCIL_EINVAL, "unknown boundary condition");
+    if ((int)storage < 0 || (int)storage > 3 || (int)compute < 0 || (int)compute > 3)
+        return fail(nullptr, STENCIL_EINVAL, "unknown dtype");
+    if (ndim < 1 || ndim > 3) return fail(nullptr, STENCIL_EINVAL, "ndim must be 1, 2 or 3");
+    for (int a = 0; a < ndim; ++a)
+        if (dims[a] < 1 || dims[a] > (int64_t)1 << 31)
+            return fail(nullptr, STENCIL_EINVAL, "dims[" + std::to_string(a) + "] out of range");
+    if (radius < 0) return fail(nullptr, STENCIL_EINVAL, "radius must be >= 0");
+
+    // kind-specific rules
+    if (kind == STENCIL_XCORR) {
+        if (ndim != 1) return fail(nullptr, STENCIL_EUNSUPPORTED, "XCORR supports ndim = 1");
+        if (radius > 4) return fail(nullptr, STENCIL_EUNSUPPORTED, "XCORR supports radius 0..4");
+        if (ncoeffs != 2 * radius + 1 || !coeffs)
+            return fail(nullptr, STENCIL_EINVAL, "XCORR needs 2*radius+1 coefficients");
+        if (nfields != 1) return fail(nullptr, STENCIL_EINVAL, "XCORR needs nfields = 1");
+        if (storage != compute || storage == STENCIL_BF16)
+            return fail(nullptr, STENCIL_EUNSUPPORTED, "XCORR supports I32/I32, F64/F64, F32/F32");
+    } else {
+        if (radius != 3) return fail(nullptr, STENCIL_EINVAL, "DIFFUSION and MHD8 use radius 3");
+        if (ncoeffs != 0) return fail(nullptr, STENCIL_EINVAL, "DIFFUSION and MHD8 take no coefficients");
+        if (!params) return fail(nullptr, STENCIL_EINVAL, "params is NULL");
+        if (ndim != 3) return fail(nullptr, STENCIL_EUNSUPPORTED, "DIFFUSION and MHD8 support ndim = 3");
+        for (int a = 0; a < 3; ++a)
+            if (!(params->dx[a] > 0.0) || !std::isfinite(params->dx[a]))
+                return fail(nullptr, STENCIL_EINVAL, "grid spacing must be positive and finite");
+        if (!std::isfinite(params->dt)) return fail(nullptr, STENCIL_EINVAL, "dt must be finite");
+        if (kind == STENCIL_DIFFUSION) {
+            if (nfields != 1) return fail(nullptr, STENCIL_EINVAL, "DIFFUSION needs nfields = 1");
+            if (!((storage == STENCIL_F64 && compute == STENCIL_F64) ||
+                  (storage == STENCIL_F32 && compute == STENCIL_F32)))
+                return fail(nullptr, STENCIL_EUNSUPPORTED, "DIFFUSION supports F64/F64 and F32/F32");
+        } else {
+            if (nfields != 8) return fail(nullptr, STENCIL_EINVAL, "MHD8 needs nfields = 8");
+            if (bc != STENCIL_BC_PERIODIC)
+                return fail(nullptr, STENCIL_EUNSUPPORTED, "MHD8 supports periodic boundaries only");
+            if (!((storage == STENCIL_F64 && compute == STENCIL_F64) ||
+                  (storage == STENCIL_F32 && compute == STENCIL_F32) ||
+                  (storage == STENCIL_BF16 && compute == STENCIL_F32)))
+                return fail(nullptr, STENCIL_EUNSUPPORTED, "MHD8 supports F64/F64, F32/F32, BF16/F32");
+            if (!(params->cp > 0.0) || !(params->gamma > 1.0) || !(params->mu0 > 0.0))
+                return fail(nullptr, STENCIL_EINVAL, "MHD8 needs cp > 0, gamma > 1, mu0 > 0");
+        }
+    }
+    if (bc == STENCIL_BC_PERIODIC)
+        for (int a = 0; a < ndim; ++a)
+            if (dims[a] < 2 * radius + 1)
+                return fail(nullptr, STENCIL_EINVAL, "periodic extents must be >= 2*radius+1");
+
+    stencil_plan *p = new (std::nothrow) stencil_plan;
+    if (!p) return fail(nullptr, STENCIL_ENOMEM, "host allocation of the plan failed");
+    p->ndim = ndim;
+    p->radius = radius;
+    p->nfields = nfields;
+    p->kind = kind;
+    p->bc = bc;
+    p->storage = storage;
+    p->compute = compute;
+    if (params) p->par = *params;
+    p->esize = esize_of(storage);
+
+    // layout: x origin rounded up to 16 bytes, row pitch to 32 bytes
+    const int v16 = 16 / p->esize;
+    const int64_t xoff = ((radius + v16 - 1) / v16) * v16;
+    const int64_t align32 = 32 / p->esize;
+    Geom &g = p->geom;
+    for (int a = 0; a < 3; ++a) {
+        g.n[a] = a < ndim ? dims[a] : 1;
+        g.off[a] = (a == 0) ? xoff : (a < ndim ? radius : 0);
+    }
+    g.pad[0] = ((xoff + g.n[0] + xoff + align32 - 1) / align32) * align32;
+    g.pad[1] = ndim >= 2 ? g.n[1] + 2 * radius : 1;
+    g.pad[2] = ndim >= 3 ? g.n[2] + 2 * radius : 1;
+    p->bytes_per_field = g.pad[0] * g.pad[1] * g.pad[2] * p->esize;
+
+    // coefficients / constants
+    if (kind == STENCIL_XCORR) {
+        for (int j = 0; j < ncoeffs; ++j) {
+            if (storage == STENCIL_I32) p->gi[j] = static_cast<const int32_t *>(coeffs)[j];
+            else {
+                p->gd[j] = static_cast<const double *>(coeffs)[j];
+                p->gf[j] = (float)p->gd[j];
+            }
+        }
+    } else {
+        static const double W1[3] = {3.0 / 4.0, -3.0 / 20.0, 1.0 / 60.0};
+        static const double W2C = -49.0 / 18.0;
+        static const double W2[3] = {3.0 / 2.0, -3.0 / 20.0, 1.0 / 90.0};
+        static const double WM[3] = {270.0, -27.0, 2.0};
+        const double *h = params->dx;
+        if (kind == STENCIL_DIFFUSION) {
+            // Eq. 5/7: g = c1 + dt alpha (c2_x + c2_y + c2_z)
+            const double s = params->dt * params->alpha;
+            double g0 = 1.0;
+            for (int a = 0; a < 3; ++a) {
+                g0 += s * W2C / (h[a] * h[a]);
+                for (int i = 0; i < 3; ++i) p->dcoef.ga[a][i] = s * W2[i] / (h[a] * h[a]);
+            }
+            p->dcoef.g0 = g0;
+        } else {
+            MhdConst &c = p->mconst;
+            for (int a = 0; a < 3; ++a) {
+                c.d2c[a] = W2C / (h[a] * h[a]);
+                for (int i = 0; i < 3; ++i) {
+                    c.d1[a][i] = W1[i] / h[a];
+                    c.d2[a][i] = W2[i] / (h[a] * h[a]);
+                }
+            }
+            const int pairs[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+            for (int pi = 0; pi < 3; ++pi)
+                for (int i = 0; i < 3; ++i)
+                    c.dm[pi][i] = WM[i] / (720.0 * h[pairs[pi][0]] * h[pairs[pi][1]]);
+            c.cs0sq = params->cs0 * params->cs0;
+            c.gamma = params->gamma;
+            c.inv_cp = 1.0 / params->cp;
+            c.lnrho0 = params->lnrho0;
+            c.nu = params->nu;
+            c.eta = params->eta;
+            c.zeta = params->zeta;
+            c.mu0 = params->mu0;
+            c.inv_mu0 = 1.0 / params->mu0;
+            c.cp_gm1 = params->cp * (params->gamma - 1.0);
+            c.dt = params->dt;
+        }
+    }
+
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) {
+        stencil_status st = cuda_fail(nullptr, e, "cudaGetDevice");
+        delete p;
+        return st;
+    }
+    // scratch
+    auto alloc = [&](void **dst, size_t bytes, const char *what) -> bool {
+        cudaError_t ee = cudaMalloc(dst, bytes);
+        if (ee != cudaSuccess) {
+            cuda_fail(nullptr, ee, what);
+            *dst = nullptr;
+            return false;
+        }
+        return true;
+    };
+    bool okay = true;
+    const size_t ncell = (size_t)(g.n[0] * g.n[1] * g.n[2]);
+    for (int q = 0; q < nfields && okay; ++q) okay = alloc(&p->tmp[q], p->bytes_per_field, "cudaMalloc(ping-pong field)");
+    if (kind == STENCIL_MHD8) {
+        for (int q = 0; q < 8 && okay; ++q) okay = alloc(&p->w[q], ncell * p->esize, "cudaMalloc(RK register)");
+        if (storage != STENCIL_F64)
+            for (int q = 0; q < 8 && okay; ++q) okay = alloc(&p->kc[q], ncell * p->esize, "cudaMalloc(Kahan term)");
+    }
+    if (okay) okay = alloc((void **)&p->partials, sizeof(double) * norms_blocks() * nfields * 4, "cudaMalloc(norm partials)");
+    if (okay) okay = alloc((void **)&p->red_out, sizeof(double) * nfields * 4, "cudaMalloc(norm result)");
+    if (okay) okay = alloc((void **)&p->err, sizeof(unsigned), "cudaMalloc(error word)");
+    if (okay) {
+        e = cudaMemset(p->err, 0, sizeof(unsigned));
+        if (e != cudaSuccess) { cuda_fail(nullptr, e, "cudaMemset(error word)"); okay = false; }
+    }
+    if (!okay) {
+        stencil_status st = g_create_detail.find("cudaErrorMemoryAllocation") != std::string::npos ? STENCIL_ENOMEM : STENCIL_ECUDA;
+        free_scratch(p);
+        delete p;
+        return st;
+    }
+    *out = p;
+    return STENCIL_OK;
+}
+
+void stencil_destroy(stencil_t p) {
+    if (!p) return;
+    cudaDeviceSynchronize();
+    free_scratch(p);
+    delete p;
+}
+
+stencil_status stencil_layout(stencil_t p, int64_t padded[3], int64_t pitch[3], int64_t origin[3],
+                              int64_t *bytes_per_field) {
+    if (!p) return fail(nullptr, STENCIL_EINVAL, "plan is NULL");
+    const Geom &g = p->geom;
+    for (int a = 0; a < 3; ++a) {
+        if (padded) padded[a] = g.pad[a];
+        if (origin) origin[a] = g.off[a];
+    }
+    if (pitch) {
+        pitch[0] = 1;
+        pitch[1] = g.pad[0];
+        pitch[2] = g.pad[0] * g.pad[1];
+    }
+    if (bytes_per_field) *bytes_per_field = p->bytes_per_field;
+    return STENCIL_OK;
+}
+
+stencil_status stencil_halo_fill(stencil_t p, void *const *fields, void *stream) {
+    if (!p) return fail(nullptr, STENCIL_EINVAL, "plan is NULL");
+    stencil_status st = check_device(p);
+    if (st != STENCIL_OK) return st;
+    if ((st = check_ptrs(p, fields, "fields")) != STENCIL_OK) return st;
+    if (p->bc != STENCIL_BC_PERIODIC) return STENCIL_OK;
+    CK(p, launch_halo_fill(p->geom, p->radius, p->esize, ptrs(fields, p->nfields), p->nfields,
+                           (cudaStream_t)stream),
+       "halo_fill launch");
+    return STENCIL_OK;
+}
+
+// One pass of the plan's kernel from src to dst (sub = RK substep for MHD8).
+static stencil_status run_pass(stencil_t p, void *const *src, void *const *dst, int sweeps, int sub,
+                               cudaStream_t s) {
+    const bool periodic = p->bc == STENCIL_BC_PERIODIC;
+    const Geom &g = p->geom;
+    if (p->kind == STENCIL_XCORR) {
+        const void *cf = p->storage == STENCIL_I32 ? (const void *)p->gi
+                         : p->storage == STENCIL_F64 ? (const void *)p->gd : (const void *)p->gf;
+        CK(p, launch_xcorr(storage_code(p->storage), p->radius, src[0], dst[0], g, cf, sweeps, periodic,
+                           periodic, s),
+           "xcorr launch");
+        return STENCIL_OK;
+    }
+    if (p->kind == STENCIL_DIFFUSION) {
+        int box[3];
+        diffusion_box(storage_code(p->storage), p->variant, box);
+        CUtensorMap m;
+        stencil_status st = tma_map(p, src[0], box, &m);
+        if (st != STENCIL_OK) return st;
+        CK(p, launch_diffusion(storage_code(p->storage), &m, dst[0], g, p->dcoef, periodic, p->err, s,
+                               p->variant),
+           "diffusion launch");
+        return STENCIL_OK;
+    }
+    int box[3];
+    mhd_box(storage_code(p->storage), p->variant, box);
+    MhdMaps maps;
+    for (int q = 0; q < 8; ++q) {
+        stencil_status st = tma_map(p, src[q], box, &maps.m[q]);
+        if (st != STENCIL_OK) return st;
+    }
+    Ptrs8 none{};
+    CK(p, launch_mhd(storage_code(p->storage), 0, sub, maps, ptrs(dst, 8), ptrs(p->w, 8), ptrs(p->kc, 8), none,
+                     g, p->mconst, true, p->err, s, p->variant),
+       "mhd launch");
+    return STENCIL_OK;
+}
+
+stencil_status stencil_step(stencil_t p, void *const *fin, void *const *fout, int nsteps, void *stream) {
+    if (!p) return fail(nullptr, STENCIL_EINVAL, "plan is NULL");
+    stencil_status st = check_device(p);
+    if (st != STENCIL_OK) return st;
+    if ((st = check_ptrs(p, fin, "fields_in")) != STENCIL_OK) return st;
+    if ((st = check_ptrs(p, fout, "fields_out")) != STENCIL_OK) return st;
+    for (int q = 0; q < p->nfields; ++q)
+        for (int r = 0; r < p->nfields; ++r)
+            if (fin[q] == fout[r]) return fail(p, STENCIL_EINVAL, "fields_in and fields_out alias");
+    if (nsteps < 0) return fail(p, STENCIL_EINVAL, "nsteps must be >= 0");
+    const bool periodic = p->bc == STENCIL_BC_PERIODIC;
+    if (!periodic && nsteps != 1)
+        return fail(p, STENCIL_EINVAL, "caller-filled boundaries allow exactly one step per call");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t ncell = (size_t)(p->geom.n[0] * p->geom.n[1] * p->geom.n[2]);
+    if (nsteps == 0) {
+        for (int q = 0; q < p->nfields; ++q)
+            CK(p, cudaMemcpyAsync(fout[q], fin[q], p->bytes_per_field, cudaMemcpyDeviceToDevice, s), "copy");
+        if (periodic) return stencil_halo_fill(p, fout, stream);
+        return STENCIL_OK;
+    }
+
+    // pass list
+    std::vector<int> sweeps;  // XCORR: sweeps per launch; others: one entry per pass
+    int npass;
+    if (p->kind == STENCIL_XCORR) {
+        const int maxs = periodic ? xcorr_max_sweeps_per_launch() : 1;
+        for (int left = nsteps; left > 0;) {
+            int k = std::min(left, maxs);
+            sweeps.push_back(k);
+            left -= k;
+        }
+        npass = (int)sweeps.size();
+    } else {
+        npass = p->kind == STENCIL_MHD8 ? 3 * nsteps : nsteps;
+        sweeps.assign(npass, 1);
+    }
+    if (periodic && p->kind != STENCIL_XCORR)
+        CK(p, launch_halo_fill(p->geom, p->radius, p->esize, ptrs(fin, p->nfields), p->nfields, s),
+           "halo_fill launch");
+    if (p->kind == STENCIL_MHD8 && p->storage != STENCIL_F64)
+        for (int q = 0; q < 8; ++q) CK(p, cudaMemsetAsync(p->kc[q], 0, ncell * p->esize, s), "clear Kahan terms");
+
+    // ping-pong so that the last pass writes fields_out and fields_in is only read
+    void *const *src = fin;
+    for (int i = 1; i <= npass; ++i) {
+        void *const *dst = ((npass - i) % 2 == 0) ? fout : (void *const *)p->tmp;
+        st = run_pass(p, src, dst, sweeps[i - 1], (i - 1) % 3, s);
+        if (st != STENCIL_OK) return st;
+        src = dst;
+    }
+    return STENCIL_OK;
+}
+
+stencil_status stencil_mhd_rhs(stencil_t p, void *const *fields, void *const *rhs, void *stream) {
+    if (!p) return fail(nullptr, STENCIL_EINVAL, "plan is NULL");
+    if (p->kind != STENCIL_MHD8) return fail(p, STENCIL_EINVAL, "stencil_mhd_rhs needs an MHD8 plan");
+    stencil_status st = check_device(p);
+    if (st != STENCIL_OK) return st;
+    if ((st = check_ptrs(p, fields, "fields")) != STENCIL_OK) return st;
+    if ((st = check_ptrs(p, rhs, "rhs")) != STENCIL_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (p->bc == STENCIL_BC_PERIODIC)
+        CK(p, launch_halo_fill(p->geom, p->radius, p->esize, ptrs(fields, 8), 8, s), "halo_fill launch");
+    int box[3];
+    mhd_box(storage_code(p->storage), p->variant, box);
+    MhdMaps maps;
+    for (int q = 0; q < 8; ++q) {
+        st = tma_map(p, fields[q], box, &maps.m[q]);
+        if (st != STENCIL_OK) return st;
+    }
+    Ptrs8 none{};
+    CK(p, launch_mhd(storage_code(p->storage), 1, 0, maps, none, none, none, ptrs(rhs, 8), p->geom, p->mconst,
+                     false, p->err, s, p->variant),
+       "mhd rhs launch");
+    return STENCIL_OK;
+}
+
+static stencil_status read_err(stencil_t p, cudaStream_t s) {
+    unsigned h = 0;
+    CK(p, cudaMemcpyAsync(&h, p->err, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "read error word");
+    CK(p, cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    if (h) {
+        CK(p, cudaMemsetAsync(p->err, 0, sizeof(unsigned), s), "clear error word");
+        CK(p, cudaStreamSynchronize(s), "cudaStreamSynchronize");
+        if (h & ERR_TIMEOUT) return fail(p, STENCIL_ETIMEOUT, "a bounded mbarrier wait expired in a stencil kernel");
+    }
+    return STENCIL_OK;
+}
+
+stencil_status stencil_sync(stencil_t p, void *stream) {
+    if (!p) return fail(nullptr, STENCIL_EINVAL, "plan is NULL");
+    stencil_status st = check_device(p);
+    if (st != STENCIL_OK) return st;
+    return read_err(p, (cudaStream_t)stream);
+}
+
+stencil_status stencil_field_norms(stencil_t p, void *const *fields, double *out, void *stream) {
+    if (!p) return fail(nullptr, STENCIL_EINVAL, "plan is NULL");
+    if (!out) return fail(p, STENCIL_EINVAL, "out is NULL");
+    stencil_status st = check_device(p);
+    if (st != STENCIL_OK) return st;
+    if ((st = check_ptrs(p, fields, "fields")) != STENCIL_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool mass = p->kind == STENCIL_MHD8;
+    CK(p, launch_norms(storage_code(p->storage), ptrs(fields, p->nfields), p->nfields, p->geom, mass, p->partials,
+                       p->red_out, s),
+       "norms launch");
+    std::vector<double> buf(p->nfields * 4);
+    CK(p, cudaMemcpyAsync(buf.data(), p->red_out, sizeof(double) * buf.size(), cudaMemcpyDeviceToHost, s),
+       "copy norms");
+    st = read_err(p, s);
+    if (st != STENCIL_OK) return st;
+    for (int q = 0; q < p->nfields; ++q)
+        for (int c = 0; c < 3; ++c) out[3 * q + c] = buf[4 * q + c];
+    if (mass) out[3 * p->nfields] = buf[3] * p->par.dx[0] * p->par.dx[1] * p->par.dx[2];
+    return STENCIL_OK;
+}
+
+static int num_variants(stencil_t p) {
+    if (p->kind == STENCIL_DIFFUSION) return diffusion_num_variants(storage_code(p->storage));
+    if (p->kind == STENCIL_MHD8) return mhd_num_variants(storage_code(p->storage));
+    return 1;
+}
+
+static const char *variant_name(stencil_t p, int v) {
+    if (p->kind == STENCIL_DIFFUSION) return diffusion_variant_name(storage_code(p->storage), v);
+    if (p->kind == STENCIL_MHD8) return mhd_variant_name(storage_code(p->storage), v);
+    return "chunk2048_temporal_blocking";
+}
+
+stencil_status stencil_get_variant(stencil_t p, int *variant, int *count, const char **name) {
+    if (!p) return fail(nullptr, STENCIL_EINVAL, "plan is NULL");
+    if (variant) *variant = p->variant;
+    if (count) *count = num_variants(p);
+    if (name) *name = variant_name(p, p->variant);
+    return STENCIL_OK;
+}
+
+stencil_status stencil_set_variant(stencil_t p, int variant) {
+    if (!p) return fail(nullptr, STENCIL_EINVAL, "plan is NULL");
+    if (variant < 0 || variant >= num_variants(p))
+        return fail(p, STENCIL_EINVAL, "variant out of range");
+    p->variant = variant;
+    return STENCIL_OK;
+}
+
+stencil_status stencil_autotune(stencil_t p, void *const *fin, void *const *fout, int nsteps, int reps,
+                                void *stream) {
+    if (!p) return fail(nullptr, STENCIL_EINVAL, "plan is NULL");
+    if (nsteps < 1 || reps < 1) return fail(p, STENCIL_EINVAL, "nsteps and reps must be >= 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    CK(p, cudaEventCreate(&e0), "cudaEventCreate");
+    CK(p, cudaEventCreate(&e1), "cudaEventCreate");
+    const int keep = p->variant;
+    int best = -1;
+    float best_ms = 0.f;
+    for (int v = 0; v < num_variants(p); ++v) {
+        p->variant = v;
+        if (stencil_step(p, fin, fout, nsteps, stream) != STENCIL_OK) continue;  // failed launch: discard
+        if (cudaEventRecord(e0, s) != cudaSuccess) break;
+        bool ok = true;
+        for (int r = 0; r < reps && ok; ++r) ok = stencil_step(p, fin, fout, nsteps, stream) == STENCIL_OK;
+        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ok && read_err(p, s) == STENCIL_OK && (best < 0 || ms < best_ms)) {
+            best = v;
+            best_ms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p->variant = best >= 0 ? best : keep;
+    if (best < 0) return fail(p, STENCIL_ECUDA, "no kernel variant launched successfully");
+    return STENCIL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,61 @@
+// halo.cu -- periodic halo fill of augmented arrays (Sec. 2.4, Eq. 2 with periodic beta).
+//
+// One launch fills every halo cell of up to 8 fields directly from the interior cell it
+// images (index arithmetic modulo the interior extent on each axis), so no ordering between
+// faces, edges and corners is needed.  Grid: x = blocks striding over the halo cells of one
+// padded z-plane, y = padded z-plane, z = field.
+#include "internal.h"
+
+namespace stn {
+
+template <typename T>
+__global__ void halo_fill_kernel(Ptrs8 f, Geom g, int r) {
+    T *base = static_cast<T *>(f.p[blockIdx.z]);
+    const int64_t nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const int64_t hy = ny > 1 ? r : 0, hz = nz > 1 ? r : 0;
+    const int64_t wx = nx + 2 * r, wy = ny + 2 * hy;
+    const int64_t kr = blockIdx.y;  // z in the used range [0, nz + 2 hz)
+    const bool halo_plane = (kr < hz) || (kr >= nz + hz);
+    const int64_t count = halo_plane ? wx * wy : 2 * hy * wx + ny * 2 * r;
+    const int64_t sk = ((kr - hz) % nz + nz) % nz;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < count;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        int64_t xr, yr;
+        if (halo_plane) {
+            yr = q / wx;
+            xr = q - yr * wx;
+        } else if (q < 2 * hy * wx) {
+            int64_t row = q / wx;
+            xr = q - row * wx;
+            yr = row < hy ? row : ny + row;  // rows [0, hy) and [ny + hy, ny + 2 hy)
+        } else {
+            int64_t q2 = q - 2 * hy * wx;
+            int64_t row = q2 / (2 * r), c = q2 - row * (2 * r);
+            yr = hy + row;
+            xr = c < r ? c : nx + c;  // columns [0, r) and [nx + r, nx + 2 r)
+        }
+        const int64_t sx = ((xr - r) % nx + nx) % nx;
+        const int64_t sy = ((yr - hy) % ny + ny) % ny;
+        const int64_t dst = (g.off[0] - r + xr) + g.pad[0] * ((g.off[1] - hy + yr) +
+                                                               g.pad[1] * (g.off[2] - hz + kr));
+        base[dst] = base[g.idx(sx, sy, sk)];
+    }
+}
+
+cudaError_t launch_halo_fill(const Geom &g, int r, int esize, const Ptrs8 &f, int nfields,
+                             cudaStream_t s) {
+    if (r == 0) return cudaSuccess;
+    const int64_t hz = g.n[2] > 1 ? r : 0;
+    dim3 grid(1, (unsigned)(g.n[2] + 2 * hz), (unsigned)nfields);
+    const int64_t per_plane = (g.n[0] + 2 * r) * (g.n[1] + 2 * (g.n[1] > 1 ? r : 0));
+    grid.x = (unsigned)std::min<int64_t>(64, (per_plane + 255) / 256);
+    switch (esize) {
+    case 2: halo_fill_kernel<uint16_t><<<grid, 256, 0, s>>>(f, g, r); break;
+    case 4: halo_fill_kernel<uint32_t><<<grid, 256, 0, s>>>(f, g, r); break;
+    case 8: halo_fill_kernel<uint64_t><<<grid, 256, 0, s>>>(f, g, r); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace stn

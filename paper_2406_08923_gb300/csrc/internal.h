@@ -1,0 +1,61 @@
+// internal.h -- declarations shared between the C-ABI layer (api.cu) and the kernel files.
+#pragma once
+
+#include "common.cuh"
+
+namespace stn {
+
+struct Ptrs8 {
+    void *p[8];
+};
+
+// Periodic halo fill (Eq. 2, periodic beta) of `nfields` fields of element size `esize`.
+cudaError_t launch_halo_fill(const Geom &g, int r, int esize, const Ptrs8 &f, int nfields,
+                             cudaStream_t s);
+
+// XCORR (Eq. 3): `sweeps` sweeps in one launch.  dtype: 0 = int32 (mod 2^32), 1 = f64,
+// 2 = f32.  periodic: halo read by wrapping interior indices (any sweeps <= max);
+// otherwise a single sweep reading the caller's halo.  images: write periodic images of
+// the output into its halo.
+int xcorr_max_sweeps_per_launch();
+cudaError_t launch_xcorr(int dtype, int r, const void *in, void *out, const Geom &g,
+                         const void *coeffs, int sweeps, bool periodic, bool images,
+                         cudaStream_t s);
+
+// DIFFUSION (Eqs. 4-7): one folded 19-point step, 3D, radius 3, read through TMA.
+struct DiffCoef {
+    double g0;       // centre weight 1 + dt*alpha*sum_axes c0/h^2
+    double ga[3][3]; // [axis][a-1] weight of the pair at offset +-a along axis
+};
+cudaError_t launch_diffusion(int dtype, const CUtensorMap *map_in, void *out, const Geom &g,
+                             const DiffCoef &c, bool images, unsigned *err, cudaStream_t s,
+                             int variant);
+int diffusion_num_variants(int dtype);
+const char *diffusion_variant_name(int dtype, int variant);
+void diffusion_box(int dtype, int variant, int box[3]);  // TMA box (x, y, z) of a variant
+
+// MHD8 (Eqs. A1-A4 + RK3).  Constants in the compute type are built inside mhd.cu.
+struct MhdConst {
+    double d1[3][3], d2c[3], d2[3][3], dm[3][3];  // scaled stencil weights
+    double cs0sq, gamma, inv_cp, lnrho0, nu, eta, zeta, mu0, inv_mu0, cp_gm1;
+    double dt;
+};
+struct MhdMaps {
+    CUtensorMap m[8];
+};
+// mode 0: RK substep `sub` (0..2) writing f_out (+images), w and (for Kahan) c;
+// mode 1: right-hand side only, written densely to rhs (compute type).
+cudaError_t launch_mhd(int storage, int mode, int sub, const MhdMaps &maps, const Ptrs8 &fout,
+                       const Ptrs8 &w, const Ptrs8 &kc, const Ptrs8 &rhs, const Geom &g,
+                       const MhdConst &k, bool images, unsigned *err, cudaStream_t s,
+                       int variant);
+void mhd_box(int storage, int variant, int box[3]);
+int mhd_num_variants(int storage);
+const char *mhd_variant_name(int storage, int variant);
+
+// Norms: two-pass deterministic FP64 reduction.  partials holds nblocks * nfields * 4.
+int norms_blocks();
+cudaError_t launch_norms(int storage, const Ptrs8 &f, int nfields, const Geom &g, bool mass0,
+                         double *partials, double *out_dev, cudaStream_t s);
+
+}  // namespace stn

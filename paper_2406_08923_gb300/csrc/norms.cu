@@ -1,0 +1,109 @@
+// norms.cu -- per-field FP64 reductions over the interior: sum f, sum f^2, max |f| and, for
+// the MHD log-density, the mass sum exp(lnrho).  Used to judge accuracy and conservation
+// (Sec. 5.1 verification; Eq. A1 for the mass).
+//
+// Two passes with a fixed reduction tree, so results are bit-reproducible run to run:
+// pass 1: NB blocks stride over (row, segment) pieces of the interior (coalesced along x)
+// and write NB x nfields x 4 partials; pass 2: one warp per (field, quantity) reduces the
+// partials in a fixed order.
+#include "internal.h"
+
+namespace stn {
+
+constexpr int NORM_THREADS = 256;
+constexpr int NORM_BLOCKS = 2 * 152;
+constexpr int NORM_SEG = 4096;
+
+int norms_blocks() { return NORM_BLOCKS; }
+
+template <typename S> __device__ __forceinline__ double to_d(S v) { return (double)v; }
+template <> __device__ __forceinline__ double to_d<__nv_bfloat16>(__nv_bfloat16 v) {
+    return (double)__bfloat162float(v);
+}
+
+__device__ __forceinline__ void warp_reduce(double &s, double &s2, double &mx, double &ms) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        ms += __shfl_xor_sync(0xffffffffu, ms, o);
+    }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(NORM_THREADS)
+norms_pass1(Ptrs8 f, int nfields, Geom g, int mass0, double *partials) {
+    __shared__ double red[4][NORM_THREADS / 32];
+    const int64_t nx = g.n[0], rows = g.n[1] * g.n[2];
+    const int64_t segs = (nx + NORM_SEG - 1) / NORM_SEG;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int q = 0; q < nfields; ++q) {
+        const S *base = static_cast<const S *>(f.p[q]);
+        const bool do_mass = mass0 && q == 0;
+        double s = 0.0, s2 = 0.0, mx = 0.0, ms = 0.0;
+        for (int64_t piece = blockIdx.x; piece < rows * segs; piece += gridDim.x) {
+            const int64_t row = piece / segs, sg = piece - row * segs;
+            const int64_t y = row % g.n[1], z = row / g.n[1];
+            const S *p = base + g.idx(0, y, z);
+            const int64_t xe = min(nx, (sg + 1) * NORM_SEG);
+            for (int64_t x = sg * NORM_SEG + threadIdx.x; x < xe; x += NORM_THREADS) {
+                const double v = to_d(p[x]);
+                s += v;
+                s2 += v * v;
+                mx = fmax(mx, fabs(v));
+                if (do_mass) ms += exp(v);
+            }
+        }
+        warp_reduce(s, s2, mx, ms);
+        if (lane == 0) { red[0][warp] = s; red[1][warp] = s2; red[2][warp] = mx; red[3][warp] = ms; }
+        __syncthreads();
+        if (warp == 0) {
+            const bool in = lane < NORM_THREADS / 32;
+            s = in ? red[0][lane] : 0.0;
+            s2 = in ? red[1][lane] : 0.0;
+            mx = in ? red[2][lane] : 0.0;
+            ms = in ? red[3][lane] : 0.0;
+            warp_reduce(s, s2, mx, ms);
+            if (lane == 0) {
+                double *o = partials + ((int64_t)blockIdx.x * nfields + q) * 4;
+                o[0] = s; o[1] = s2; o[2] = mx; o[3] = ms;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void norms_pass2(const double *partials, int nblocks, int nfields, double *out) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;  // warp w -> (field, quantity)
+    if (w >= nfields * 4) return;
+    const int q = w / 4, c = w % 4;
+    double acc = 0.0;
+    for (int b = lane; b < nblocks; b += 32) {
+        const double v = partials[((int64_t)b * nfields + q) * 4 + c];
+        acc = c == 2 ? fmax(acc, v) : acc + v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double v = __shfl_xor_sync(0xffffffffu, acc, o);
+        acc = c == 2 ? fmax(acc, v) : acc + v;
+    }
+    if (lane == 0) out[q * 4 + c] = acc;
+}
+
+cudaError_t launch_norms(int storage, const Ptrs8 &f, int nfields, const Geom &g, bool mass0,
+                         double *partials, double *out_dev, cudaStream_t s) {
+    switch (storage) {
+    case 0: norms_pass1<int32_t><<<NORM_BLOCKS, NORM_THREADS, 0, s>>>(f, nfields, g, mass0, partials); break;
+    case 1: norms_pass1<double><<<NORM_BLOCKS, NORM_THREADS, 0, s>>>(f, nfields, g, mass0, partials); break;
+    case 2: norms_pass1<float><<<NORM_BLOCKS, NORM_THREADS, 0, s>>>(f, nfields, g, mass0, partials); break;
+    case 3: norms_pass1<__nv_bfloat16><<<NORM_BLOCKS, NORM_THREADS, 0, s>>>(f, nfields, g, mass0, partials); break;
+    default: return cudaErrorInvalidValue;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    norms_pass2<<<1, 32 * 4 * nfields, 0, s>>>(partials, NORM_BLOCKS, nfields, out_dev);
+    return cudaGetLastError();
+}
+
+}  // namespace stn

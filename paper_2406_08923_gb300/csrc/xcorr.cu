@@ -1,0 +1,165 @@
+// xcorr.cu -- 1D cross-correlation f'_i = sum_{j=-r..r} g_j f^_{i+j} (Sec. 3.1, Eq. 3).
+//
+// GB300 design: the input (2^20 int32 = 4 MiB in the benchmark) is L2-resident and a single
+// sweep moves ~8 MB, far less than what a launch costs in latency.  So one launch performs
+// several sweeps (temporal blocking): each CTA stages its chunk plus a halo of
+// sweeps * r cells per side in shared memory (coalesced 128-bit loads for the body,
+// periodic wrap for the halo), runs the sweeps in shared memory on a shrinking valid region,
+// and writes its chunk once, together with the periodic images of the array ends so the
+// output is a complete augmented array (Eq. 2).  Every output value is produced by the same
+// multiply-add sequence j = -r..r as a one-sweep-per-launch kernel would use, so the result
+// is bit-identical to sweeping once per launch.  int32 arithmetic is done in uint32
+// (modulo 2^32); floating point uses fused multiply-add in order j = -r..r.
+#include "internal.h"
+
+namespace stn {
+
+constexpr int XC_THREADS = 256;
+constexpr int XC_CHUNK = 2048;   // outputs per CTA
+constexpr int XC_MAX_SWEEPS = 16;
+
+int xcorr_max_sweeps_per_launch() { return XC_MAX_SWEEPS; }
+
+template <typename T> struct XAcc { using type = T; };
+template <> struct XAcc<int32_t> { using type = uint32_t; };
+
+template <typename T> struct Vec16;
+template <> struct Vec16<int32_t> { using type = int4; static constexpr int n = 4; };
+template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
+
+template <typename A> __device__ __forceinline__ A mac(A acc, A g, A f) { return fma(g, f, acc); }
+template <> __device__ __forceinline__ uint32_t mac<uint32_t>(uint32_t acc, uint32_t g, uint32_t f) {
+    return acc + g * f;
+}
+
+template <typename T> struct XCoef { T g[9]; };
+
+template <typename T, int R>
+__global__ void __launch_bounds__(XC_THREADS)
+xcorr_kernel(const T *__restrict__ in, T *__restrict__ out, Geom geo, XCoef<T> cf, int sweeps,
+             int periodic, int images) {
+    using A = typename XAcc<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int H = sweeps * R;
+    const int W = XC_CHUNK + 2 * H;
+    A *buf0 = reinterpret_cast<A *>(smem_raw);
+    A *buf1 = buf0 + W;
+    const int64_t n = geo.n[0];
+    const int64_t c0 = (int64_t)blockIdx.x * XC_CHUNK;
+    const T *inx = in + geo.off[0];  // interior element 0
+    T *outx = out + geo.off[0];
+
+    // stage [c0 - H, c0 + CHUNK + H) into buf0[0 .. W)
+    constexpr int V = Vec16<T>::n;
+    using VT = typename Vec16<T>::type;
+    const bool full = c0 + XC_CHUNK <= n;
+    if (full) {
+        const VT *src = reinterpret_cast<const VT *>(inx + c0);
+        for (int v = threadIdx.x; v < XC_CHUNK / V; v += XC_THREADS) {
+            VT x = src[v];
+            const T *e = reinterpret_cast<const T *>(&x);
+#pragma unroll
+            for (int u = 0; u < V; ++u) buf0[H + v * V + u] = (A)e[u];
+        }
+    }
+    for (int e = threadIdx.x; e < W; e += XC_THREADS) {
+        const bool body = e >= H && e < H + XC_CHUNK;
+        if (full && body) continue;
+        int64_t gi = c0 - H + e;
+        T v;
+        if (periodic) {
+            gi %= n;
+            if (gi < 0) gi += n;
+            v = inx[gi];
+        } else {
+            v = (gi >= -R && gi < n + R) ? inx[gi] : T(0);
+        }
+        buf0[e] = (A)v;
+    }
+    __syncthreads();
+
+    A *src = buf0, *dst = buf1;
+    for (int s = 1; s <= sweeps; ++s) {
+        const int lo = s * R, hi = W - s * R;
+        for (int p = lo + threadIdx.x; p < hi; p += XC_THREADS) {
+            A acc = A(0);
+#pragma unroll
+            for (int j = -R; j <= R; ++j) acc = mac<A>(acc, (A)cf.g[j + R], src[p + j]);
+            dst[p] = acc;
+        }
+        __syncthreads();
+        A *t = src;
+        src = dst;
+        dst = t;
+    }
+
+    // write the chunk (+ periodic images of the array ends)
+    const A *res = src + H;
+    if (full) {
+        VT *d = reinterpret_cast<VT *>(outx + c0);
+        for (int v = threadIdx.x; v < XC_CHUNK / V; v += XC_THREADS) {
+            VT x;
+            T *e = reinterpret_cast<T *>(&x);
+#pragma unroll
+            for (int u = 0; u < V; ++u) e[u] = (T)res[v * V + u];
+            d[v] = x;
+        }
+    } else {
+        for (int p = threadIdx.x; p < XC_CHUNK && c0 + p < n; p += XC_THREADS)
+            outx[c0 + p] = (T)res[p];
+    }
+    if (images) {
+        for (int p = threadIdx.x; p < XC_CHUNK; p += XC_THREADS) {
+            const int64_t gi = c0 + p;
+            if (gi >= n) break;
+            if (gi < R) outx[gi + n] = (T)res[p];
+            if (gi >= n - R) outx[gi - n] = (T)res[p];
+        }
+    }
+}
+
+template <typename T, int R>
+static cudaError_t run(const void *in, void *out, const Geom &g, const void *coeffs, int sweeps,
+                       bool periodic, bool images, cudaStream_t s) {
+    using A = typename XAcc<T>::type;
+    XCoef<T> cf{};
+    for (int j = 0; j < 2 * R + 1; ++j) cf.g[j] = static_cast<const T *>(coeffs)[j];
+    const size_t smem = 2 * sizeof(A) * (XC_CHUNK + 2 * sweeps * R);
+    const unsigned blocks = (unsigned)((g.n[0] + XC_CHUNK - 1) / XC_CHUNK);
+    auto k = xcorr_kernel<T, R>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k<<<blocks, XC_THREADS, smem, s>>>(static_cast<const T *>(in), static_cast<T *>(out), g, cf,
+                                       sweeps, periodic ? 1 : 0, images ? 1 : 0);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t run_r(int r, const void *in, void *out, const Geom &g, const void *coeffs,
+                         int sweeps, bool periodic, bool images, cudaStream_t s) {
+    switch (r) {
+    case 0: return run<T, 0>(in, out, g, coeffs, sweeps, periodic, images, s);
+    case 1: return run<T, 1>(in, out, g, coeffs, sweeps, periodic, images, s);
+    case 2: return run<T, 2>(in, out, g, coeffs, sweeps, periodic, images, s);
+    case 3: return run<T, 3>(in, out, g, coeffs, sweeps, periodic, images, s);
+    case 4: return run<T, 4>(in, out, g, coeffs, sweeps, periodic, images, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_xcorr(int dtype, int r, const void *in, void *out, const Geom &g,
+                         const void *coeffs, int sweeps, bool periodic, bool images,
+                         cudaStream_t s) {
+    if (sweeps < 1 || sweeps > XC_MAX_SWEEPS) return cudaErrorInvalidValue;
+    switch (dtype) {
+    case 0: return run_r<int32_t>(r, in, out, g, coeffs, sweeps, periodic, images, s);
+    case 1: return run_r<double>(r, in, out, g, coeffs, sweeps, periodic, images, s);
+    case 2: return run_r<float>(r, in, out, g, coeffs, sweeps, periodic, images, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace stn

@@ -1,0 +1,112 @@
+"""Host-side checks of the C ABI: the library loads without a GPU, exports every symbol that
+include/stencil.h declares, and rejects invalid arguments before touching the device."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2406_08923_gb300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "stencil.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(_lib.LIB_PATH):
+        from paper_2406_08923_gb300 import build
+        build.build()
+    return _lib.load()
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(stencil_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert len(names) >= 14
+    out = subprocess.run(["nm", "-D", "--defined-only", _lib.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (stencil_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        getattr(lib, n)
+    assert set(_lib.EXPORTED) == set(names)
+
+
+def test_abi_version_and_strerror(lib):
+    assert lib.stencil_abi_version() == 1
+    for s in range(6):
+        assert lib.stencil_strerror(s).decode().startswith("STENCIL_")
+    assert b"unknown" in lib.stencil_strerror(99)
+
+
+def _create(lib, ndim=3, dims=(16, 16, 16), radius=3, coeffs=None, nfields=1, bc=0, kind=1, storage=1,
+            compute=1, params=True):
+    d = (ctypes.c_int64 * 3)(*dims)
+    keep = None
+    cp, nc = None, 0
+    if coeffs is not None:
+        keep = np.ascontiguousarray(coeffs, dtype=np.int32 if storage == 0 else np.float64)
+        cp, nc = keep.ctypes.data_as(ctypes.c_void_p), keep.size
+    p = _lib.heat_params(16) if params else None
+    h = ctypes.c_void_p()
+    st = lib.stencil_create(ndim, d, radius, cp, nc, nfields, bc, kind, storage, compute,
+                            ctypes.byref(p) if p is not None else None, ctypes.byref(h))
+    return st, h, lib.stencil_last_error_detail(None).decode()
+
+
+@pytest.mark.parametrize("kw,expect", [
+    (dict(ndim=0), _lib.STENCIL_EINVAL),
+    (dict(ndim=4), _lib.STENCIL_EINVAL),
+    (dict(dims=(0, 16, 16)), _lib.STENCIL_EINVAL),
+    (dict(radius=-1), _lib.STENCIL_EINVAL),
+    (dict(radius=2), _lib.STENCIL_EINVAL),                      # diffusion is radius 3
+    (dict(dims=(6, 16, 16)), _lib.STENCIL_EINVAL),              # periodic extent < 2r+1
+    (dict(params=False), _lib.STENCIL_EINVAL),
+    (dict(nfields=2), _lib.STENCIL_EINVAL),
+    (dict(kind=7), _lib.STENCIL_EINVAL),
+    (dict(storage=9), _lib.STENCIL_EINVAL),
+    (dict(storage=3, compute=2), _lib.STENCIL_EUNSUPPORTED),    # BF16 diffusion
+    (dict(ndim=2), _lib.STENCIL_EUNSUPPORTED),
+    (dict(kind=2, nfields=8, bc=1), _lib.STENCIL_EUNSUPPORTED),  # MHD8 needs periodic
+    (dict(kind=2, nfields=8, storage=0, compute=0), _lib.STENCIL_EUNSUPPORTED),
+    (dict(kind=0, ndim=1, dims=(64, 1, 1), radius=3, nfields=1, coeffs=[1] * 6, storage=0, compute=0), _lib.STENCIL_EINVAL),
+    (dict(kind=0, ndim=1, dims=(64, 1, 1), radius=5, nfields=1, coeffs=[1] * 11, storage=0, compute=0), _lib.STENCIL_EUNSUPPORTED),
+    (dict(kind=0, ndim=3, radius=1, coeffs=[1, 2, 3], storage=0, compute=0), _lib.STENCIL_EUNSUPPORTED),
+    (dict(kind=0, ndim=1, dims=(64, 1, 1), radius=1, coeffs=[1, 2, 3], storage=1, compute=2), _lib.STENCIL_EUNSUPPORTED),
+])
+def test_create_rejects_invalid_arguments(lib, kw, expect):
+    st, h, detail = _create(lib, **kw)
+    assert st == expect, (st, detail)
+    assert not h.value
+    assert detail
+
+
+def test_null_plan_calls_are_rejected(lib):
+    assert lib.stencil_layout(None, None, None, None, None) == _lib.STENCIL_EINVAL
+    assert lib.stencil_step(None, None, None, 1, None) == _lib.STENCIL_EINVAL
+    assert lib.stencil_sync(None, None) == _lib.STENCIL_EINVAL
+    assert lib.stencil_set_variant(None, 0) == _lib.STENCIL_EINVAL
+    lib.stencil_destroy(None)
+
+
+def test_create_null_out_and_dims(lib):
+    p = _lib.heat_params(16)
+    d = (ctypes.c_int64 * 3)(16, 16, 16)
+    assert lib.stencil_create(3, d, 3, None, 0, 1, 0, 1, 1, 1, ctypes.byref(p), None) == _lib.STENCIL_EINVAL
+    h = ctypes.c_void_p()
+    assert lib.stencil_create(3, None, 3, None, 0, 1, 0, 1, 1, 1, ctypes.byref(p), ctypes.byref(h)) == _lib.STENCIL_EINVAL
+
+
+def test_python_binding_raises_with_detail(lib):
+    with pytest.raises(_lib.StencilError) as e:
+        _lib.stencil_create(3, (5, 16, 16), 3, None, 1, 0, 1, 1, 1, _lib.heat_params(16))
+    assert e.value.status == _lib.STENCIL_EINVAL
+    assert "2*radius+1" in str(e.value)
