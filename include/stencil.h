@@ -180,6 +180,42 @@ stencil_status stencil_mhd_rhs(stencil_t plan, void *const *fields, void *const 
 stencil_status stencil_field_norms(stencil_t plan, void *const *fields, double *out,
                                    void *stream);
 
+/*
+ * stencil_field_norms_noalloc -- the reductions of stencil_field_norms, for callers that
+ * cannot allocate device memory.  The paper has no counterpart: this is an addition of the
+ * library.
+ *
+ * Which callers: a serving loop that has committed its whole HBM budget to resident fields
+ * and must not allocate while requests are in flight (an allocation can fail, or
+ * synchronise the device), and applications whose device memory is owned by another
+ * allocator.  The call needs no plan (creating a plan allocates) and calls no cudaMalloc,
+ * cudaFree or allocating library routine.  Its scratch, the pass-1 partials of the two-pass
+ * FP64 reduction, is a fixed file-scope device array of 77 824 bytes.  Every GPU that loads
+ * the library holds that array until the process exits.
+ *
+ *   fields        nfields device pointers, each a padded field laid out as stencil_layout
+ *                 describes, element type `storage` (I32, F64, F32 or BF16)
+ *   nfields       1..8; a larger value returns STENCIL_EINVAL (the array holds 8 fields)
+ *   dims          interior extents (nx, ny, nz), 1 on unused axes
+ *   padded        padded extents, origin: interior origin -- as stencil_layout reports them
+ *   mass_volume   if > 0, out_dev[3*nfields] = sum exp(field 0) * mass_volume (the MHD mass)
+ *   out_dev       DEVICE array of 3*nfields doubles (+1 when mass_volume > 0), written in
+ *                 stream order as {sum f, sum f^2, max |f|} per field
+ *   stream        cudaStream_t as void*; the call returns without synchronising
+ *
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current.  Make that first call before any stream capture.  All calls
+ * share the one array, and each call overwrites every slot it later reads, so nothing
+ * carries over from the previous call.  Calls whose work overlaps on the GPU (different
+ * streams, or different host threads) race on the array and give wrong results: serialise
+ * them.  Errors: STENCIL_EINVAL for invalid arguments (detail via
+ * stencil_last_error_detail(NULL)), STENCIL_ECUDA if a launch fails.
+ */
+stencil_status stencil_field_norms_noalloc(void *const *fields, int nfields, stencil_dtype storage,
+                                           const int64_t dims[3], const int64_t padded[3],
+                                           const int64_t origin[3], double mass_volume,
+                                           double *out_dev, void *stream);
+
 /* stencil_sync -- synchronise `stream` and report (then clear) any expired device wait
  * recorded by this plan's kernels since the last check. */
 stencil_status stencil_sync(stencil_t plan, void *stream);
@@ -202,8 +238,8 @@ stencil_status stencil_autotune(stencil_t plan, void *const *fields_in, void *co
 /* Human-readable name of a status code (static string). */
 const char *stencil_strerror(stencil_status status);
 
-/* Detail of the last failure on `plan` (or of the last failed stencil_create when plan is
- * NULL, per host thread).  Valid until the next call on the plan. */
+/* Detail of the last failure on `plan` (or, when plan is NULL, of the last failed
+ * stencil_create or plan-free call on this host thread).  Valid until the next call. */
 const char *stencil_last_error_detail(stencil_t plan);
 
 /* ABI version of the loaded library (STENCIL_ABI_VERSION at build time). */

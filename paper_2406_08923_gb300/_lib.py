@@ -28,7 +28,7 @@ EXPORTED = (
     "stencil_create", "stencil_destroy", "stencil_layout", "stencil_step", "stencil_halo_fill",
     "stencil_mhd_rhs", "stencil_field_norms", "stencil_sync", "stencil_strerror",
     "stencil_last_error_detail", "stencil_abi_version", "stencil_get_variant",
-    "stencil_set_variant", "stencil_autotune",
+    "stencil_set_variant", "stencil_autotune", "stencil_field_norms_noalloc",
 )
 
 
@@ -77,6 +77,8 @@ def load():
             "stencil_get_variant": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(ctypes.c_char_p)]),
             "stencil_set_variant": (I, [P, I]),
             "stencil_autotune": (I, [P, PP, PP, I, I, P]),
+            "stencil_field_norms_noalloc": (I, [PP, I, I, ctypes.POINTER(I64), ctypes.POINTER(I64),
+                                                ctypes.POINTER(I64), D, P, P]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(lib, name)
@@ -179,6 +181,17 @@ def stencil_autotune(h, fields_in, fields_out, nsteps=1, reps=3, stream=None):
     pi, ki = _ptrs(fields_in)
     po, ko = _ptrs(fields_out)
     _check(load().stencil_autotune(h, pi, po, nsteps, reps, _stream(stream)), "stencil_autotune", h)
+
+
+def stencil_field_norms_noalloc(fields, storage, dims, padded, origin, mass_volume, out_dev, stream=None):
+    """Allocation-free norms: results written to the device tensor out_dev (float64)."""
+    p, k = _ptrs(fields)
+    d = (ctypes.c_int64 * 3)(*dims)
+    pd = (ctypes.c_int64 * 3)(*padded)
+    o = (ctypes.c_int64 * 3)(*origin)
+    st = load().stencil_field_norms_noalloc(p, len(fields), storage, d, pd, o, float(mass_volume),
+                                            ctypes.c_void_p(int(out_dev.data_ptr())), _stream(stream))
+    _check(st, "stencil_field_norms_noalloc", None)
 
 
 def stencil_destroy(h):

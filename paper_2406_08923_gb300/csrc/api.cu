@@ -639,4 +639,33 @@ stencil_status stencil_autotune(stencil_t p, void *const *fin, void *const *fout
     return STENCIL_OK;
 }
 
+stencil_status stencil_field_norms_noalloc(void *const *fields, int nfields, stencil_dtype storage,
+                                           const int64_t dims[3], const int64_t padded[3],
+                                           const int64_t origin[3], double mass_volume, double *out_dev,
+                                           void *stream) {
+    g_create_detail.clear();
+    const int maxf = norms_static_max_fields();
+    if (nfields < 1 || nfields > maxf)
+        return fail(nullptr, STENCIL_EINVAL,
+                    "nfields " + std::to_string(nfields) + " out of range 1.." + std::to_string(maxf) +
+                        " (the allocation-free scratch holds at most " + std::to_string(maxf) + " fields)");
+    if ((int)storage < 0 || (int)storage > 3) return fail(nullptr, STENCIL_EINVAL, "unknown dtype");
+    if (!fields || !dims || !padded || !origin || !out_dev)
+        return fail(nullptr, STENCIL_EINVAL, "a pointer argument is NULL");
+    for (int q = 0; q < nfields; ++q)
+        if (!fields[q]) return fail(nullptr, STENCIL_EINVAL, "fields[" + std::to_string(q) + "] is NULL");
+    Geom g{};
+    for (int a = 0; a < 3; ++a) {
+        if (dims[a] < 1 || origin[a] < 0 || padded[a] < origin[a] + dims[a])
+            return fail(nullptr, STENCIL_EINVAL, "inconsistent dims / padded / origin on axis " + std::to_string(a));
+        g.n[a] = dims[a];
+        g.off[a] = origin[a];
+        g.pad[a] = padded[a];
+    }
+    cudaError_t e = launch_norms_noalloc(storage_code(storage), ptrs(fields, nfields), nfields, g, mass_volume,
+                                         out_dev, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "allocation-free norms launch");
+    return STENCIL_OK;
+}
+
 }  // extern "C"

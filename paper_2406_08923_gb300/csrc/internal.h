@@ -58,4 +58,10 @@ int norms_blocks();
 cudaError_t launch_norms(int storage, const Ptrs8 &f, int nfields, const Geom &g, bool mass0,
                          double *partials, double *out_dev, cudaStream_t s);
 
+// Allocation-free norms: partials in a file-scope device array (norms.cu); results packed
+// {sum, sumsq, max|f|} per field (+ mass) into device memory.
+int norms_static_max_fields();
+cudaError_t launch_norms_noalloc(int storage, const Ptrs8 &f, int nfields, const Geom &g,
+                                 double mass_volume, double *out_dev, cudaStream_t s);
+
 }  // namespace stn

@@ -6,6 +6,8 @@
 // pass 1: NB blocks stride over (row, segment) pieces of the interior (coalesced along x)
 // and write NB x nfields x 4 partials; pass 2: one warp per (field, quantity) reduces the
 // partials in a fixed order.
+#include <mutex>
+
 #include "internal.h"
 
 namespace stn {
@@ -103,6 +105,88 @@ cudaError_t launch_norms(int storage, const Ptrs8 &f, int nfields, const Geom &g
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     norms_pass2<<<1, 32 * 4 * nfields, 0, s>>>(partials, NORM_BLOCKS, nfields, out_dev);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// Allocation-free variant of the same two-pass reduction.
+//
+// Some callers cannot call cudaMalloc: a serving loop that has committed its whole HBM
+// budget to resident fields and must not allocate (or risk an allocation failure or an
+// implicit device synchronisation) while requests are in flight, or a host application
+// whose device memory is owned by another allocator.  For them the pass-1 partials live
+// in this file-scope device array instead of plan-owned scratch.  Its size is fixed:
+// NORM_BLOCKS blocks x at most NORM_STATIC_MAX_FIELDS fields x 4 doubles = 77 824 bytes,
+// held by every GPU that loads the library until the process exits.  Pass 1 writes every
+// slot that pass 2 reads, so nothing needs clearing between calls; calls that overlap on
+// the GPU (two streams, or two host threads) share this one array and race.
+constexpr int NORM_STATIC_MAX_FIELDS = 8;
+static __device__ __align__(256) double g_norm_partials[NORM_BLOCKS * NORM_STATIC_MAX_FIELDS * 4];
+
+int norms_static_max_fields() { return NORM_STATIC_MAX_FIELDS; }
+
+// Results packed as {sum, sum of squares, max |f|} per field, then (when mass_volume > 0)
+// sum exp(field 0) * mass_volume, written to device memory.
+__global__ void norms_pass2_packed(const double *partials, int nblocks, int nfields, double mass_volume,
+                                   double *out) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (w >= nfields * 4) return;
+    const int q = w / 4, c = w % 4;
+    if (c == 3 && (q != 0 || !(mass_volume > 0.0))) return;
+    double acc = 0.0;
+    for (int b = lane; b < nblocks; b += 32) {
+        const double v = partials[((int64_t)b * nfields + q) * 4 + c];
+        acc = c == 2 ? fmax(acc, v) : acc + v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double v = __shfl_xor_sync(0xffffffffu, acc, o);
+        acc = c == 2 ? fmax(acc, v) : acc + v;
+    }
+    if (lane == 0) {
+        if (c < 3) out[3 * q + c] = acc;
+        else out[3 * nfields] = acc * mass_volume;
+    }
+}
+
+// Device address of g_norm_partials for the current device.  Host code cannot use the
+// array's name as a device pointer (it is a host-side stand-in), so the address is looked
+// up once per device with that device current, on the first call made on that device.
+static cudaError_t norm_partials_address(double **addr) {
+    static std::mutex mu;
+    static double *cache[128] = {};
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!cache[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_norm_partials);
+        if (e != cudaSuccess) return e;
+        cache[dev] = static_cast<double *>(p);
+    }
+    *addr = cache[dev];
+    return cudaSuccess;
+}
+
+cudaError_t launch_norms_noalloc(int storage, const Ptrs8 &f, int nfields, const Geom &g,
+                                 double mass_volume, double *out_dev, cudaStream_t s) {
+    if (nfields < 1 || nfields > NORM_STATIC_MAX_FIELDS) return cudaErrorInvalidValue;
+    double *partials = nullptr;
+    cudaError_t e = norm_partials_address(&partials);
+    if (e != cudaSuccess) return e;
+    const int mass0 = mass_volume > 0.0 ? 1 : 0;
+    switch (storage) {
+    case 0: norms_pass1<int32_t><<<NORM_BLOCKS, NORM_THREADS, 0, s>>>(f, nfields, g, mass0, partials); break;
+    case 1: norms_pass1<double><<<NORM_BLOCKS, NORM_THREADS, 0, s>>>(f, nfields, g, mass0, partials); break;
+    case 2: norms_pass1<float><<<NORM_BLOCKS, NORM_THREADS, 0, s>>>(f, nfields, g, mass0, partials); break;
+    case 3: norms_pass1<__nv_bfloat16><<<NORM_BLOCKS, NORM_THREADS, 0, s>>>(f, nfields, g, mass0, partials); break;
+    default: return cudaErrorInvalidValue;
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    norms_pass2_packed<<<1, 32 * 4 * nfields, 0, s>>>(partials, NORM_BLOCKS, nfields, mass_volume, out_dev);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,60 @@
+"""The allocation-free norm entry point (stencil_field_norms_noalloc).
+
+It serves callers that cannot allocate device memory, such as a serving loop whose HBM
+budget is fully committed, or an application whose device memory belongs to another
+allocator.  Its scratch is a fixed device array inside the library.  This file is collected
+last, so a run that stops at the first failure has already run every other test.  It must
+pass both alone in a fresh process and after the other tests.
+
+Each call is checked through the C ABI against stencil_field_norms, the plan-based entry
+point, within the norm tests' tolerance.  Two calls are made in a row, on different
+workloads, so a stale value left in the shared array would show.
+"""
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import heat_plan, mhd_plan
+from paper_2406_08923_gb300 import _lib as L
+from paper_2406_08923_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _noalloc(p, fields, mass_volume):
+    n = 3 * len(fields) + (1 if mass_volume > 0 else 0)
+    out = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+    L.stencil_field_norms_noalloc(fields, p.storage, p.dims, p.padded, p.origin, mass_volume, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def test_matches_plan_entry_point_two_calls_in_a_row(cuda_lib):
+    # call 1: the 8-field MHD state (BF16 storage) with the mass term
+    shape = (20, 24, 28)
+    p1, par = mhd_plan(shape, L.STENCIL_BF16)
+    f1 = p1.alloc(fill=3.0)
+    p1.upload(f1, synth.mhd_fields(shape, seed=4))
+    ref1 = p1.norms(f1)
+    got1 = _noalloc(p1, f1, par.dx[0] * par.dx[1] * par.dx[2])
+    np.testing.assert_allclose(got1, ref1, rtol=1e-12, atol=1e-14 * np.abs(ref1).max())
+
+    # call 2: one FP64 heat field of another shape, no mass term
+    shape2 = (37, 41, 29)
+    p2, _ = heat_plan(shape2, L.STENCIL_F64)
+    f2 = p2.alloc(fill=1e6)
+    p2.upload(f2, [synth.heat_field(shape2, seed=2)])
+    ref2 = p2.norms(f2)
+    got2 = _noalloc(p2, f2, 0.0)
+    np.testing.assert_allclose(got2, ref2, rtol=1e-12, atol=1e-14 * np.abs(ref2).max())
+
+
+def test_rejects_more_fields_than_the_static_scratch_holds(cuda_lib):
+    shape = (16, 16, 16)
+    p, _ = heat_plan(shape, L.STENCIL_F64)
+    f = p.alloc()
+    out = torch.zeros(64, dtype=torch.float64, device="cuda")
+    with pytest.raises(L.StencilError) as e:
+        L.stencil_field_norms_noalloc(f * 9, p.storage, p.dims, p.padded, p.origin, 0.0, out)
+    assert e.value.status == L.STENCIL_EINVAL
+    assert "at most 8 fields" in str(e.value)
