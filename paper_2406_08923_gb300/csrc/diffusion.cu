@@ -4,56 +4,132 @@
 // (Eqs. 5 and 7): f' = g0 f + sum_axes sum_{a=1..3} g_{axis,a} (f(+a) + f(-a)).
 //
 // GB300 design (2.5D z-streaming):
-//   * A CTA owns a TX x (BY*RY) tile of the xy-plane and marches along z over a chunk of ZC
-//     planes.  Each padded input plane tile (TX + 2 HX) x (BY*RY + 6) is brought into a
-//     ring of NSLOT shared-memory slots by one TMA load (cp.async.bulk.tensor.3d) signalled
-//     on a per-slot mbarrier; loads run NSLOT - 3 planes ahead of the compute.
-//   * Each thread keeps the z-column of its RY cells for planes z-3..z+3 in a register queue,
-//     so z-neighbours cost no shared-memory traffic; x- and y-neighbours are read from the
-//     centre plane in shared memory (conflict-free: a warp reads 32 consecutive words).
-//   * Outputs are stored once, coalesced, and cells within r of a face also store their
-//     periodic images (Eq. 2), so the next step needs no separate halo pass.
+//   * A CTA owns a TX x TY tile of the xy-plane (TX = 32 VX, TY = BY RY) and marches along z
+//     over a chunk of planes (chunk length chosen by the host from the kernel's occupancy so
+//     the grid fills whole waves of the 152 SMs).  Each padded input plane tile
+//     (TX + 8) x (TY + 6) arrives by one TMA load (cp.async.bulk.tensor.3d) in a ring of
+//     NSLOT shared-memory slots, completion on one mbarrier per slot; loads run NSLOT - 3
+//     planes ahead of the compute.
+//   * A thread owns VX = 2 VP consecutive x cells in RY rows and computes them as VP pairs:
+//     FP32 pairs use Blackwell's packed FP32x2 FMA/ADD (one instruction per two cells).
+//     Neighbours at even x offsets and all y/z neighbours are naturally aligned pairs; the
+//     odd x offsets take two scalar adds.  Shared memory is read with 16-byte vector loads.
+//   * Each iteration computes ZB consecutive z planes (register blocking in z).  The
+//     z-columns (planes z-3..z+ZB+2) live in a register queue that shifts by ZB once per
+//     iteration, so z-neighbours cost no shared-memory traffic and the per-iteration work
+//     (mbarrier waits, the block barrier, refills) is amortised over VX x RY x ZB cells.
+//   * Outputs are stored once as vectors.  Threads whose cells lie within r of a face also
+//     store the periodic images (Eq. 2) on a slow path, so no separate halo pass is needed.
 //   * Waits are bounded (globaltimer); on expiry the CTA records ERR_TIMEOUT, drains its
 //     in-flight TMA loads (again bounded) and returns.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace stn {
+
+// Ring slot and mbarrier phase parity of plane j for a power-of-two ring depth N.
+template <int N> __device__ __forceinline__ int slot_of(int j) { return (int)((unsigned)j & (N - 1)); }
+template <int N> __device__ __forceinline__ uint32_t parity_of(int j) { return ((unsigned)j / (unsigned)N) & 1u; }
+
+// Pair arithmetic: PK selects Blackwell's packed FP32x2 instructions for float; otherwise
+// the two lanes are computed with scalar instructions.
+template <typename T, bool PK> struct PairOps;
+template <> struct PairOps<float, true> {
+    using P = float2;
+    static __device__ __forceinline__ P add(P a, P b) { return __fadd2_rn(a, b); }
+    static __device__ __forceinline__ P mul(P a, P b) { return __fmul2_rn(a, b); }
+    static __device__ __forceinline__ P fma2(P a, P b, P c) { return __ffma2_rn(a, b, c); }
+    static __device__ __forceinline__ P make(float a, float b) { return make_float2(a, b); }
+};
+template <> struct PairOps<float, false> {
+    using P = float2;
+    static __device__ __forceinline__ P add(P a, P b) { return make_float2(a.x + b.x, a.y + b.y); }
+    static __device__ __forceinline__ P mul(P a, P b) { return make_float2(a.x * b.x, a.y * b.y); }
+    static __device__ __forceinline__ P fma2(P a, P b, P c) {
+        return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
+    }
+    static __device__ __forceinline__ P make(float a, float b) { return make_float2(a, b); }
+};
+template <bool PK> struct PairOps<double, PK> {
+    using P = double2;
+    static __device__ __forceinline__ P add(P a, P b) { return make_double2(a.x + b.x, a.y + b.y); }
+    static __device__ __forceinline__ P mul(P a, P b) { return make_double2(a.x * b.x, a.y * b.y); }
+    static __device__ __forceinline__ P fma2(P a, P b, P c) {
+        return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+    }
+    static __device__ __forceinline__ P make(double a, double b) { return make_double2(a, b); }
+};
 
 template <typename T> struct DC {
     T g0;
     T ga[3][3];
 };
 
-template <typename T, int TX, int BY, int RY, int NSLOT, int ZC>
+template <typename T, int VP, int BY, int RY, int ZB, int NSLOT>
 struct DiffCfg {
-    static constexpr int HX = 16 / sizeof(T) >= 4 ? 16 / (int)sizeof(T) : 4;  // 4 for f32/f64
+    static constexpr int VX = 2 * VP;
+    static constexpr int HX = 4;  // x halo kept in shared memory: 16 B aligned TMA box start
+    static constexpr int TX = 32 * VX;
     static constexpr int TY = BY * RY;
     static constexpr int TXP = TX + 2 * HX;
     static constexpr int ROWS = TY + 2 * R6;
     static constexpr int SLOT_ELEMS = ((TXP * ROWS * (int)sizeof(T) + 127) / 128) * 128 / (int)sizeof(T);
     static constexpr uint32_t BOX_BYTES = TXP * ROWS * sizeof(T);
     static constexpr size_t SMEM = (size_t)NSLOT * SLOT_ELEMS * sizeof(T) + 128;
+    // elements per shared-memory vector load: 16 bytes, or the whole VX group if smaller
+    static constexpr int LV = (VX * (int)sizeof(T) >= 16) ? 16 / (int)sizeof(T) : VX;
     static_assert((TXP * sizeof(T)) % 16 == 0, "TMA box inner extent must be a multiple of 16 B");
-    static_assert(NSLOT >= 7, "ring must hold planes z-3..z+3");
+    static_assert(TXP <= 256 && ROWS <= 256, "TMA box extents are limited to 256");
+    static_assert(NSLOT >= ZB + 4, "ring must hold the ZB centre planes, the ZB leading planes and a refill");
+    static_assert((NSLOT & (NSLOT - 1)) == 0, "ring depth is a power of two (slot = j & (NSLOT-1))");
+    static_assert(VX % LV == 0 && HX % LV == 0 && TXP % LV == 0, "vector loads must stay aligned");
 };
 
-template <typename T, int TX, int BY, int RY, int NSLOT, int ZC>
-__global__ void __launch_bounds__(TX *BY)
-diffusion_kernel(const __grid_constant__ CUtensorMap map_in, T *__restrict__ out, Geom g,
-                 DC<T> c, int images, unsigned *err) {
-    using Cfg = DiffCfg<T, TX, BY, RY, NSLOT, ZC>;
+// Load `n` consecutive elements (n a multiple of LV) at an LV-aligned shared address.
+template <typename T, int LV, int N>
+__device__ __forceinline__ void ld_vec(const T *p, T (&dst)[N]) {
+    static_assert(N % LV == 0, "");
+#pragma unroll
+    for (int i = 0; i < N / LV; ++i) {
+        if constexpr (LV * sizeof(T) == 16) {
+            const uint4 v = *reinterpret_cast<const uint4 *>(p + i * LV);
+            const T *e = reinterpret_cast<const T *>(&v);
+#pragma unroll
+            for (int u = 0; u < LV; ++u) dst[i * LV + u] = e[u];
+        } else if constexpr (LV * sizeof(T) == 8) {
+            const uint2 v = *reinterpret_cast<const uint2 *>(p + i * LV);
+            const T *e = reinterpret_cast<const T *>(&v);
+#pragma unroll
+            for (int u = 0; u < LV; ++u) dst[i * LV + u] = e[u];
+        } else {
+            dst[i] = p[i];
+        }
+    }
+}
+
+template <typename T, int VP, int BY, int RY, int ZB, int NSLOT, bool PK>
+__global__ void __launch_bounds__(32 * BY)
+diffusion_kernel(const __grid_constant__ CUtensorMap map_in, T *__restrict__ out, Geom g, DC<T> c,
+                 int zc, int images, unsigned *err) {
+    using Cfg = DiffCfg<T, VP, BY, RY, ZB, NSLOT>;
+    using O = PairOps<T, PK>;
+    using P = typename O::P;
+    constexpr int VX = Cfg::VX, LV = Cfg::LV;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // TMA destinations are kept 128-byte aligned (dynamic smem has 128 spare bytes)
     T *ring = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     __shared__ __align__(8) uint64_t full[NSLOT];
 
-    const int tx = threadIdx.x % TX, by = threadIdx.x / TX;
-    const int64_t x0 = (int64_t)blockIdx.x * TX, y0 = (int64_t)blockIdx.y * Cfg::TY;
-    const int64_t zc0 = (int64_t)blockIdx.z * ZC;
-    const int64_t zend = min((int64_t)g.n[2], zc0 + ZC);
-    const int nplanes = (int)(zend - zc0) + 2 * R6;  // planes zc0-3 .. zend+2
-    const int64_t x = x0 + tx;
-    const bool active_x = x < g.n[0];
+    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+    const int x0 = blockIdx.x * Cfg::TX, y0 = blockIdx.y * Cfg::TY;
+    const int zc0 = blockIdx.z * zc;
+    const int nx = (int)g.n[0], ny = (int)g.n[1], nz = (int)g.n[2];
+    const int zend = min(nz, zc0 + zc);
+    const int count = zend - zc0;
+    const int nplanes = count + 2 * R6;  // planes zc0-3 .. zend+2
+    const int x = x0 + lane * VX;       // first of this thread's VX cells
+    const int yb = y0 + wy * RY;        // first of its RY rows
 
     if (threadIdx.x == 0) {
         tma_prefetch_desc(&map_in);
@@ -62,13 +138,11 @@ diffusion_kernel(const __grid_constant__ CUtensorMap map_in, T *__restrict__ out
     }
     __syncthreads();
 
-    // TMA box origin in padded coordinates: x start rounded down by HX (16-byte aligned),
-    // y start = first halo row, z = padded plane index.
-    const int bx = (int)(g.off[0] + x0 - Cfg::HX);
-    const int by0 = (int)(g.off[1] + y0 - R6);
-    const int bz0 = (int)(g.off[2] + zc0 - R6);
-    auto issue = [&](int j) {  // load plane j (0-based from zc0-3) into slot j % NSLOT
-        const int s = j % NSLOT;
+    const int bx = (int)g.off[0] + x0 - Cfg::HX;
+    const int by0 = (int)g.off[1] + y0 - R6;
+    const int bz0 = (int)g.off[2] + zc0 - R6;
+    auto issue = [&](int j) {  // plane j (0-based from zc0-3) into its ring slot
+        const int s = slot_of<NSLOT>(j);
         mbar_arrive_expect_tx(&full[s], Cfg::BOX_BYTES);
         tma_load_3d(ring + s * Cfg::SLOT_ELEMS, &map_in, &full[s], bx, by0, bz0 + j);
     };
@@ -76,118 +150,298 @@ diffusion_kernel(const __grid_constant__ CUtensorMap map_in, T *__restrict__ out
     if (threadIdx.x == 0)
         for (; issued < NSLOT && issued < nplanes; ++issued) issue(issued);
 
-    T q[RY][7];
-    bool ok = true;
-    // centre of row r of this thread within a slot
-    auto cell = [&](int slot, int r) -> T * {
-        return ring + slot * Cfg::SLOT_ELEMS + (by * RY + r + R6) * Cfg::TXP + tx + Cfg::HX;
-    };
-    // prologue: own values of planes zc0-3 .. zc0+2 (j = 0..5)
-    for (int j = 0; j < 2 * R6; ++j) {
-        ok = ok && mbar_wait_bounded(&full[j % NSLOT], (j / NSLOT) & 1);
+    // element offset of (row 0 of this thread, first cell) inside a slot
+    const int own = (wy * RY + R6) * Cfg::TXP + Cfg::HX + lane * VX;
+
+    // weights as pairs
+    const P G0 = O::make(c.g0, c.g0);
+    P GA[3][3];
 #pragma unroll
-        for (int r = 0; r < RY; ++r) q[r][j + 1] = ok ? *cell(j % NSLOT, r) : T(0);
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) GA[a][b] = O::make(c.ga[a][b], c.ga[a][b]);
+
+    // z queue: Q[k] holds plane z-3+k of the iteration's first output plane z (k < ZB + 6)
+    P Q[ZB + 6][RY][VP];
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < 2 * R6; ++j) {  // prologue: planes zc0-3 .. zc0+2 into Q[0..5]
+        ok = ok && mbar_wait_bounded(&full[slot_of<NSLOT>(j)], parity_of<NSLOT>(j));
+        const T *sp = ring + slot_of<NSLOT>(j) * Cfg::SLOT_ELEMS + own;
+#pragma unroll
+        for (int r = 0; r < RY; ++r) {
+            T e[VX];
+            if (ok) ld_vec<T, LV>(sp + r * Cfg::TXP, e);
+            else {
+#pragma unroll
+                for (int u = 0; u < VX; ++u) e[u] = T(0);
+            }
+#pragma unroll
+            for (int p = 0; p < VP; ++p) Q[j][r][p] = O::make(e[2 * p], e[2 * p + 1]);
+        }
     }
     bool bad = __syncthreads_or(!ok);
-    // planes j = 0..2 are no longer needed: refill their slots
+    // planes j = 0..2 are never read from shared memory again: refill their slots
     if (!bad && threadIdx.x == 0)
         for (; issued < NSLOT + R6 && issued < nplanes; ++issued) issue(issued);
 
-    for (int m = 0; !bad && m < (int)(zend - zc0); ++m) {
-        const int jl = m + 2 * R6;  // leading plane z+3
-        const int sl = jl % NSLOT, sc = (m + R6) % NSLOT;
-        ok = mbar_wait_bounded(&full[sl], (jl / NSLOT) & 1);
-        if (ok) {
-            const int64_t z = zc0 + m;
+    // Periodic images (Eq. 2) of this thread's cells.  z- and y-images repeat the row's vector
+    // store at a shifted plane/row (warp-uniform); x-images are per-lane scalar stores.
+    const bool full_tile = x + VX <= nx && yb + RY <= ny;
+    const bool any_cell = x < nx && yb < ny;
+    int xmask = 0;        // bit u: cell x+u has an x-image
+    int xshift = 0;       // +nx (low face) or -nx (high face)
 #pragma unroll
-            for (int r = 0; r < RY; ++r) {
+    for (int u = 0; u < VX; ++u) {
+        if (x + u < R6) { xmask |= 1 << u; xshift = nx; }
+        else if (x + u >= nx - R6) { xmask |= 1 << u; xshift = -nx; }
+    }
+    int yshift[RY];
 #pragma unroll
-                for (int k = 0; k < 6; ++k) q[r][k] = q[r][k + 1];
-                q[r][6] = *cell(sl, r);
-                const T *p = cell(sc, r);
-                T acc = c.g0 * q[r][3];
+    for (int r = 0; r < RY; ++r) yshift[r] = (yb + r < R6) ? ny : (yb + r >= ny - R6) ? -ny : 0;
+    if (!images) {
+        xmask = 0;
 #pragma unroll
-                for (int a = 1; a <= R6; ++a) {
-                    acc = fma(c.ga[0][a - 1], p[a] + p[-a], acc);
-                    acc = fma(c.ga[1][a - 1], p[a * Cfg::TXP] + p[-a * Cfg::TXP], acc);
-                    acc = fma(c.ga[2][a - 1], q[r][3 + a] + q[r][3 - a], acc);
+        for (int r = 0; r < RY; ++r) yshift[r] = 0;
+    }
+    const int64_t pitch_y = g.pad[0], pitch_z = g.pad[0] * g.pad[1];
+    T *optr = out + g.idx(x, yb, zc0);
+
+    for (int m = 0; !bad && m < count; m += ZB) {
+        // leading planes j = m+6 .. m+5+ZB (those that exist) enter the queue at Q[6..]
+#pragma unroll
+        for (int b = 0; b < ZB; ++b) {
+            const int jl = m + 2 * R6 + b;
+            if (jl < nplanes) {
+                ok = ok && mbar_wait_bounded(&full[slot_of<NSLOT>(jl)], parity_of<NSLOT>(jl));
+                if (ok && any_cell) {
+                    const T *lp = ring + slot_of<NSLOT>(jl) * Cfg::SLOT_ELEMS + own;
+#pragma unroll
+                    for (int r = 0; r < RY; ++r) {
+                        T le[VX];
+                        ld_vec<T, LV>(lp + r * Cfg::TXP, le);
+#pragma unroll
+                        for (int p = 0; p < VP; ++p) Q[6 + b][r][p] = O::make(le[2 * p], le[2 * p + 1]);
+                    }
                 }
-                const int64_t y = y0 + by * RY + r;
-                if (active_x && y < g.n[1]) store_with_images(out, g, R6, images != 0, x, y, z, acc);
             }
         }
+        if (ok && any_cell) {
+#pragma unroll
+            for (int b = 0; b < ZB; ++b) {
+                if (m + b < count) {
+                    const int z = zc0 + m + b;
+                    const T *cp = ring + slot_of<NSLOT>(m + b + R6) * Cfg::SLOT_ELEMS + own;
+                    // y column: rows -3 .. RY+2 of this thread's cells, as pairs
+                    P Y[RY + 6][VP];
+#pragma unroll
+                    for (int d = 0; d < RY + 6; ++d) {
+                        T e[VX];
+                        ld_vec<T, LV>(cp + (d - R6) * Cfg::TXP, e);
+#pragma unroll
+                        for (int p = 0; p < VP; ++p) Y[d][p] = O::make(e[2 * p], e[2 * p + 1]);
+                    }
+                    P res[RY][VP];
+#pragma unroll
+                    for (int r = 0; r < RY; ++r) {
+                        // x window: cells -4 .. VX+3 of row r
+                        T E[VX + 8];
+                        ld_vec<T, LV>(cp + r * Cfg::TXP - 4, E);
+#pragma unroll
+                        for (int p = 0; p < VP; ++p) {
+                            const int i0 = 4 + 2 * p;  // E index of the pair's first cell
+                            P acc = O::mul(G0, Y[r + R6][p]);
+                            // x: even offset from aligned pairs, odd offsets from scalar adds
+                            const P sx1 = O::make(E[i0 + 1] + E[i0 - 1], E[i0 + 2] + E[i0]);
+                            const P sx2 = O::add(O::make(E[i0 + 2], E[i0 + 3]), O::make(E[i0 - 2], E[i0 - 1]));
+                            const P sx3 = O::make(E[i0 + 3] + E[i0 - 3], E[i0 + 4] + E[i0 - 2]);
+                            acc = O::fma2(GA[0][0], sx1, acc);
+                            acc = O::fma2(GA[1][0], O::add(Y[r + R6 + 1][p], Y[r + R6 - 1][p]), acc);
+                            acc = O::fma2(GA[2][0], O::add(Q[b + 4][r][p], Q[b + 2][r][p]), acc);
+                            acc = O::fma2(GA[0][1], sx2, acc);
+                            acc = O::fma2(GA[1][1], O::add(Y[r + R6 + 2][p], Y[r + R6 - 2][p]), acc);
+                            acc = O::fma2(GA[2][1], O::add(Q[b + 5][r][p], Q[b + 1][r][p]), acc);
+                            acc = O::fma2(GA[0][2], sx3, acc);
+                            acc = O::fma2(GA[1][2], O::add(Y[r + R6 + 3][p], Y[r + R6 - 3][p]), acc);
+                            acc = O::fma2(GA[2][2], O::add(Q[b + 6][r][p], Q[b][r][p]), acc);
+                            res[r][p] = acc;
+                        }
+                    }
+                    T *op = optr + b * pitch_z;
+                    if (full_tile) {
+                        const int zshift = images ? ((z < R6) ? nz : (z >= nz - R6) ? -nz : 0) : 0;
+#pragma unroll
+                        for (int zi = 0; zi < 2; ++zi) {
+                            if (zi == 1 && zshift == 0) break;
+                            T *zp = op + (zi ? (int64_t)zshift * pitch_z : 0);
+#pragma unroll
+                            for (int r = 0; r < RY; ++r) {
+#pragma unroll
+                                for (int yi = 0; yi < 2; ++yi) {
+                                    if (yi == 1 && yshift[r] == 0) break;
+                                    T *rp = zp + (int64_t)(r + (yi ? yshift[r] : 0)) * pitch_y;
+                                    if constexpr (VP == 2 && sizeof(T) == 4) {  // one 16-byte store
+                                        *reinterpret_cast<float4 *>(rp) =
+                                            make_float4(res[r][0].x, res[r][0].y, res[r][1].x, res[r][1].y);
+                                    } else {
+#pragma unroll
+                                        for (int p = 0; p < VP; ++p) *reinterpret_cast<P *>(rp + 2 * p) = res[r][p];
+                                    }
+                                    if (xmask) {
+#pragma unroll
+                                        for (int p = 0; p < VP; ++p) {
+                                            if (xmask & (1 << (2 * p))) rp[2 * p + xshift] = res[r][p].x;
+                                            if (xmask & (2 << (2 * p))) rp[2 * p + 1 + xshift] = res[r][p].y;
+                                        }
+                                    }
+                                }
+                            }
+                        }
+                    } else {
+                        // ragged tile: element-wise stores with bounds checks and all images
+#pragma unroll
+                        for (int r = 0; r < RY; ++r)
+#pragma unroll
+                            for (int p = 0; p < VP; ++p) {
+                                const T v2[2] = {res[r][p].x, res[r][p].y};
+#pragma unroll
+                                for (int u = 0; u < 2; ++u)
+                                    if (x + 2 * p + u < nx && yb + r < ny)
+                                        store_with_images(out, g, R6, images != 0, x + 2 * p + u, yb + r, z, v2[u]);
+                            }
+                    }
+                }
+            }
+            // shift the queue by ZB planes
+#pragma unroll
+            for (int k = 0; k < 6; ++k)
+#pragma unroll
+                for (int r = 0; r < RY; ++r)
+#pragma unroll
+                    for (int p = 0; p < VP; ++p) Q[k][r][p] = Q[k + ZB][r][p];
+        }
+        optr += ZB * pitch_z;
         bad = __syncthreads_or(!ok);
-        // plane j = m + 3 (centre of this iteration) is retired: reuse its slot
-        if (!bad && threadIdx.x == 0 && issued < nplanes && issued == m + R6 + NSLOT) issue(issued++);
+        // planes j < m + ZB + 3 are retired: refill the ring up to NSLOT planes ahead
+        if (!bad && threadIdx.x == 0) {
+            const int lim = min(nplanes, m + ZB + R6 + NSLOT);
+            for (; issued < lim; ++issued) issue(issued);
+        }
     }
     if (bad && threadIdx.x == 0) {
         atomicOr(err, ERR_TIMEOUT);
         // drain loads still in flight before the CTA's shared memory is released
         for (int j = max(0, issued - NSLOT); j < issued; ++j)
-            (void)mbar_wait_bounded(&full[j % NSLOT], (j / NSLOT) & 1, 100000000ull);
+            (void)mbar_wait_bounded(&full[slot_of<NSLOT>(j)], parity_of<NSLOT>(j), 100000000ull);
     }
 }
 
 // ------------------------------------------------------------------ variants / launch
 
-template <typename T, int TX, int BY, int RY, int NSLOT, int ZC>
-static cudaError_t run(const CUtensorMap *map, void *out, const Geom &g, const DiffCoef &dc,
-                       bool images, unsigned *err, cudaStream_t s) {
-    using Cfg = DiffCfg<T, TX, BY, RY, NSLOT, ZC>;
+// Number of z-chunks for a grid of `tiles` xy-tiles: maximise the fraction of the last wave
+// that is occupied, with a mild penalty for the 6 extra planes each chunk re-reads.
+int choose_zchunks(int tiles, int nz, int slots, double reread_weight) {
+    int best = 1;
+    double best_score = -1.0;
+    for (int c = 1; c <= std::min(nz, 512); ++c) {
+        const int zc = (nz + c - 1) / c;
+        const int cc = (nz + zc - 1) / zc;
+        if (cc != c) continue;
+        const long ctas = (long)tiles * c;
+        const long waves = (ctas + slots - 1) / slots;
+        const double eff = (double)ctas / (double)(waves * slots);
+        const double score = eff * (1.0 - reread_weight * 6.0 / (zc + 6.0)) - 1e-4 * c;
+        if (score > best_score) {
+            best_score = score;
+            best = c;
+        }
+    }
+    return best;
+}
+
+int device_sms() {
+    static int sms[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (!sms[dev] && cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        sms[dev] = 152;
+    return sms[dev];
+}
+
+template <typename T, int VP, int BY, int RY, int ZB, int NSLOT, bool PK>
+static cudaError_t run(const CUtensorMap *map, void *out, const Geom &g, const DiffCoef &dc, bool images,
+                       unsigned *err, cudaStream_t s) {
+    using Cfg = DiffCfg<T, VP, BY, RY, ZB, NSLOT>;
     DC<T> c;
     c.g0 = (T)dc.g0;
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) c.ga[a][b] = (T)dc.ga[a][b];
-    auto k = diffusion_kernel<T, TX, BY, RY, NSLOT, ZC>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+    auto k = diffusion_kernel<T, VP, BY, RY, ZB, NSLOT, PK>;
+    static int occ[64] = {};  // resident CTAs per SM, per device
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)((g.n[0] + TX - 1) / TX), (unsigned)((g.n[1] + Cfg::TY - 1) / Cfg::TY),
-              (unsigned)((g.n[2] + ZC - 1) / ZC));
-    k<<<grid, TX * BY, Cfg::SMEM, s>>>(*map, static_cast<T *>(out), g, c, images ? 1 : 0, err);
+    if (dev >= 64) return cudaErrorInvalidDevice;
+    if (!occ[dev]) {
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+        if (e != cudaSuccess) return e;
+        int o = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, 32 * BY, Cfg::SMEM);
+        if (e != cudaSuccess) return e;
+        occ[dev] = std::max(o, 1);
+    }
+    const int tx = (int)((g.n[0] + Cfg::TX - 1) / Cfg::TX), ty = (int)((g.n[1] + Cfg::TY - 1) / Cfg::TY);
+    const int nz = (int)g.n[2];
+    const int chunks = choose_zchunks(tx * ty, nz, occ[dev] * device_sms(), sizeof(T) == 4 ? 0.5 : 0.05);
+    const int zc = (nz + chunks - 1) / chunks;
+    dim3 grid(tx, ty, (unsigned)((nz + zc - 1) / zc));
+    k<<<grid, 32 * BY, Cfg::SMEM, s>>>(*map, static_cast<T *>(out), g, c, zc, images ? 1 : 0, err);
     return cudaGetLastError();
 }
 
-// Variant table: (TX, BY, RY, NSLOT, ZC) per dtype.  The autotuner times each on the
-// problem and keeps the fastest.
+// Variant table: (VP pairs per row, BY warps, RY rows, ZB planes, NSLOT, packed FP32x2)
+// per dtype.  The autotuner times each on the problem and keeps the fastest.
 #define DIFF_VARIANTS_F64(X) \
-    X(32, 8, 1, 7, 64)       \
-    X(32, 4, 2, 7, 64)       \
-    X(64, 4, 1, 7, 64)       \
-    X(32, 8, 1, 8, 32)
+    X(1, 8, 1, 2, 8, false)  \
+    X(1, 4, 1, 2, 8, false)  \
+    X(1, 8, 1, 1, 8, false)  \
+    X(1, 4, 2, 2, 8, false)
 #define DIFF_VARIANTS_F32(X) \
-    X(32, 8, 1, 8, 64)       \
-    X(32, 4, 2, 8, 64)       \
-    X(64, 4, 2, 8, 64)       \
-    X(128, 2, 2, 9, 64)
+    X(1, 8, 2, 4, 16, true)  \
+    X(1, 8, 2, 2, 8, true)   \
+    X(1, 8, 1, 4, 16, true)  \
+    X(1, 4, 2, 4, 16, true)  \
+    X(2, 4, 2, 2, 8, true)   \
+    X(1, 8, 2, 4, 16, false)
 
-int diffusion_num_variants(int dtype) { return dtype == 1 ? 4 : 4; }
+static const char *F64_NAMES[] = {"vx2_by8_ry1_zb2_s8", "vx2_by4_ry1_zb2_s8", "vx2_by8_ry1_zb1_s8",
+                                  "vx2_by4_ry2_zb2_s8"};
+static const char *F32_NAMES[] = {"vx2_by8_ry2_zb4_s16_pk", "vx2_by8_ry2_zb2_s8_pk", "vx2_by8_ry1_zb4_s16_pk",
+                                  "vx2_by4_ry2_zb4_s16_pk", "vx4_by4_ry2_zb2_s8_pk", "vx2_by8_ry2_zb4_s16"};
+
+int diffusion_num_variants(int dtype) { return dtype == 1 ? 4 : 6; }
 
 const char *diffusion_variant_name(int dtype, int v) {
-    static const char *f64[] = {"tx32_by8_ry1_s7_zc64", "tx32_by4_ry2_s7_zc64", "tx64_by4_ry1_s7_zc64",
-                                "tx32_by8_ry1_s8_zc32"};
-    static const char *f32[] = {"tx32_by8_ry1_s8_zc64", "tx32_by4_ry2_s8_zc64", "tx64_by4_ry2_s8_zc64",
-                                "tx128_by2_ry2_s9_zc64"};
-    if (v < 0 || v >= 4) return "?";
-    return dtype == 1 ? f64[v] : f32[v];
+    if (v < 0 || v >= diffusion_num_variants(dtype)) return "?";
+    return dtype == 1 ? F64_NAMES[v] : F32_NAMES[v];
 }
 
 void diffusion_box(int dtype, int v, int box[3]) {
     int i = 0;
-    auto put = [&](int tx, int ty, int hx) {
-        if (i++ == v) { box[0] = tx + 2 * hx; box[1] = ty + 2 * R6; box[2] = 1; }
+    auto put = [&](int vp, int by, int ry) {
+        if (i++ == v) { box[0] = 64 * vp + 8; box[1] = by * ry + 2 * R6; box[2] = 1; }
     };
-#define X(TX, BY, RY, NS, ZC) put(TX, BY * RY, 4);
+#define X(VP, BY, RY, ZB, NS, PK) put(VP, BY, RY);
     if (dtype == 1) { DIFF_VARIANTS_F64(X) } else { DIFF_VARIANTS_F32(X) }
 #undef X
 }
 
-cudaError_t launch_diffusion(int dtype, const CUtensorMap *map, void *out, const Geom &g,
-                             const DiffCoef &c, bool images, unsigned *err, cudaStream_t s,
-                             int variant) {
+cudaError_t launch_diffusion(int dtype, const CUtensorMap *map, void *out, const Geom &g, const DiffCoef &c,
+                             bool images, unsigned *err, cudaStream_t s, int variant) {
     int i = 0;
     cudaError_t res = cudaErrorInvalidValue;
-#define X(TX, BY, RY, NS, ZC) \
-    if (i++ == variant) res = run<T, TX, BY, RY, NS, ZC>(map, out, g, c, images, err, s);
+#define X(VP, BY, RY, ZB, NS, PK) \
+    if (i++ == variant) res = run<T, VP, BY, RY, ZB, NS, PK>(map, out, g, c, images, err, s);
     if (dtype == 1) {
         using T = double;
         DIFF_VARIANTS_F64(X)

@@ -22,6 +22,11 @@ cudaError_t launch_xcorr(int dtype, int r, const void *in, void *out, const Geom
                          const void *coeffs, int sweeps, bool periodic, bool images,
                          cudaStream_t s);
 
+// Grid sizing shared by the z-streaming kernels: number of z-chunks that best fills whole
+// waves of `slots` resident CTAs (see diffusion.cu), and the SM count of the current device.
+int choose_zchunks(int tiles, int nz, int slots, double reread_weight);
+int device_sms();
+
 // DIFFUSION (Eqs. 4-7): one folded 19-point step, 3D, radius 3, read through TMA.
 struct DiffCoef {
     double g0;       // centre weight 1 + dt*alpha*sum_axes c0/h^2

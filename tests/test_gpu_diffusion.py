@@ -47,8 +47,8 @@ def test_against_oracle(cuda_lib, dtype, shape):
 
 
 @pytest.mark.parametrize("dtype", DT)
-def test_halo_images_and_input_untouched(cuda_lib, dtype):
-    shape = (20, 21, 22)
+@pytest.mark.parametrize("shape", [(20, 21, 22), (40, 48, 128), (7, 16, 64)])
+def test_halo_images_and_input_untouched(cuda_lib, dtype, shape):
     f0 = synth.heat_field(shape, seed=3)
     got, p, par, (a, b) = _steps(shape, dtype, 1, f0)
     whole = p.view3(b[0]).double().cpu().numpy()
