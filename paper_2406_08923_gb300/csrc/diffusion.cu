@@ -186,20 +186,29 @@ diffusion_kernel(const __grid_constant__ CUtensorMap map_in, T *__restrict__ out
         for (; issued < NSLOT + R6 && issued < nplanes; ++issued) issue(issued);
 
     // Periodic images (Eq. 2) of this thread's cells.  z- and y-images repeat the row's vector
-    // store at a shifted plane/row (warp-uniform); x-images are per-lane scalar stores.
+    // store at a shifted plane/row (warp-uniform).  x-images: threads holding cells within 4 of
+    // a face store their whole vector again, shifted by -+nx, into the halo and the unused
+    // padding next to it (when nx is a multiple of VX); otherwise per-cell scalar stores.
     const bool full_tile = x + VX <= nx && yb + RY <= ny;
     const bool any_cell = x < nx && yb < ny;
-    int xmask = 0;        // bit u: cell x+u has an x-image
-    int xshift = 0;       // +nx (low face) or -nx (high face)
+    const bool xvec = (nx % VX == 0) && nx >= 8 && g.off[0] >= 4 && g.pad[0] >= g.off[0] + nx + 4;
+    int xshift = 0;  // interior-coordinate shift of this thread's x-image, 0 if none
+    int xmask = 0;   // scalar fallback: bit u set if cell x+u has an image
+    if (xvec) {
+        if (x < 4) xshift = nx;
+        else if (x >= nx - 4) xshift = -nx;
+    } else {
 #pragma unroll
-    for (int u = 0; u < VX; ++u) {
-        if (x + u < R6) { xmask |= 1 << u; xshift = nx; }
-        else if (x + u >= nx - R6) { xmask |= 1 << u; xshift = -nx; }
+        for (int u = 0; u < VX; ++u) {
+            if (x + u < R6) { xmask |= 1 << u; xshift = nx; }
+            else if (x + u >= nx - R6) { xmask |= 1 << u; xshift = -nx; }
+        }
     }
     int yshift[RY];
 #pragma unroll
     for (int r = 0; r < RY; ++r) yshift[r] = (yb + r < R6) ? ny : (yb + r >= ny - R6) ? -ny : 0;
     if (!images) {
+        xshift = 0;
         xmask = 0;
 #pragma unroll
         for (int r = 0; r < RY; ++r) yshift[r] = 0;
@@ -280,12 +289,17 @@ diffusion_kernel(const __grid_constant__ CUtensorMap map_in, T *__restrict__ out
                                 for (int yi = 0; yi < 2; ++yi) {
                                     if (yi == 1 && yshift[r] == 0) break;
                                     T *rp = zp + (int64_t)(r + (yi ? yshift[r] : 0)) * pitch_y;
-                                    if constexpr (VP == 2 && sizeof(T) == 4) {  // one 16-byte store
-                                        *reinterpret_cast<float4 *>(rp) =
-                                            make_float4(res[r][0].x, res[r][0].y, res[r][1].x, res[r][1].y);
-                                    } else {
 #pragma unroll
-                                        for (int p = 0; p < VP; ++p) *reinterpret_cast<P *>(rp + 2 * p) = res[r][p];
+                                    for (int xi = 0; xi < 2; ++xi) {
+                                        if (xi == 1 && (!xvec || xshift == 0)) break;
+                                        T *xp = rp + (xi ? xshift : 0);
+                                        if constexpr (VP == 2 && sizeof(T) == 4) {  // one 16-byte store
+                                            *reinterpret_cast<float4 *>(xp) =
+                                                make_float4(res[r][0].x, res[r][0].y, res[r][1].x, res[r][1].y);
+                                        } else {
+#pragma unroll
+                                            for (int p = 0; p < VP; ++p) *reinterpret_cast<P *>(xp + 2 * p) = res[r][p];
+                                        }
                                     }
                                     if (xmask) {
 #pragma unroll
@@ -407,17 +421,17 @@ static cudaError_t run(const CUtensorMap *map, void *out, const Geom &g, const D
     X(1, 8, 1, 1, 8, false)  \
     X(1, 4, 2, 2, 8, false)
 #define DIFF_VARIANTS_F32(X) \
-    X(1, 8, 2, 4, 16, true)  \
-    X(1, 8, 2, 2, 8, true)   \
-    X(1, 8, 1, 4, 16, true)  \
-    X(1, 4, 2, 4, 16, true)  \
     X(2, 4, 2, 2, 8, true)   \
-    X(1, 8, 2, 4, 16, false)
+    X(2, 8, 2, 2, 8, true)   \
+    X(2, 4, 4, 2, 8, true)   \
+    X(2, 4, 4, 1, 8, true)   \
+    X(1, 4, 2, 4, 16, true)  \
+    X(2, 8, 2, 1, 8, true)
 
 static const char *F64_NAMES[] = {"vx2_by8_ry1_zb2_s8", "vx2_by4_ry1_zb2_s8", "vx2_by8_ry1_zb1_s8",
                                   "vx2_by4_ry2_zb2_s8"};
-static const char *F32_NAMES[] = {"vx2_by8_ry2_zb4_s16_pk", "vx2_by8_ry2_zb2_s8_pk", "vx2_by8_ry1_zb4_s16_pk",
-                                  "vx2_by4_ry2_zb4_s16_pk", "vx4_by4_ry2_zb2_s8_pk", "vx2_by8_ry2_zb4_s16"};
+static const char *F32_NAMES[] = {"vx4_by4_ry2_zb2_s8_pk", "vx4_by8_ry2_zb2_s8_pk", "vx4_by4_ry4_zb2_s8_pk",
+                                  "vx4_by4_ry4_zb1_s8_pk", "vx2_by4_ry2_zb4_s16_pk", "vx4_by8_ry2_zb1_s8_pk"};
 
 int diffusion_num_variants(int dtype) { return dtype == 1 ? 4 : 6; }
 
