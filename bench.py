@@ -131,7 +131,9 @@ class Clocks:
 # ----------------------------------------------------------------------------- helpers
 
 
-def _dist():
+def _dist(backend=None):
+    """(rank, world, torch.distributed or None) from the torchrun environment.  The data path
+    has no collective: ranks only meet in barriers and the max-over-ranks timing reduction."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws <= 1:
         return 0, 1, None
@@ -139,8 +141,11 @@ def _dist():
     import torch.distributed as dist
     rank = int(os.environ["RANK"])
     local = int(os.environ.get("LOCAL_RANK", rank))
-    torch.cuda.set_device(local)
-    dist.init_process_group("nccl")
+    if backend is None:
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if backend == "nccl":
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend)
     return rank, ws, dist
 
 
@@ -153,9 +158,16 @@ def _max_over_ranks(v, dist):
     if dist is None:
         return v
     import torch
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def weak_scaling_value(world, units_per_rank, seconds):
+    """Whole-job throughput in millions of units per second: every rank processed
+    units_per_rank in the same (max-over-ranks) time."""
+    return world * units_per_rank / seconds / 1e6
 
 
 def _timed(fn, reps, stream):
@@ -352,7 +364,7 @@ def run_ours(args):
     ms = e0.elapsed_time(e1) / args.steps
     ms = _max_over_ranks(ms, dist)
     clocks = clk.summary()
-    value = world * cells * HEAT_STEPS / (ms / 1e3) / 1e6
+    value = weak_scaling_value(world, cells * HEAT_STEPS, ms / 1e3)
 
     # per-kernel average: job time minus the one input halo fill, over 100 passes
     ms_halo = _timed(lambda: p.halo_fill(a, stream), 20, stream)

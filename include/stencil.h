@@ -216,6 +216,16 @@ stencil_status stencil_field_norms_noalloc(void *const *fields, int nfields, ste
                                            const int64_t origin[3], double mass_volume,
                                            double *out_dev, void *stream);
 
+/*
+ * stencil_selftest_wait -- exercise the failure-detection path of the bounded device waits.
+ * Launches one CTA that waits on an mbarrier that nothing will ever complete, for at most
+ * limit_ns nanoseconds (clamped to 1 us .. 2 s).  The expiry is recorded exactly like a
+ * timed-out wait in a stencil kernel: the next stencil_sync (or stencil_field_norms) on
+ * the plan returns STENCIL_ETIMEOUT and clears it.  Nothing faults or hangs and the CUDA
+ * context stays usable.  The paper has no counterpart; this exists for testing.
+ */
+stencil_status stencil_selftest_wait(stencil_t plan, int64_t limit_ns, void *stream);
+
 /* stencil_sync -- synchronise `stream` and report (then clear) any expired device wait
  * recorded by this plan's kernels since the last check. */
 stencil_status stencil_sync(stencil_t plan, void *stream);

@@ -28,7 +28,7 @@ EXPORTED = (
     "stencil_create", "stencil_destroy", "stencil_layout", "stencil_step", "stencil_halo_fill",
     "stencil_mhd_rhs", "stencil_field_norms", "stencil_sync", "stencil_strerror",
     "stencil_last_error_detail", "stencil_abi_version", "stencil_get_variant",
-    "stencil_set_variant", "stencil_autotune", "stencil_field_norms_noalloc",
+    "stencil_set_variant", "stencil_autotune", "stencil_field_norms_noalloc", "stencil_selftest_wait",
 )
 
 
@@ -77,6 +77,7 @@ def load():
             "stencil_get_variant": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(ctypes.c_char_p)]),
             "stencil_set_variant": (I, [P, I]),
             "stencil_autotune": (I, [P, PP, PP, I, I, P]),
+            "stencil_selftest_wait": (I, [P, I64, P]),
             "stencil_field_norms_noalloc": (I, [PP, I, I, ctypes.POINTER(I64), ctypes.POINTER(I64),
                                                 ctypes.POINTER(I64), D, P, P]),
         }
@@ -181,6 +182,10 @@ def stencil_autotune(h, fields_in, fields_out, nsteps=1, reps=3, stream=None):
     pi, ki = _ptrs(fields_in)
     po, ko = _ptrs(fields_out)
     _check(load().stencil_autotune(h, pi, po, nsteps, reps, _stream(stream)), "stencil_autotune", h)
+
+
+def stencil_selftest_wait(h, limit_ns, stream=None):
+    _check(load().stencil_selftest_wait(h, int(limit_ns), _stream(stream)), "stencil_selftest_wait", h)
 
 
 def stencil_field_norms_noalloc(fields, storage, dims, padded, origin, mass_volume, out_dev, stream=None):
@@ -289,6 +294,9 @@ class Plan:
 
     def set_variant(self, v):
         stencil_set_variant(self.h, v)
+
+    def selftest_wait(self, limit_ns, stream=None):
+        stencil_selftest_wait(self.h, limit_ns, stream)
 
     def autotune(self, fin, fout, nsteps=1, reps=3, stream=None):
         stencil_autotune(self.h, fin, fout, nsteps, reps, stream)

@@ -550,6 +550,15 @@ static stencil_status read_err(stencil_t p, cudaStream_t s) {
     return STENCIL_OK;
 }
 
+stencil_status stencil_selftest_wait(stencil_t p, int64_t limit_ns, void *stream) {
+    if (!p) return fail(nullptr, STENCIL_EINVAL, "plan is NULL");
+    stencil_status st = check_device(p);
+    if (st != STENCIL_OK) return st;
+    const uint64_t lim = (uint64_t)std::min<int64_t>(std::max<int64_t>(limit_ns, 1000), 2000000000);
+    CK(p, launch_selftest_wait(lim, p->err, (cudaStream_t)stream), "self-test launch");
+    return STENCIL_OK;
+}
+
 stencil_status stencil_sync(stencil_t p, void *stream) {
     if (!p) return fail(nullptr, STENCIL_EINVAL, "plan is NULL");
     stencil_status st = check_device(p);

@@ -108,13 +108,17 @@ __device__ __forceinline__ uint64_t global_ns() {
 
 // Wait for phase `parity` of `bar` for at most `limit_ns` nanoseconds.  Returns false if
 // the wait expired (the caller then records ERR_TIMEOUT and leaves the kernel cleanly).
+// Two independent bounds: the global nanosecond timer and the SM cycle counter (3 cycles per
+// nanosecond of limit, i.e. at least the limit at clocks up to 3 GHz), whichever trips first.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
                                                   uint64_t limit_ns = 2000000000ull) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
+    const long long c0 = clock64();
+    const long long climit = (long long)(3 * limit_ns);
     for (uint32_t it = 0;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 63u) == 63u && global_ns() - t0 > limit_ns) return false;
+        if ((it & 63u) == 63u && (global_ns() - t0 > limit_ns || clock64() - c0 > climit)) return false;
     }
 }
 

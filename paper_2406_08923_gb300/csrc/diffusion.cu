@@ -108,22 +108,20 @@ __device__ __forceinline__ void ld_vec(const T *p, T (&dst)[N]) {
     }
 }
 
+// One xy-tile of one z-chunk: the whole 2.5D pipeline of a CTA.  `map` may point at a
+// __grid_constant__ parameter or at a descriptor in global memory (batched launches).
+// Returns false if a bounded wait expired (ERR_TIMEOUT recorded, loads drained).
 template <typename T, int VP, int BY, int RY, int ZB, int NSLOT, bool PK>
-__global__ void __launch_bounds__(32 * BY)
-diffusion_kernel(const __grid_constant__ CUtensorMap map_in, T *__restrict__ out, Geom g, DC<T> c,
-                 int zc, int images, unsigned *err) {
+__device__ __forceinline__ bool diffusion_tile(const CUtensorMap *map, T *__restrict__ out, const Geom &g,
+                                               const DC<T> &c, int tile_x, int tile_y, int tile_z, int zc,
+                                               int images, unsigned *err, T *ring, uint64_t *full) {
     using Cfg = DiffCfg<T, VP, BY, RY, ZB, NSLOT>;
     using O = PairOps<T, PK>;
     using P = typename O::P;
     constexpr int VX = Cfg::VX, LV = Cfg::LV;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    // TMA destinations are kept 128-byte aligned (dynamic smem has 128 spare bytes)
-    T *ring = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    __shared__ __align__(8) uint64_t full[NSLOT];
-
     const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
-    const int x0 = blockIdx.x * Cfg::TX, y0 = blockIdx.y * Cfg::TY;
-    const int zc0 = blockIdx.z * zc;
+    const int x0 = tile_x * Cfg::TX, y0 = tile_y * Cfg::TY;
+    const int zc0 = tile_z * zc;
     const int nx = (int)g.n[0], ny = (int)g.n[1], nz = (int)g.n[2];
     const int zend = min(nz, zc0 + zc);
     const int count = zend - zc0;
@@ -132,7 +130,7 @@ diffusion_kernel(const __grid_constant__ CUtensorMap map_in, T *__restrict__ out
     const int yb = y0 + wy * RY;        // first of its RY rows
 
     if (threadIdx.x == 0) {
-        tma_prefetch_desc(&map_in);
+        tma_prefetch_desc(map);
         for (int s = 0; s < NSLOT; ++s) mbar_init(&full[s], 1);
         mbar_fence_init();
     }
@@ -144,7 +142,7 @@ diffusion_kernel(const __grid_constant__ CUtensorMap map_in, T *__restrict__ out
     auto issue = [&](int j) {  // plane j (0-based from zc0-3) into its ring slot
         const int s = slot_of<NSLOT>(j);
         mbar_arrive_expect_tx(&full[s], Cfg::BOX_BYTES);
-        tma_load_3d(ring + s * Cfg::SLOT_ELEMS, &map_in, &full[s], bx, by0, bz0 + j);
+        tma_load_3d(ring + s * Cfg::SLOT_ELEMS, map, &full[s], bx, by0, bz0 + j);
     };
     int issued = 0;
     if (threadIdx.x == 0)
@@ -348,6 +346,19 @@ diffusion_kernel(const __grid_constant__ CUtensorMap map_in, T *__restrict__ out
         for (int j = max(0, issued - NSLOT); j < issued; ++j)
             (void)mbar_wait_bounded(&full[slot_of<NSLOT>(j)], parity_of<NSLOT>(j), 100000000ull);
     }
+    return !bad;
+}
+
+template <typename T, int VP, int BY, int RY, int ZB, int NSLOT, bool PK>
+__global__ void __launch_bounds__(32 * BY)
+diffusion_kernel(const __grid_constant__ CUtensorMap map_in, T *__restrict__ out, Geom g, DC<T> c,
+                 int zc, int images, unsigned *err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // TMA destinations are kept 128-byte aligned (dynamic smem has 128 spare bytes)
+    T *ring = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    __shared__ __align__(8) uint64_t full[NSLOT];
+    diffusion_tile<T, VP, BY, RY, ZB, NSLOT, PK>(&map_in, out, g, c, blockIdx.x, blockIdx.y, blockIdx.z, zc,
+                                                 images, err, ring, full);
 }
 
 // ------------------------------------------------------------------ variants / launch

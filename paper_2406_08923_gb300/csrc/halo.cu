@@ -58,4 +58,22 @@ cudaError_t launch_halo_fill(const Geom &g, int r, int esize, const Ptrs8 &f, in
     return cudaGetLastError();
 }
 
+// Failure-detection self-test: wait on an mbarrier that never completes (nothing arrives and
+// no transaction bytes are expected), bounded by limit_ns, and report the expiry.
+__global__ void selftest_wait_kernel(uint64_t limit_ns, unsigned *err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(&bar, 0, limit_ns);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(err, ERR_TIMEOUT);
+}
+
+cudaError_t launch_selftest_wait(uint64_t limit_ns, unsigned *err, cudaStream_t s) {
+    selftest_wait_kernel<<<1, 32, 0, s>>>(limit_ns, err);
+    return cudaGetLastError();
+}
+
 }  // namespace stn

@@ -63,6 +63,9 @@ int norms_blocks();
 cudaError_t launch_norms(int storage, const Ptrs8 &f, int nfields, const Geom &g, bool mass0,
                          double *partials, double *out_dev, cudaStream_t s);
 
+// Bounded-wait self-test: one CTA waits on an mbarrier nothing completes.
+cudaError_t launch_selftest_wait(uint64_t limit_ns, unsigned *err, cudaStream_t s);
+
 // Allocation-free norms: partials in a file-scope device array (norms.cu); results packed
 // {sum, sumsq, max|f|} per field (+ mass) into device memory.
 int norms_static_max_fields();
