@@ -245,6 +245,63 @@ stencil_status stencil_set_variant(stencil_t plan, int variant);
 stencil_status stencil_autotune(stencil_t plan, void *const *fields_in, void *const *fields_out,
                                 int nsteps, int reps, void *stream);
 
+/*
+ * Continuous-batching server.  Many independent problems of different kinds and sizes are
+ * resident on the device at once and are advanced together: each iteration runs one step
+ * of every active problem (a heat Euler step, an MHD RK3 step, or a cross-correlation
+ * sweep) through one persistent batched launch per kind.  Problems are admitted in arrival
+ * order while an HBM byte budget and an active-slot limit allow, so requests that arrive
+ * while others run join the batch as memory and slots free up.  Storage and arithmetic are
+ * FP32 (MHD with Kahan-compensated RK); boundaries are periodic, radius 3.  None of this is
+ * in the paper: it is the serving layer of this library.
+ *
+ * A server belongs to the device current at creation and issues all work on `stream`.
+ * Calls on one server must come from one host thread at a time.
+ */
+typedef struct stencil_server *stencil_server_t;
+
+typedef struct stencil_request {
+    stencil_kind kind;     /* XCORR (1D, dims[0] cells), DIFFUSION or MHD8 (3D) */
+    int64_t dims[3];       /* interior extents, each 7 .. 2^20 */
+    int nsteps;            /* sweeps / Euler steps / RK3 steps, >= 1 */
+    double coeffs[7];      /* XCORR: weights g_{-3..3}; ignored otherwise */
+    stencil_params params; /* DIFFUSION and MHD8 constants (as for stencil_create) */
+} stencil_request;
+
+enum { STENCIL_REQ_PENDING = 0, STENCIL_REQ_ACTIVE = 1, STENCIL_REQ_COMPLETING = 2, STENCIL_REQ_DONE = 3 };
+
+/* Create a server with an HBM budget (bytes of problem data resident at once) and at most
+ * max_active problems in flight.  Allocates only small tables; problem memory comes from
+ * the device's stream-ordered memory pool at admission. */
+stencil_status stencil_server_create(int64_t hbm_budget_bytes, int max_active, void *stream,
+                                     stencil_server_t *out);
+/* Release the server and every problem's device memory (synchronises its stream). */
+void stencil_server_destroy(stencil_server_t server);
+/*
+ * Queue a problem.  host_in / host_out: nfields (1, or 8 for MHD8) host arrays of
+ * dims[0]*dims[1]*dims[2] floats, dense, x fastest.  host_in is read when the problem is
+ * admitted and host_out written when it completes; both must stay valid until the ticket
+ * reports STENCIL_REQ_DONE, and should be page-locked so that the copies are asynchronous.
+ * EINVAL if the request is malformed or needs more memory than the whole budget.
+ */
+stencil_status stencil_server_submit(stencil_server_t server, const stencil_request *req,
+                                     const float *const *host_in, float *const *host_out,
+                                     int64_t *ticket);
+/* One scheduling iteration: retire finished copy-backs, admit pending problems, launch one
+ * step of every active problem, queue copy-back of problems that reached nsteps.  Returns
+ * without waiting for the GPU.  Any output pointer may be NULL. */
+stencil_status stencil_server_progress(stencil_server_t server, int *n_pending, int *n_active,
+                                       int *n_done);
+/* State of a ticket (STENCIL_REQ_*). */
+stencil_status stencil_server_poll(stencil_server_t server, int64_t ticket, int *state);
+/* Bytes resident now, the peak, and cells x steps of all finished problems. */
+stencil_status stencil_server_stats(stencil_server_t server, int64_t *bytes_in_use,
+                                    int64_t *peak_bytes, int64_t *cell_updates_done);
+/* Synchronise the server's stream; STENCIL_ETIMEOUT if a bounded wait expired in a kernel. */
+stencil_status stencil_server_sync(stencil_server_t server);
+/* Detail of the last failure on `server` (or of the last failed create when NULL). */
+const char *stencil_server_last_error_detail(stencil_server_t server);
+
 /* Human-readable name of a status code (static string). */
 const char *stencil_strerror(stencil_status status);
 

@@ -29,7 +29,11 @@ EXPORTED = (
     "stencil_mhd_rhs", "stencil_field_norms", "stencil_sync", "stencil_strerror",
     "stencil_last_error_detail", "stencil_abi_version", "stencil_get_variant",
     "stencil_set_variant", "stencil_autotune", "stencil_field_norms_noalloc", "stencil_selftest_wait",
+    "stencil_server_create", "stencil_server_destroy", "stencil_server_submit", "stencil_server_progress",
+    "stencil_server_poll", "stencil_server_stats", "stencil_server_sync", "stencil_server_last_error_detail",
 )
+
+STENCIL_REQ_PENDING, STENCIL_REQ_ACTIVE, STENCIL_REQ_COMPLETING, STENCIL_REQ_DONE = range(4)
 
 
 class stencil_params(ctypes.Structure):
@@ -37,6 +41,11 @@ class stencil_params(ctypes.Structure):
                 ("cs0", ctypes.c_double), ("gamma", ctypes.c_double), ("cp", ctypes.c_double),
                 ("lnrho0", ctypes.c_double), ("nu", ctypes.c_double), ("eta", ctypes.c_double),
                 ("zeta", ctypes.c_double), ("mu0", ctypes.c_double)]
+
+
+class stencil_request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("dims", ctypes.c_int64 * 3), ("nsteps", ctypes.c_int),
+                ("coeffs", ctypes.c_double * 7), ("params", stencil_params)]
 
 
 class StencilError(RuntimeError):
@@ -78,6 +87,14 @@ def load():
             "stencil_set_variant": (I, [P, I]),
             "stencil_autotune": (I, [P, PP, PP, I, I, P]),
             "stencil_selftest_wait": (I, [P, I64, P]),
+            "stencil_server_create": (I, [I64, I, P, ctypes.POINTER(P)]),
+            "stencil_server_destroy": (None, [P]),
+            "stencil_server_submit": (I, [P, ctypes.POINTER(stencil_request), PP, PP, ctypes.POINTER(I64)]),
+            "stencil_server_progress": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
+            "stencil_server_poll": (I, [P, I64, ctypes.POINTER(I)]),
+            "stencil_server_stats": (I, [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)]),
+            "stencil_server_sync": (I, [P]),
+            "stencil_server_last_error_detail": (ctypes.c_char_p, [P]),
             "stencil_field_norms_noalloc": (I, [PP, I, I, ctypes.POINTER(I64), ctypes.POINTER(I64),
                                                 ctypes.POINTER(I64), D, P, P]),
         }
@@ -197,6 +214,59 @@ def stencil_field_norms_noalloc(fields, storage, dims, padded, origin, mass_volu
     st = load().stencil_field_norms_noalloc(p, len(fields), storage, d, pd, o, float(mass_volume),
                                             ctypes.c_void_p(int(out_dev.data_ptr())), _stream(stream))
     _check(st, "stencil_field_norms_noalloc", None)
+
+
+def _scheck(status, where, server):
+    if status != STENCIL_OK:
+        detail = load().stencil_server_last_error_detail(server).decode()
+        raise StencilError(status, where, detail)
+
+
+def stencil_server_create(hbm_budget_bytes, max_active, stream=None):
+    h = ctypes.c_void_p()
+    _scheck(load().stencil_server_create(int(hbm_budget_bytes), int(max_active), _stream(stream), ctypes.byref(h)),
+            "stencil_server_create", None)
+    return h
+
+
+def stencil_server_destroy(h):
+    if h:
+        load().stencil_server_destroy(h)
+
+
+def stencil_server_submit(h, req, host_in_ptrs, host_out_ptrs):
+    """host_in_ptrs / host_out_ptrs: lists of integer host addresses (float32 arrays)."""
+    pi = (ctypes.c_void_p * len(host_in_ptrs))(*host_in_ptrs)
+    po = (ctypes.c_void_p * len(host_out_ptrs))(*host_out_ptrs)
+    t = ctypes.c_int64()
+    _scheck(load().stencil_server_submit(h, ctypes.byref(req), ctypes.cast(pi, ctypes.POINTER(ctypes.c_void_p)),
+                                         ctypes.cast(po, ctypes.POINTER(ctypes.c_void_p)), ctypes.byref(t)),
+            "stencil_server_submit", h)
+    return t.value
+
+
+def stencil_server_progress(h):
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _scheck(load().stencil_server_progress(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+            "stencil_server_progress", h)
+    return a.value, b.value, c.value
+
+
+def stencil_server_poll(h, ticket):
+    st = ctypes.c_int()
+    _scheck(load().stencil_server_poll(h, int(ticket), ctypes.byref(st)), "stencil_server_poll", h)
+    return st.value
+
+
+def stencil_server_stats(h):
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _scheck(load().stencil_server_stats(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+            "stencil_server_stats", h)
+    return a.value, b.value, c.value
+
+
+def stencil_server_sync(h):
+    _scheck(load().stencil_server_sync(h), "stencil_server_sync", h)
 
 
 def stencil_destroy(h):

@@ -478,4 +478,66 @@ cudaError_t launch_diffusion(int dtype, const CUtensorMap *map, void *out, const
     return res;
 }
 
+// ------------------------------------------------------------------ batched (serving)
+
+// FP32, the tile shape of variant vx4_by4_ry2_zb2_s8_pk.
+constexpr int DB_VP = 2, DB_BY = 4, DB_RY = 2, DB_ZB = 2, DB_NSLOT = 8;
+using DbCfg = DiffCfg<float, DB_VP, DB_BY, DB_RY, DB_ZB, DB_NSLOT>;
+
+__global__ void __launch_bounds__(32 * DB_BY)
+diffusion_batch_kernel(const BatchHeader *hdr, const BatchHeat *items, unsigned *err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float *ring = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    __shared__ __align__(8) uint64_t full[DB_NSLOT];
+    const int total = hdr->heat_ctas, n = hdr->n_heat;
+    for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (items[mid].cta_begin <= vb) lo = mid; else hi = mid - 1;
+        }
+        const BatchHeat &it = items[lo];
+        int r = vb - it.cta_begin;
+        const int tx = r % it.tiles_x;
+        r /= it.tiles_x;
+        const int ty = r % it.tiles_y, tz = r / it.tiles_y;
+        DC<float> c;
+        c.g0 = it.g0;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) c.ga[a][b] = it.ga[a][b];
+        const Geom g = it.g;
+        const bool ok = diffusion_tile<float, DB_VP, DB_BY, DB_RY, DB_ZB, DB_NSLOT, true>(
+            it.map, it.out, g, c, tx, ty, tz, it.zc, 1, err, ring, full);
+        __syncthreads();
+        if (!ok) return;
+    }
+}
+
+int diffusion_batch_grid() {
+    static int grid[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return 152;
+    if (!grid[dev]) {
+        cudaFuncSetAttribute(diffusion_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DbCfg::SMEM);
+        int o = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, diffusion_batch_kernel, 32 * DB_BY, DbCfg::SMEM);
+        grid[dev] = std::max(o, 1) * device_sms();
+    }
+    return grid[dev];
+}
+
+void diffusion_batch_tile(int *tx, int *ty, int box[3]) {
+    *tx = DbCfg::TX;
+    *ty = DbCfg::TY;
+    box[0] = DbCfg::TXP;
+    box[1] = DbCfg::ROWS;
+    box[2] = 1;
+}
+
+cudaError_t launch_diffusion_batch(const BatchHeader *hdr, const BatchHeat *items, unsigned *err, int grid,
+                                   cudaStream_t s) {
+    diffusion_batch_kernel<<<grid, 32 * DB_BY, DbCfg::SMEM, s>>>(hdr, items, err);
+    return cudaGetLastError();
+}
+
 }  // namespace stn

@@ -72,4 +72,61 @@ int norms_static_max_fields();
 cudaError_t launch_norms_noalloc(int storage, const Ptrs8 &f, int nfields, const Geom &g,
                                  double mass_volume, double *out_dev, cudaStream_t s);
 
+// ------------------------------------------------------------------ batched serving
+// Scaled MHD constants in the compute type (defined here so batched work items can carry
+// them); alpha/beta are the RK substep coefficients.
+template <typename C> struct MK {
+    C d1[3][3], d2c[3], d2[3][3], dm[3][3];
+    C cs0sq, gamma, inv_cp, lnrho0, nu, eta, zeta, mu0, inv_mu0, cp_gm1;
+    C dt, alpha, beta;
+};
+
+// Work items of one batched launch.  Every item owns a contiguous range of virtual CTAs
+// [cta_begin, cta_begin + tiles); a persistent grid strides over the virtual CTAs and finds
+// the item by binary search on cta_begin.  All pointers are device pointers; descriptors are
+// resident in device memory (64-byte aligned).  Storage and arithmetic are FP32.
+struct BatchHeat {
+    const CUtensorMap *map;  // source field
+    float *out;
+    Geom g;
+    float g0, ga[3][3];
+    int zc, tiles_x, tiles_y, tiles_z;
+    int cta_begin, pad_;
+};
+struct BatchMhd {
+    const CUtensorMap *maps;  // 8 consecutive descriptors of the source field set
+    Ptrs8 fout, w, kc;
+    Geom g;
+    MK<float> k;  // alpha/beta filled in per launch
+    int zc, tiles_x, tiles_y, tiles_z;
+    int cta_begin, pad_;
+};
+struct BatchXcorr {
+    const float *in;
+    float *out;
+    Geom g;
+    float w[7];  // weights g_{-3..3}
+    int chunks;
+    int cta_begin, pad_;
+};
+// Counts of one batched iteration (device memory, read by the persistent kernels).
+struct BatchHeader {
+    int n_heat, heat_ctas, n_mhd, mhd_ctas, n_xc, xc_ctas, pad_[2];
+};
+
+cudaError_t launch_diffusion_batch(const BatchHeader *hdr, const BatchHeat *items, unsigned *err, int grid,
+                                   cudaStream_t s);
+cudaError_t launch_mhd_batch(const BatchHeader *hdr, const BatchMhd *items, int sub, unsigned *err, int grid,
+                             cudaStream_t s);
+cudaError_t launch_xcorr_batch(const BatchHeader *hdr, const BatchXcorr *items, unsigned *err, int grid,
+                               cudaStream_t s);
+// persistent grid sizes (resident CTAs on the current device) and tile shapes of the batched kernels
+int diffusion_batch_grid();
+int mhd_batch_grid();
+int xcorr_batch_grid();
+void diffusion_batch_tile(int *tx, int *ty, int box[3]);
+void mhd_batch_tile(int *tx, int *ty, int box[3]);
+int xcorr_batch_chunk();
+void mhd_scaled_constants(const MhdConst &c, MK<float> *k);
+
 }  // namespace stn

@@ -31,12 +31,6 @@ namespace stn {
 
 enum { F_LNRHO = 0, F_UX, F_UY, F_UZ, F_AX, F_AY, F_AZ, F_SS };
 
-template <typename C> struct MK {
-    C d1[3][3], d2c[3], d2[3][3], dm[3][3];
-    C cs0sq, gamma, inv_cp, lnrho0, nu, eta, zeta, mu0, inv_mu0, cp_gm1;
-    C dt, alpha, beta;
-};
-
 template <typename S, int TX, int TY, int NSLOT>
 struct MhdCfg {
     static constexpr int HX = 16 / (int)sizeof(S) >= 4 ? 16 / (int)sizeof(S) : 4;
@@ -200,19 +194,19 @@ __device__ __forceinline__ void mhd_rhs_cell(const W &w, const MK<C> &k, C *rhs,
     rhs[F_AZ] = (ux * by - uy * bx) + k.eta * lapa[2];
 }
 
-template <typename S, typename C, bool KAHAN, int MODE, int TX, int TY, int NSLOT, int MINB>
-__global__ void __launch_bounds__(TX *TY, MINB)
-mhd_kernel(const __grid_constant__ MhdMaps maps, Ptrs8 fout, Ptrs8 wbuf, Ptrs8 kbuf, Ptrs8 rbuf, Geom g,
-           MK<C> k, int zc, int first, int last, int images, unsigned *err) {
+// One xy-tile of one z-chunk of one RK substep (or RHS evaluation): the whole pipeline of a
+// CTA.  `maps` points at 8 consecutive descriptors (parameter or global memory); `k` may live
+// in parameter or shared memory.  Returns false if a bounded wait expired.
+template <typename S, typename C, bool KAHAN, int MODE, int TX, int TY, int NSLOT>
+__device__ __forceinline__ bool mhd_tile(const CUtensorMap *maps, const Ptrs8 &fout, const Ptrs8 &wbuf,
+                                         const Ptrs8 &kbuf, const Ptrs8 &rbuf, const Geom &g, const MK<C> &k,
+                                         int tile_x, int tile_y, int tile_z, int zc, int first, int last,
+                                         int images, unsigned *err, S *ring, uint64_t *full) {
     using Cfg = MhdCfg<S, TX, TY, NSLOT>;
     using W = Win<C, S, Cfg::FIELD_ELEMS, Cfg::TXP>;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    S *ring = reinterpret_cast<S *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    __shared__ __align__(8) uint64_t full[NSLOT];
-
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int zc0 = blockIdx.z * zc;
+    const int x0 = tile_x * TX, y0 = tile_y * TY;
+    const int zc0 = tile_z * zc;
     const int nx = (int)g.n[0], ny = (int)g.n[1], nz = (int)g.n[2];
     const int zend = min(nz, zc0 + zc);
     const int nplanes = (zend - zc0) + 2 * R6;
@@ -220,7 +214,7 @@ mhd_kernel(const __grid_constant__ MhdMaps maps, Ptrs8 fout, Ptrs8 wbuf, Ptrs8 k
     const bool active = x < nx && y < ny;
 
     if (threadIdx.x == 0) {
-        for (int q = 0; q < 8; ++q) tma_prefetch_desc(&maps.m[q]);
+        for (int q = 0; q < 8; ++q) tma_prefetch_desc(&maps[q]);
         for (int s = 0; s < NSLOT; ++s) mbar_init(&full[s], 1);
         mbar_fence_init();
     }
@@ -234,7 +228,7 @@ mhd_kernel(const __grid_constant__ MhdMaps maps, Ptrs8 fout, Ptrs8 wbuf, Ptrs8 k
         mbar_arrive_expect_tx(&full[s], 8 * Cfg::BOX_BYTES);
 #pragma unroll
         for (int q = 0; q < 8; ++q)
-            tma_load_3d(ring + s * Cfg::SLOT_ELEMS + q * Cfg::FIELD_ELEMS, &maps.m[q], &full[s], bx, by0, bz0 + j);
+            tma_load_3d(ring + s * Cfg::SLOT_ELEMS + q * Cfg::FIELD_ELEMS, &maps[q], &full[s], bx, by0, bz0 + j);
     };
     int issued = 0;
     if (threadIdx.x == 0)
@@ -315,6 +309,20 @@ mhd_kernel(const __grid_constant__ MhdMaps maps, Ptrs8 fout, Ptrs8 wbuf, Ptrs8 k
         for (int j = max(0, issued - NSLOT); j < issued; ++j)
             (void)mbar_wait_bounded(&full[(unsigned)j & (NSLOT - 1)], ((unsigned)j / NSLOT) & 1u, 100000000ull);
     }
+    return !bad;
+}
+
+template <typename S, typename C, bool KAHAN, int MODE, int TX, int TY, int NSLOT, int MINB>
+__global__ void __launch_bounds__(TX *TY, MINB)
+mhd_kernel(const __grid_constant__ MhdMaps maps, Ptrs8 fout, Ptrs8 wbuf, Ptrs8 kbuf, Ptrs8 rbuf, Geom g,
+           MK<C> k, int zc, int first, int last, int images, unsigned *err) {
+    using Cfg = MhdCfg<S, TX, TY, NSLOT>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    S *ring = reinterpret_cast<S *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    __shared__ __align__(8) uint64_t full[NSLOT];
+    (void)Cfg::SMEM;
+    mhd_tile<S, C, KAHAN, MODE, TX, TY, NSLOT>(maps.m, fout, wbuf, kbuf, rbuf, g, k, blockIdx.x, blockIdx.y,
+                                               blockIdx.z, zc, first, last, images, err, ring, full);
 }
 
 // ------------------------------------------------------------------ host side
@@ -422,6 +430,75 @@ cudaError_t launch_mhd(int storage, int mode, int sub, const MhdMaps &maps, cons
     }
 #undef X
     return res;
+}
+
+// ------------------------------------------------------------------ batched (serving)
+
+// FP32 storage, Kahan-compensated RK, the tile shape of variant tx32_ty4_s8_b2.
+constexpr int MB_TX = 32, MB_TY = 4, MB_NSLOT = 8;
+using MbCfg = MhdCfg<float, MB_TX, MB_TY, MB_NSLOT>;
+
+__global__ void __launch_bounds__(MB_TX *MB_TY, 2)
+mhd_batch_kernel(const BatchHeader *hdr, const BatchMhd *items, float alpha, float beta, int first, int last,
+                 unsigned *err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float *ring = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    __shared__ __align__(8) uint64_t full[MB_NSLOT];
+    __shared__ MK<float> ks;
+    const int total = hdr->mhd_ctas, n = hdr->n_mhd;
+    for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (items[mid].cta_begin <= vb) lo = mid; else hi = mid - 1;
+        }
+        const BatchMhd &it = items[lo];
+        int r = vb - it.cta_begin;
+        const int tx = r % it.tiles_x;
+        r /= it.tiles_x;
+        const int ty = r % it.tiles_y, tz = r / it.tiles_y;
+        constexpr int KW = (int)(sizeof(MK<float>) / sizeof(float));
+        for (int i = threadIdx.x; i < KW; i += blockDim.x)
+            reinterpret_cast<float *>(&ks)[i] = reinterpret_cast<const float *>(&it.k)[i];
+        if (threadIdx.x == 0) { ks.alpha = alpha; ks.beta = beta; }
+        __syncthreads();
+        const Geom g = it.g;
+        Ptrs8 none{};
+        const bool ok = mhd_tile<float, float, true, 0, MB_TX, MB_TY, MB_NSLOT>(
+            it.maps, it.fout, it.w, it.kc, none, g, ks, tx, ty, tz, it.zc, first, last, 1, err, ring, full);
+        __syncthreads();
+        if (!ok) return;
+    }
+}
+
+int mhd_batch_grid() {
+    static int grid[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return 152;
+    if (!grid[dev]) {
+        cudaFuncSetAttribute(mhd_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MbCfg::SMEM);
+        int o = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, mhd_batch_kernel, MB_TX * MB_TY, MbCfg::SMEM);
+        grid[dev] = std::max(o, 1) * device_sms();
+    }
+    return grid[dev];
+}
+
+void mhd_batch_tile(int *tx, int *ty, int box[3]) {
+    *tx = MB_TX;
+    *ty = MB_TY;
+    box[0] = MB_TX + 2 * MbCfg::HX;
+    box[1] = MB_TY + 2 * R6;
+    box[2] = 1;
+}
+
+void mhd_scaled_constants(const MhdConst &c, MK<float> *k) { *k = make_k<float>(c, 0.0, 0.0); }
+
+cudaError_t launch_mhd_batch(const BatchHeader *hdr, const BatchMhd *items, int sub, unsigned *err, int grid,
+                             cudaStream_t s) {
+    mhd_batch_kernel<<<grid, MB_TX * MB_TY, MbCfg::SMEM, s>>>(hdr, items, (float)RK_A[sub], (float)RK_B[sub],
+                                                              sub == 0 ? 1 : 0, sub == 2 ? 1 : 0, err);
+    return cudaGetLastError();
 }
 
 }  // namespace stn

@@ -10,6 +10,8 @@
 // multiply-add sequence j = -r..r as a one-sweep-per-launch kernel would use, so the result
 // is bit-identical to sweeping once per launch.  int32 arithmetic is done in uint32
 // (modulo 2^32); floating point uses fused multiply-add in order j = -r..r.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace stn {
@@ -35,18 +37,18 @@ template <> __device__ __forceinline__ uint32_t mac<uint32_t>(uint32_t acc, uint
 
 template <typename T> struct XCoef { T g[9]; };
 
+// One chunk of XC_CHUNK outputs: stage, sweep in shared memory, write (+ images).
 template <typename T, int R>
-__global__ void __launch_bounds__(XC_THREADS)
-xcorr_kernel(const T *__restrict__ in, T *__restrict__ out, Geom geo, XCoef<T> cf, int sweeps,
-             int periodic, int images) {
+__device__ __forceinline__ void xcorr_chunk(const T *__restrict__ in, T *__restrict__ out, const Geom &geo,
+                                            const XCoef<T> &cf, int sweeps, int periodic, int images, int chunk,
+                                            unsigned char *smem_raw) {
     using A = typename XAcc<T>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int H = sweeps * R;
     const int W = XC_CHUNK + 2 * H;
     A *buf0 = reinterpret_cast<A *>(smem_raw);
     A *buf1 = buf0 + W;
     const int64_t n = geo.n[0];
-    const int64_t c0 = (int64_t)blockIdx.x * XC_CHUNK;
+    const int64_t c0 = (int64_t)chunk * XC_CHUNK;
     const T *inx = in + geo.off[0];  // interior element 0
     T *outx = out + geo.off[0];
 
@@ -120,6 +122,14 @@ xcorr_kernel(const T *__restrict__ in, T *__restrict__ out, Geom geo, XCoef<T> c
 }
 
 template <typename T, int R>
+__global__ void __launch_bounds__(XC_THREADS)
+xcorr_kernel(const T *__restrict__ in, T *__restrict__ out, Geom geo, XCoef<T> cf, int sweeps, int periodic,
+             int images) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    xcorr_chunk<T, R>(in, out, geo, cf, sweeps, periodic, images, blockIdx.x, smem_raw);
+}
+
+template <typename T, int R>
 static cudaError_t run(const void *in, void *out, const Geom &g, const void *coeffs, int sweeps,
                        bool periodic, bool images, cudaStream_t s) {
     using A = typename XAcc<T>::type;
@@ -160,6 +170,51 @@ cudaError_t launch_xcorr(int dtype, int r, const void *in, void *out, const Geom
     case 2: return run_r<float>(r, in, out, g, coeffs, sweeps, periodic, images, s);
     default: return cudaErrorInvalidValue;
     }
+}
+
+// ------------------------------------------------------------------ batched (serving)
+
+// FP32, radius 3, one periodic sweep per item, with periodic images.
+__global__ void __launch_bounds__(XC_THREADS)
+xcorr_batch_kernel(const BatchHeader *hdr, const BatchXcorr *items) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int total = hdr->xc_ctas, n = hdr->n_xc;
+    for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (items[mid].cta_begin <= vb) lo = mid; else hi = mid - 1;
+        }
+        const BatchXcorr &it = items[lo];
+        XCoef<float> cf{};
+        for (int j = 0; j < 7; ++j) cf.g[j] = it.w[j];
+        const Geom g = it.g;
+        xcorr_chunk<float, 3>(it.in, it.out, g, cf, 1, 1, 1, vb - it.cta_begin, smem_raw);
+        __syncthreads();
+    }
+}
+
+static size_t xcorr_batch_smem() { return 2 * sizeof(float) * (XC_CHUNK + 2 * 3); }
+
+int xcorr_batch_grid() {
+    static int grid[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return 152;
+    if (!grid[dev]) {
+        int o = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, xcorr_batch_kernel, XC_THREADS, xcorr_batch_smem());
+        grid[dev] = std::max(o, 1) * device_sms();
+    }
+    return grid[dev];
+}
+
+int xcorr_batch_chunk() { return XC_CHUNK; }
+
+cudaError_t launch_xcorr_batch(const BatchHeader *hdr, const BatchXcorr *items, unsigned *err, int grid,
+                               cudaStream_t s) {
+    (void)err;
+    xcorr_batch_kernel<<<grid, XC_THREADS, xcorr_batch_smem(), s>>>(hdr, items);
+    return cudaGetLastError();
 }
 
 }  // namespace stn
