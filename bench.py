@@ -270,6 +270,81 @@ def xcorr_job(L, synth, dtype, warmup, reps, stream):
     return {"ms_job": ms}
 
 
+def run_serving_leg(n_requests=1024, load=0.7, fp64_subset=96):
+    """Serving configuration: 1024 requests (log-uniform 32^3..192^3, mixed kinds, 10-50
+    steps, FP32) through the continuous-batching server under a 120 GB budget.
+
+    1. saturation: every request arrives at t = 0; capacity = requests / wall time;
+    2. open loop: Poisson arrivals at `load` x capacity; p50/p99 arrival-to-result latency
+       and aggregate throughput;
+    3. the plain per-grid FP64 path (one plan per request, in arrival order) on the first
+       `fp64_subset` requests: service times measured, FIFO latencies under the same arrival
+       process computed from them; speedup = batched / per-grid throughput at equal work."""
+    import torch
+
+    from paper_2406_08923_gb300 import _lib as L
+    from paper_2406_08923_gb300 import serving
+    t_gen = time.perf_counter()
+    templates = serving.Templates(pinned=True)
+    reqs = serving.make_requests(n_requests)
+    for r in reqs:
+        templates.get(r.kind, r.n)
+    t_gen = time.perf_counter() - t_gen
+    work = sum(r.work() for r in reqs)
+    # warm-up: a few small requests (module load, graph instantiation, pool growth)
+    warm = [serving.Request(i, k, 32, 2) for i, k in enumerate(serving.KINDS)]
+    serving.serve(warm, templates)
+    # 1. saturation
+    for r in reqs:
+        r.arrival = 0.0
+    wall_sat, peak_sat, _ = serving.serve(reqs, templates)
+    cap_rps = n_requests / wall_sat
+    # 2. open loop at load x capacity
+    serving.poisson_arrivals(reqs, load * cap_rps)
+    wall, peak, updates = serving.serve(reqs, templates)
+    lat = serving.latency_stats(reqs)
+    # 3. per-grid FP64 path on a subset, FIFO latencies under the same arrivals
+    sub = sorted(reqs, key=lambda r: r.arrival)[:fp64_subset]
+    arr = [r.arrival for r in sub]
+    serving.serve_per_grid(sub[:2], templates, storage=L.STENCIL_F64)  # warm-up
+    t0 = time.perf_counter()
+    service = []
+    for r in sub:
+        t1 = time.perf_counter()
+        serving.serve_per_grid([r], templates, storage=L.STENCIL_F64)
+        service.append(time.perf_counter() - t1)
+    wall64 = time.perf_counter() - t0
+    done, lat64 = 0.0, []
+    for a, sv in zip(arr, service):
+        start = max(a, done)
+        done = start + sv
+        lat64.append(done - a)
+    work_sub = sum(r.work() for r in sub)
+    thr = updates / wall / 1e6
+    thr64 = work_sub / wall64 / 1e6
+    torch.cuda.synchronize()
+    return {
+        "requests": n_requests, "mix": "n log-uniform 32..192 (multiples of 8), kinds uniform {xcorr1d n^3, heat3d, mhd8}, "
+                                        "10-50 steps, FP32, Poisson arrivals",
+        "budget_gb": 120, "template_gen_s": round(t_gen, 1),
+        "work_gcell_updates": round(work / 1e9, 2),
+        "saturation": {"wall_s": round(wall_sat, 3), "requests_per_s": round(cap_rps, 1),
+                       "mcell_updates_per_s": round(work / wall_sat / 1e6, 1), "peak_gb": round(peak_sat / 1e9, 2)},
+        "open_loop": {"load": load, "rate_rps": round(load * cap_rps, 1), "wall_s": round(wall, 3),
+                      "mcell_updates_per_s": round(thr, 1), "p50_ms": round(lat["p50_ms"], 2),
+                      "p99_ms": round(lat["p99_ms"], 2), "peak_gb": round(peak / 1e9, 2)},
+        "per_grid_fp64_subset": {"requests": len(sub), "wall_s": round(wall64, 3),
+                                 "mcell_updates_per_s": round(thr64, 1),
+                                 "p50_ms": round(float(np.percentile(lat64, 50) * 1e3), 2),
+                                 "p99_ms": round(float(np.percentile(lat64, 99) * 1e3), 2)},
+        # capacity ratio: saturated batched throughput vs back-to-back per-grid FP64 throughput
+        "speedup_vs_per_grid_fp64": round(work / wall_sat / 1e6 / thr64, 2),
+        "speedup_open_loop_throughput": round(thr / thr64, 2),
+        "accuracy": "FP32 results within 1e-5 of the FP64 oracle and bit-identical alone vs in the mix "
+                    "(tests/test_gpu_serving.py)",
+    }
+
+
 def cpu_baseline(seconds_target=10.0):
     """The FP64 oracle, as it stands, on the host cores: a bounded sample of the headline
     workload (256^3 heat field, a number of Euler steps chosen to take ~10 s)."""
@@ -392,6 +467,8 @@ def run_ours(args):
     extras = {}
     if not args.no_extras:
         extras = run_extras(L, synth, stream, hbm_peak, args)
+        if world == 1:
+            extras["serving"] = run_serving_leg()
 
     line = {
         "metric": "heat3d_256_fp64_mcell_updates_per_s",
@@ -528,6 +605,7 @@ def main():
                     help="run one workload only (no autotune), e.g. for an ncu capture")
     ap.add_argument("--n", type=int, default=None, help="grid size for --case")
     ap.add_argument("--variant", type=int, default=0, help="kernel variant for --case")
+    ap.add_argument("--serving", action="store_true", help="serving configuration only (one JSON line)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -535,6 +613,10 @@ def main():
         return run_reference(args)
     if args.case:
         return run_case(args)
+    if args.serving:
+        print(json.dumps({"metric": "serving_p50_p99_latency_and_mcell_updates_per_s", "serving": run_serving_leg()}),
+              flush=True)
+        return 0
     return run_ours(args)
 
 

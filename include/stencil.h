@@ -262,7 +262,7 @@ typedef struct stencil_server *stencil_server_t;
 
 typedef struct stencil_request {
     stencil_kind kind;     /* XCORR (1D, dims[0] cells), DIFFUSION or MHD8 (3D) */
-    int64_t dims[3];       /* interior extents, each 7 .. 2^20 */
+    int64_t dims[3];       /* interior extents: 1D 7 .. 2^31-16; 3D each 7 .. 2^15 */
     int nsteps;            /* sweeps / Euler steps / RK3 steps, >= 1 */
     double coeffs[7];      /* XCORR: weights g_{-3..3}; ignored otherwise */
     stencil_params params; /* DIFFUSION and MHD8 constants (as for stencil_create) */

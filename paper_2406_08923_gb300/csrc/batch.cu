@@ -133,6 +133,11 @@ struct stencil_server {
     unsigned char *dev_tab = nullptr;
     unsigned *err = nullptr;
     int grid_heat = 0, grid_mhd = 0, grid_xc = 0;
+    bool own_stream = false;
+    // one captured graph per pinned table buffer: table upload + every batched launch
+    cudaGraph_t graph[2] = {};  // kept alive: exec node updates refer to its nodes
+    cudaGraphExec_t exec[2] = {};
+    cudaGraphNode_t copy_node[2] = {};
     std::string detail;
 };
 
@@ -238,6 +243,59 @@ stencil_status finish(stencil_server_t s, Req *r) {
     return STENCIL_OK;
 }
 
+struct TableLayout {
+    size_t off_heat, off_mhd, mhd_stride, off_xc;
+};
+
+TableLayout table_layout(int max_active) {
+    TableLayout t;
+    t.off_heat = up256(sizeof(BatchHeader));
+    t.off_mhd = t.off_heat + up256(sizeof(BatchHeat) * max_active);
+    t.mhd_stride = up256(sizeof(BatchMhd) * max_active);
+    t.off_xc = t.off_mhd + 3 * t.mhd_stride;
+    return t;
+}
+
+// Capture, for each pinned table buffer, one iteration: table upload followed by the
+// persistent batched launches of every kind.  The grids are occupancy-sized and the kernels
+// read their work counts from the uploaded table, so one graph serves every batch; only the
+// upload size changes between replays.
+stencil_status capture_graphs(stencil_server_t s) {
+    const TableLayout t = table_layout(s->max_active);
+    const BatchHeader *dhdr = reinterpret_cast<const BatchHeader *>(s->dev_tab);
+    for (int i = 0; i < 2; ++i) {
+        cudaGraph_t graph = nullptr;
+        SCK(s, cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        cudaError_t e = cudaMemcpyAsync(s->dev_tab, s->host_tab[i], s->table_bytes, cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess)
+            e = launch_diffusion_batch(dhdr, reinterpret_cast<const BatchHeat *>(s->dev_tab + t.off_heat), s->err,
+                                       s->grid_heat, s->stream);
+        for (int sub = 0; sub < 3 && e == cudaSuccess; ++sub)
+            e = launch_mhd_batch(dhdr, reinterpret_cast<const BatchMhd *>(s->dev_tab + t.off_mhd + sub * t.mhd_stride),
+                                 sub, s->err, s->grid_mhd, s->stream);
+        if (e == cudaSuccess)
+            e = launch_xcorr_batch(dhdr, reinterpret_cast<const BatchXcorr *>(s->dev_tab + t.off_xc), s->err,
+                                   s->grid_xc, s->stream);
+        cudaError_t e2 = cudaStreamEndCapture(s->stream, &graph);
+        if (e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return scuda(s, e, "capture of the batched iteration");
+        }
+        SCK(s, e2, "end capture");
+        // find the memcpy node (the graph's only root)
+        size_t nroot = 0;
+        e = cudaGraphGetRootNodes(graph, nullptr, &nroot);
+        cudaGraphNode_t root = nullptr;
+        if (e == cudaSuccess && nroot == 1) e = cudaGraphGetRootNodes(graph, &root, &nroot);
+        if (e == cudaSuccess && nroot != 1) e = cudaErrorInvalidValue;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&s->exec[i], graph, 0);
+        s->graph[i] = graph;
+        SCK(s, e, "graph instantiation");
+        s->copy_node[i] = root;
+    }
+    return STENCIL_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -253,6 +311,13 @@ stencil_status stencil_server_create(int64_t hbm_budget_bytes, int max_active, v
     s->budget = hbm_budget_bytes;
     s->max_active = max_active;
     s->stream = (cudaStream_t)stream;
+    if (!s->stream) {  // graphs cannot be captured on the legacy default stream
+        if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete s;
+            return sfail(nullptr, STENCIL_ECUDA, "cudaStreamCreate failed");
+        }
+        s->own_stream = true;
+    }
     cudaError_t e = cudaGetDevice(&s->device);
     if (e == cudaSuccess) e = cudaDeviceGetDefaultMemPool(&s->pool, s->device);
     if (e == cudaSuccess) {
@@ -275,6 +340,12 @@ stencil_status stencil_server_create(int64_t hbm_budget_bytes, int max_active, v
     s->grid_heat = diffusion_batch_grid();
     s->grid_mhd = mhd_batch_grid();
     s->grid_xc = xcorr_batch_grid();
+    stencil_status gst = capture_graphs(s);
+    if (gst != STENCIL_OK) {
+        g_server_detail = s->detail;
+        stencil_server_destroy(s);
+        return gst;
+    }
     *out = s;
     return STENCIL_OK;
 }
@@ -293,7 +364,12 @@ void stencil_server_destroy(stencil_server_t s) {
         if (s->host_tab[i]) cudaFreeHost(s->host_tab[i]);
         if (s->tab_ev[i]) cudaEventDestroy(s->tab_ev[i]);
     }
+    for (int i = 0; i < 2; ++i) {
+        if (s->exec[i]) cudaGraphExecDestroy(s->exec[i]);
+        if (s->graph[i]) cudaGraphDestroy(s->graph[i]);
+    }
     if (s->dev_tab) cudaFree(s->dev_tab);
+    if (s->own_stream) cudaStreamDestroy(s->stream);
     if (s->err) cudaFree(s->err);
     delete s;
 }
@@ -314,10 +390,12 @@ stencil_status stencil_server_submit(stencil_server_t s, const stencil_request *
     default: delete r; return sfail(s, STENCIL_EINVAL, "unknown kind");
     }
     if (req->nsteps < 1) { delete r; return sfail(s, STENCIL_EINVAL, "nsteps must be >= 1"); }
+    const int64_t dmax = ndim == 1 ? ((int64_t)1 << 31) - 16 : ((int64_t)1 << 15);
     for (int a = 0; a < ndim; ++a)
-        if (req->dims[a] < 2 * R + 1 || req->dims[a] > (1 << 20)) {
+        if (req->dims[a] < 2 * R + 1 || req->dims[a] > dmax) {
             delete r;
-            return sfail(s, STENCIL_EINVAL, "dims must be in 7 .. 2^20 (periodic, radius 3)");
+            return sfail(s, STENCIL_EINVAL, ndim == 1 ? "1D extent must be in 7 .. 2^31-16 (periodic, radius 3)"
+                                                      : "3D extents must be in 7 .. 2^15 (periodic, radius 3)");
         }
     for (int q = 0; q < r->nf; ++q)
         if (!host_in[q] || !host_out[q]) { delete r; return sfail(s, STENCIL_EINVAL, "host field pointer is NULL"); }
@@ -482,27 +560,17 @@ stencil_status stencil_server_progress(stencil_server_t s, int *n_pending, int *
                 hdr->xc_ctas += r->tiles[0];
             }
         }
-        // upload the whole table region that is in use (header + every used item range)
+        // upload the table region in use (header + every used item range), then every batched
+        // launch, as one replay of the captured iteration graph
         const size_t used_bytes = hdr->n_xc ? off_xc + sizeof(BatchXcorr) * hdr->n_xc
                                   : hdr->n_mhd ? off_mhd + 2 * mhd_stride + sizeof(BatchMhd) * hdr->n_mhd
                                   : off_heat + sizeof(BatchHeat) * hdr->n_heat;
-        SCK(s, cudaMemcpyAsync(s->dev_tab, h, used_bytes, cudaMemcpyHostToDevice, st), "table upload");
+        SCK(s, cudaGraphExecMemcpyNodeSetParams1D(s->exec[i], s->copy_node[i], s->dev_tab, h, used_bytes,
+                                                  cudaMemcpyHostToDevice),
+            "table upload size");
+        SCK(s, cudaGraphLaunch(s->exec[i], st), "batched iteration graph");
         SCK(s, cudaEventRecord(s->tab_ev[i], st), "table event");
         s->tab_i ^= 1;
-        const BatchHeader *dhdr = reinterpret_cast<const BatchHeader *>(s->dev_tab);
-        if (hdr->n_heat)
-            SCK(s, launch_diffusion_batch(dhdr, reinterpret_cast<const BatchHeat *>(s->dev_tab + off_heat), s->err,
-                                          std::min(s->grid_heat, hdr->heat_ctas), st),
-                "batched heat launch");
-        if (hdr->n_mhd)
-            for (int sub = 0; sub < 3; ++sub)
-                SCK(s, launch_mhd_batch(dhdr, reinterpret_cast<const BatchMhd *>(s->dev_tab + off_mhd + sub * mhd_stride),
-                                        sub, s->err, std::min(s->grid_mhd, hdr->mhd_ctas), st),
-                    "batched MHD launch");
-        if (hdr->n_xc)
-            SCK(s, launch_xcorr_batch(dhdr, reinterpret_cast<const BatchXcorr *>(s->dev_tab + off_xc), s->err,
-                                      std::min(s->grid_xc, hdr->xc_ctas), st),
-                "batched xcorr launch");
         // 4. advance the bookkeeping; queue copy-back of finished problems
         for (size_t a = 0; a < s->active.size();) {
             Req *r = s->active[a];
