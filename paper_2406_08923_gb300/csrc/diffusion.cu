@@ -3,6 +3,9 @@
 // The Euler update and the three axis Laplacians fold into one 19-point cross-correlation
 // (Eqs. 5 and 7): f' = g0 f + sum_axes sum_{a=1..3} g_{axis,a} (f(+a) + f(-a)).
 //
+// This file holds the FP64 kernel family (FP64 on GB300 is bound by the FP64 pipe, ~1/60 of
+// the FP32 rate); FP32 has its own issue-lean kernel in diffusion_f32.cu.
+//
 // GB300 design (2.5D z-streaming):
 //   * A CTA owns a TX x TY tile of the xy-plane (TX = 32 VX, TY = BY RY) and marches along z
 //     over a chunk of planes (chunk length chosen by the host from the kernel's occupancy so
@@ -10,10 +13,9 @@
 //     (TX + 8) x (TY + 6) arrives by one TMA load (cp.async.bulk.tensor.3d) in a ring of
 //     NSLOT shared-memory slots, completion on one mbarrier per slot; loads run NSLOT - 3
 //     planes ahead of the compute.
-//   * A thread owns VX = 2 VP consecutive x cells in RY rows and computes them as VP pairs:
-//     FP32 pairs use Blackwell's packed FP32x2 FMA/ADD (one instruction per two cells).
-//     Neighbours at even x offsets and all y/z neighbours are naturally aligned pairs; the
-//     odd x offsets take two scalar adds.  Shared memory is read with 16-byte vector loads.
+//   * A thread owns VX = 2 VP consecutive x cells in RY rows and computes them as VP pairs
+//     (the pair template also admits FP32 with Blackwell's packed FP32x2 FMA/ADD).  Shared
+//     memory is read with 16-byte vector loads.
 //   * Each iteration computes ZB consecutive z planes (register blocking in z).  The
 //     z-columns (planes z-3..z+ZB+2) live in a register queue that shifts by ZB once per
 //     iteration, so z-neighbours cost no shared-memory traffic and the per-iteration work
@@ -431,33 +433,24 @@ static cudaError_t run(const CUtensorMap *map, void *out, const Geom &g, const D
     X(1, 4, 1, 2, 8, false)  \
     X(1, 8, 1, 1, 8, false)  \
     X(1, 4, 2, 2, 8, false)
-#define DIFF_VARIANTS_F32(X) \
-    X(2, 4, 2, 2, 8, true)   \
-    X(2, 8, 2, 2, 8, true)   \
-    X(2, 4, 4, 2, 8, true)   \
-    X(2, 4, 4, 1, 8, true)   \
-    X(1, 4, 2, 4, 16, true)  \
-    X(2, 8, 2, 1, 8, true)
-
 static const char *F64_NAMES[] = {"vx2_by8_ry1_zb2_s8", "vx2_by4_ry1_zb2_s8", "vx2_by8_ry1_zb1_s8",
                                   "vx2_by4_ry2_zb2_s8"};
-static const char *F32_NAMES[] = {"vx4_by4_ry2_zb2_s8_pk", "vx4_by8_ry2_zb2_s8_pk", "vx4_by4_ry4_zb2_s8_pk",
-                                  "vx4_by4_ry4_zb1_s8_pk", "vx2_by4_ry2_zb4_s16_pk", "vx4_by8_ry2_zb1_s8_pk"};
-
-int diffusion_num_variants(int dtype) { return dtype == 1 ? 4 : 6; }
+int diffusion_num_variants(int dtype) { return dtype == 1 ? 4 : diffusion_f32_num_variants(); }
 
 const char *diffusion_variant_name(int dtype, int v) {
+    if (dtype != 1) return diffusion_f32_variant_name(v);
     if (v < 0 || v >= diffusion_num_variants(dtype)) return "?";
-    return dtype == 1 ? F64_NAMES[v] : F32_NAMES[v];
+    return F64_NAMES[v];
 }
 
 void diffusion_box(int dtype, int v, int box[3]) {
+    if (dtype != 1) return diffusion_f32_box(v, box);
     int i = 0;
     auto put = [&](int vp, int by, int ry) {
         if (i++ == v) { box[0] = 64 * vp + 8; box[1] = by * ry + 2 * R6; box[2] = 1; }
     };
 #define X(VP, BY, RY, ZB, NS, PK) put(VP, BY, RY);
-    if (dtype == 1) { DIFF_VARIANTS_F64(X) } else { DIFF_VARIANTS_F32(X) }
+    DIFF_VARIANTS_F64(X)
 #undef X
 }
 
@@ -471,73 +464,10 @@ cudaError_t launch_diffusion(int dtype, const CUtensorMap *map, void *out, const
         using T = double;
         DIFF_VARIANTS_F64(X)
     } else if (dtype == 2) {
-        using T = float;
-        DIFF_VARIANTS_F32(X)
+        return launch_diffusion_f32(map, static_cast<float *>(out), g, c, images, err, s, variant);
     }
 #undef X
     return res;
-}
-
-// ------------------------------------------------------------------ batched (serving)
-
-// FP32, the tile shape of variant vx4_by4_ry2_zb2_s8_pk.
-constexpr int DB_VP = 2, DB_BY = 4, DB_RY = 2, DB_ZB = 2, DB_NSLOT = 8;
-using DbCfg = DiffCfg<float, DB_VP, DB_BY, DB_RY, DB_ZB, DB_NSLOT>;
-
-__global__ void __launch_bounds__(32 * DB_BY)
-diffusion_batch_kernel(const BatchHeader *hdr, const BatchHeat *items, unsigned *err) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    float *ring = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    __shared__ __align__(8) uint64_t full[DB_NSLOT];
-    const int total = hdr->heat_ctas, n = hdr->n_heat;
-    for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
-        int lo = 0, hi = n - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (items[mid].cta_begin <= vb) lo = mid; else hi = mid - 1;
-        }
-        const BatchHeat &it = items[lo];
-        int r = vb - it.cta_begin;
-        const int tx = r % it.tiles_x;
-        r /= it.tiles_x;
-        const int ty = r % it.tiles_y, tz = r / it.tiles_y;
-        DC<float> c;
-        c.g0 = it.g0;
-        for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b) c.ga[a][b] = it.ga[a][b];
-        const Geom g = it.g;
-        const bool ok = diffusion_tile<float, DB_VP, DB_BY, DB_RY, DB_ZB, DB_NSLOT, true>(
-            it.map, it.out, g, c, tx, ty, tz, it.zc, 1, err, ring, full);
-        __syncthreads();
-        if (!ok) return;
-    }
-}
-
-int diffusion_batch_grid() {
-    static int grid[64] = {};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return 152;
-    if (!grid[dev]) {
-        cudaFuncSetAttribute(diffusion_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DbCfg::SMEM);
-        int o = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, diffusion_batch_kernel, 32 * DB_BY, DbCfg::SMEM);
-        grid[dev] = std::max(o, 1) * device_sms();
-    }
-    return grid[dev];
-}
-
-void diffusion_batch_tile(int *tx, int *ty, int box[3]) {
-    *tx = DbCfg::TX;
-    *ty = DbCfg::TY;
-    box[0] = DbCfg::TXP;
-    box[1] = DbCfg::ROWS;
-    box[2] = 1;
-}
-
-cudaError_t launch_diffusion_batch(const BatchHeader *hdr, const BatchHeat *items, unsigned *err, int grid,
-                                   cudaStream_t s) {
-    diffusion_batch_kernel<<<grid, 32 * DB_BY, DbCfg::SMEM, s>>>(hdr, items, err);
-    return cudaGetLastError();
 }
 
 }  // namespace stn

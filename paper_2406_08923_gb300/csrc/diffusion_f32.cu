@@ -1,0 +1,427 @@
+// diffusion_f32.cu -- FP32 forward-Euler step of the 3D heat equation (Sec. 3.2, Eqs. 4-7).
+//
+// The Euler update and the three axis Laplacians fold into one 19-point cross-correlation
+// (Eqs. 5 and 7): f' = g0 f + sum_axes sum_{a=1..3} g_{axis,a} (f(+a) + f(-a)).
+//
+// FP32 is bandwidth-class work on GB300 (8 B per cell-update against ~10 packed FP32
+// instructions), so this kernel is built to spend as few issue slots per cell as possible:
+//   * 2.5D z-streaming as in the FP64 kernel: a CTA owns a 128 x (BY RY) tile of the
+//     xy-plane and marches along a chunk of z; each padded plane tile (136 x (BY RY + 6))
+//     arrives by one TMA load into a ring of NSLOT shared-memory slots (one mbarrier each).
+//   * A thread owns 4 consecutive x cells (one float4) in RY rows.  The z-columns of its cells
+//     (planes z-3 .. z+ZB+2) live in a register queue.  The queue is never shifted: the
+//     z-loop is unrolled over the queue's period and each unrolled iteration addresses the
+//     queue with a compile-time rotation, so advancing by ZB planes costs no moves.
+//   * The centre row of a cell comes from the queue; shared memory supplies only the six y
+//     rows around the thread's RY rows (shared by those rows) and two 16-byte x-neighbour
+//     loads per row.  Pairs of cells use Blackwell's packed FP32x2 FMA/ADD.
+//   * Stores are one 16-byte vector per row.  Periodic images (Eq. 2) cost one predicated
+//     vector store on the two x-face lanes (XVEC: nx a multiple of 4, the 4th element lands in
+//     the row padding) or per-cell scalar stores otherwise; y- and z-images are behind one
+//     test that is uniform per warp row and per plane.  Tiles that overhang the interior
+//     store element-wise through an out-of-line path.
+//   * Waits are bounded (globaltimer); on expiry the CTA records ERR_TIMEOUT, drains its
+//     in-flight TMA loads (again bounded) and returns.
+// The multiply-add order per cell is the same as the FP64 kernel's (x, y, z pairs of offset
+// 1, then 2, then 3), so results do not depend on the variant.
+#include <algorithm>
+#include <type_traits>
+
+#include "internal.h"
+
+namespace stn {
+namespace {
+
+constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
+
+struct Coef32 {
+    float g0;
+    float ga[3][3];  // [axis][a-1]
+};
+
+template <int BY, int RY, int ZB, int NSLOT>
+struct H32 {
+    static constexpr int TX = 128, HX = 4, TXP = TX + 2 * HX;
+    static constexpr int TY = BY * RY, ROWS = TY + 2 * R6;
+    static constexpr int SLOT = ((TXP * ROWS * 4 + 127) / 128) * 128 / 4;  // floats, 128 B aligned
+    static constexpr uint32_t BOX_BYTES = TXP * ROWS * 4;
+    static constexpr size_t SMEM = (size_t)NSLOT * SLOT * 4 + 128;
+    static constexpr int S = ZB + 2 * R6;       // queue length (planes)
+    static constexpr int U = S / gcd_c(S, ZB);  // iterations per queue period
+    static_assert(NSLOT >= ZB + R6 + 1, "ring: ZB + 3 planes in use plus one refill");
+    static_assert((NSLOT & (NSLOT - 1)) == 0, "ring depth is a power of two (slot = j & (NSLOT-1))");
+    static_assert(ROWS <= 256, "TMA box extents are limited to 256");
+    static_assert(U <= 4, "the z-loop is unrolled over one queue period");
+};
+
+__device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void stg4(float *p, const float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+
+// Element-wise store of a (possibly overhanging) group of 4 cells with all periodic images.
+__device__ __noinline__ void store4_bounded(float *out, const Geom &g, int images, int x, int y, int z, float4 v) {
+    const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        if (x + u < g.n[0] && y < g.n[1]) store_with_images(out, g, R6, images != 0, x + u, y, z, e[u]);
+}
+
+// One xy-tile of one z-chunk.  `map` may point at a __grid_constant__ parameter or at a
+// descriptor in global memory (batched launches).  Returns false if a bounded wait expired.
+template <int BY, int RY, int ZB, int NSLOT, bool XVEC>
+__device__ __forceinline__ bool heat32_tile(const CUtensorMap *map, float *__restrict__ out, const Geom &g,
+                                            const Coef32 &c, int tile_x, int tile_y, int tile_z, int zc, int images,
+                                            unsigned *err, float *ring, uint64_t *full) {
+    using Cfg = H32<BY, RY, ZB, NSLOT>;
+    constexpr int TXP = Cfg::TXP, S = Cfg::S;
+    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+    const int x0 = tile_x * Cfg::TX, y0 = tile_y * Cfg::TY, zc0 = tile_z * zc;
+    const int nx = (int)g.n[0], ny = (int)g.n[1], nz = (int)g.n[2];
+    const int count = min(nz, zc0 + zc) - zc0;
+    const int nplanes = count + 2 * R6;  // planes zc0-3 .. zc0+count+2
+    const int x = x0 + 4 * lane, yb = y0 + wy * RY;
+
+    if (threadIdx.x == 0) {
+        tma_prefetch_desc(map);
+        for (int s = 0; s < NSLOT; ++s) mbar_init(&full[s], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const int bx = (int)g.off[0] + x0 - Cfg::HX, by0 = (int)g.off[1] + y0 - R6, bz0 = (int)g.off[2] + zc0 - R6;
+    int issued = 0;
+    auto issue = [&](int j) {  // plane j (0-based from zc0-3) into its ring slot
+        const int s = j & (NSLOT - 1);
+        mbar_arrive_expect_tx(&full[s], Cfg::BOX_BYTES);
+        tma_load_3d(ring + s * Cfg::SLOT, map, &full[s], bx, by0, bz0 + j);
+    };
+    auto slot = [&](int j) { return ring + (j & (NSLOT - 1)) * Cfg::SLOT; };
+    auto parity = [](int j) { return ((unsigned)j / (unsigned)NSLOT) & 1u; };
+    if (threadIdx.x == 0)
+        for (; issued < NSLOT && issued < nplanes; ++issued) issue(issued);
+
+    // float offset of (row 0 of this thread, first cell) inside a slot
+    const int own = (wy * RY + R6) * TXP + Cfg::HX + 4 * lane;
+    const float2 G0 = make_float2(c.g0, c.g0);
+    float2 GA[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) GA[a][b] = make_float2(c.ga[a][b], c.ga[a][b]);
+
+    // z queue: logical entry k of an iteration with rotation ROT is Q[(ROT + k) % S]; entry k
+    // holds plane (first output plane of the iteration) - 3 + k.
+    float4 Q[S][RY];
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < 2 * R6; ++j) {  // prologue: planes zc0-3 .. zc0+2
+        ok = ok && mbar_wait_bounded(&full[j & (NSLOT - 1)], parity(j));
+        const float *sp = slot(j) + own;
+#pragma unroll
+        for (int r = 0; r < RY; ++r) Q[j][r] = ok ? lds4(sp + r * TXP) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    bool bad = __syncthreads_or(!ok);
+    // planes 0..2 are never read from shared memory again: refill their slots
+    if (!bad && threadIdx.x == 0)
+        for (; issued < NSLOT + R6 && issued < nplanes; ++issued) issue(issued);
+
+    // Store targets.  x-images: lanes whose cells lie within 4 (XVEC) or 3 of an x face.
+    const bool full_tile = x + 4 <= nx && yb + RY <= ny;
+    int xs = 0, xmask = 0;
+    int ys[RY];
+#pragma unroll
+    for (int r = 0; r < RY; ++r) ys[r] = 0;
+    if (images) {
+        if (XVEC) {
+            xs = x < 4 ? nx : (x >= nx - 4 ? -nx : 0);
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (x + u < R6) { xmask |= 1 << u; xs = nx; }
+                else if (x + u >= nx - R6 && x + u < nx) { xmask |= 1 << u; xs = -nx; }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < RY; ++r) ys[r] = (yb + r < R6) ? ny : (yb + r >= ny - R6 ? -ny : 0);
+    }
+    const bool xi = XVEC ? xs != 0 : xmask != 0;
+    const int pitch_y = (int)g.pad[0];
+    const int64_t pitch_z = g.pad[0] * g.pad[1];
+    float *optr = out + g.idx(x, yb, zc0);
+    auto put = [&](float *p, const float4 v) {  // one row of 4 cells and its x-image
+        stg4(p, v);
+        if (XVEC) {
+            if (xi) stg4(p + xs, v);
+        } else if (xi) {
+            if (xmask & 1) p[xs] = v.x;
+            if (xmask & 2) p[1 + xs] = v.y;
+            if (xmask & 4) p[2 + xs] = v.z;
+            if (xmask & 8) p[3 + xs] = v.w;
+        }
+    };
+
+    auto iter = [&](auto rot_c, int m) {
+        constexpr int ROT = decltype(rot_c)::value;
+        if (bad || m >= count) return;
+        // leading planes j = m+6 .. m+5+ZB enter the queue at logical entries 6 .. 5+ZB
+#pragma unroll
+        for (int b = 0; b < ZB; ++b) {
+            const int jl = m + 2 * R6 + b;
+            if (jl < nplanes) {
+                ok = ok && mbar_wait_bounded(&full[jl & (NSLOT - 1)], parity(jl));
+                const float *lp = slot(jl) + own;
+#pragma unroll
+                for (int r = 0; r < RY; ++r) Q[(ROT + 2 * R6 + b) % S][r] = lds4(lp + r * TXP);
+            }
+        }
+        if (ok) {
+#pragma unroll
+            for (int b = 0; b < ZB; ++b) {
+                if (m + b < count) {
+                    const float *cp = slot(m + b + R6) + own;
+                    float4 Yn[3], Yp[3];  // rows -1, -2, -3 and RY, RY+1, RY+2
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        Yn[a] = lds4(cp - (a + 1) * TXP);
+                        Yp[a] = lds4(cp + (RY + a) * TXP);
+                    }
+                    auto row = [&](int d) -> float4 {  // row d of the centre plane
+                        return d < 0 ? Yn[-d - 1] : (d >= RY ? Yp[d - RY] : Q[(ROT + b + R6) % S][d]);
+                    };
+                    float4 res[RY];
+#pragma unroll
+                    for (int r = 0; r < RY; ++r) {
+                        const float4 C = Q[(ROT + b + R6) % S][r];
+                        const float4 L = lds4(cp + r * TXP - 4), R = lds4(cp + r * TXP + 4);
+                        // x pairs: even offsets are aligned pairs, odd offsets two scalar adds
+                        float2 sx[2][3], sy[2][3], sz[2][3];
+                        sx[0][0] = make_float2(C.y + L.w, C.z + C.x);
+                        sx[0][1] = __fadd2_rn(make_float2(C.z, C.w), make_float2(L.z, L.w));
+                        sx[0][2] = make_float2(C.w + L.y, R.x + L.z);
+                        sx[1][0] = make_float2(C.w + C.y, R.x + C.z);
+                        sx[1][1] = __fadd2_rn(make_float2(R.x, R.y), make_float2(C.x, C.y));
+                        sx[1][2] = make_float2(R.y + L.w, R.z + C.x);
+#pragma unroll
+                        for (int a = 1; a <= 3; ++a) {
+                            const float4 yp = row(r + a), ym = row(r - a);
+                            const float4 zp = Q[(ROT + b + R6 + a) % S][r], zm = Q[(ROT + b + R6 - a) % S][r];
+                            sy[0][a - 1] = __fadd2_rn(make_float2(yp.x, yp.y), make_float2(ym.x, ym.y));
+                            sy[1][a - 1] = __fadd2_rn(make_float2(yp.z, yp.w), make_float2(ym.z, ym.w));
+                            sz[0][a - 1] = __fadd2_rn(make_float2(zp.x, zp.y), make_float2(zm.x, zm.y));
+                            sz[1][a - 1] = __fadd2_rn(make_float2(zp.z, zp.w), make_float2(zm.z, zm.w));
+                        }
+                        float2 o[2];
+#pragma unroll
+                        for (int p = 0; p < 2; ++p) {
+                            float2 acc = __fmul2_rn(G0, p ? make_float2(C.z, C.w) : make_float2(C.x, C.y));
+#pragma unroll
+                            for (int a = 0; a < 3; ++a) {
+                                acc = __ffma2_rn(GA[0][a], sx[p][a], acc);
+                                acc = __ffma2_rn(GA[1][a], sy[p][a], acc);
+                                acc = __ffma2_rn(GA[2][a], sz[p][a], acc);
+                            }
+                            o[p] = acc;
+                        }
+                        res[r] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+                    }
+                    const int z = zc0 + m + b;
+                    const int zs = images ? (z < R6 ? nz : (z >= nz - R6 ? -nz : 0)) : 0;
+                    float *op = optr + b * pitch_z;
+                    if (full_tile) {
+#pragma unroll
+                        for (int r = 0; r < RY; ++r) {
+                            float *p = op + r * pitch_y;
+                            put(p, res[r]);
+                            if (ys[r] | zs) {  // y- and z-images: uniform per warp row / per plane
+                                const int64_t dy = (int64_t)ys[r] * pitch_y, dz = (int64_t)zs * pitch_z;
+                                if (ys[r]) put(p + dy, res[r]);
+                                if (zs) put(p + dz, res[r]);
+                                if (ys[r] && zs) put(p + dy + dz, res[r]);
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int r = 0; r < RY; ++r) store4_bounded(out, g, images, x, yb + r, z, res[r]);
+                    }
+                }
+            }
+        }
+        optr += ZB * pitch_z;
+        bad = __syncthreads_or(!ok);
+        // planes j < m + ZB + 3 are retired: refill the ring up to NSLOT planes ahead
+        if (!bad && threadIdx.x == 0) {
+            const int lim = min(nplanes, m + ZB + R6 + NSLOT);
+            for (; issued < lim; ++issued) issue(issued);
+        }
+    };
+    for (int m = 0; !bad && m < count; m += Cfg::U * ZB) {
+        iter(std::integral_constant<int, 0>{}, m);
+        if constexpr (Cfg::U > 1) iter(std::integral_constant<int, (1 * ZB) % S>{}, m + ZB);
+        if constexpr (Cfg::U > 2) iter(std::integral_constant<int, (2 * ZB) % S>{}, m + 2 * ZB);
+        if constexpr (Cfg::U > 3) iter(std::integral_constant<int, (3 * ZB) % S>{}, m + 3 * ZB);
+    }
+    if (bad && threadIdx.x == 0) {
+        atomicOr(err, ERR_TIMEOUT);
+        // drain loads still in flight before the CTA's shared memory is released
+        for (int j = max(0, issued - NSLOT); j < issued; ++j)
+            (void)mbar_wait_bounded(&full[j & (NSLOT - 1)], parity(j), 100000000ull);
+    }
+    return !bad;
+}
+
+template <int BY, int RY, int ZB, int NSLOT, int MINB, bool XVEC>
+__global__ void __launch_bounds__(32 * BY, MINB)
+heat32_kernel(const __grid_constant__ CUtensorMap map_in, float *__restrict__ out, Geom g, Coef32 c, int zc,
+              int images, unsigned *err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float *ring = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    __shared__ __align__(8) uint64_t full[NSLOT];
+    heat32_tile<BY, RY, ZB, NSLOT, XVEC>(&map_in, out, g, c, blockIdx.x, blockIdx.y, blockIdx.z, zc, images, err,
+                                         ring, full);
+}
+
+// Vector x-images need nx a multiple of 4 and one spare padding element beyond each x halo.
+__host__ __device__ bool xvec_ok(const Geom &g) { return g.n[0] % 4 == 0 && g.n[0] >= 8 && g.off[0] >= 4 && g.pad[0] >= g.off[0] + g.n[0] + 4; }
+
+Coef32 coef32(const DiffCoef &dc) {
+    Coef32 c;
+    c.g0 = (float)dc.g0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) c.ga[a][b] = (float)dc.ga[a][b];
+    return c;
+}
+
+template <int BY, int RY, int ZB, int NSLOT, int MINB, bool XVEC>
+cudaError_t run(const CUtensorMap *map, float *out, const Geom &g, const Coef32 &c, bool images, unsigned *err,
+                cudaStream_t s) {
+    using Cfg = H32<BY, RY, ZB, NSLOT>;
+    auto k = heat32_kernel<BY, RY, ZB, NSLOT, MINB, XVEC>;
+    static int occ[64] = {};  // resident CTAs per SM, per device
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 64) return cudaErrorInvalidDevice;
+    if (!occ[dev]) {
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+        if (e != cudaSuccess) return e;
+        int o = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, 32 * BY, Cfg::SMEM);
+        if (e != cudaSuccess) return e;
+        occ[dev] = std::max(o, 1);
+    }
+    const int tx = (int)((g.n[0] + Cfg::TX - 1) / Cfg::TX), ty = (int)((g.n[1] + Cfg::TY - 1) / Cfg::TY);
+    const int nz = (int)g.n[2];
+    const int chunks = choose_zchunks(tx * ty, nz, occ[dev] * device_sms(), 0.5);
+    const int zc = (nz + chunks - 1) / chunks;
+    dim3 grid(tx, ty, (unsigned)((nz + zc - 1) / zc));
+    k<<<grid, 32 * BY, Cfg::SMEM, s>>>(*map, out, g, c, zc, images ? 1 : 0, err);
+    return cudaGetLastError();
+}
+
+// Variant table: (BY warps, RY rows, ZB planes per iteration, NSLOT ring depth, MINB resident
+// CTAs the register budget is sized for).  The autotuner times each on the problem.
+#define HEAT32_VARIANTS(X) \
+    X(4, 2, 2, 8, 3)       \
+    X(4, 1, 2, 8, 4)       \
+    X(8, 1, 2, 8, 2)       \
+    X(4, 1, 2, 8, 3)
+
+const char *const NAMES[] = {"f32_by4_ry2_zb2_s8_m3", "f32_by4_ry1_zb2_s8_m4", "f32_by8_ry1_zb2_s8_m2",
+                             "f32_by4_ry1_zb2_s8_m3"};
+constexpr int NVAR = 4;
+
+}  // namespace
+
+int diffusion_f32_num_variants() { return NVAR; }
+
+const char *diffusion_f32_variant_name(int v) { return (v >= 0 && v < NVAR) ? NAMES[v] : "?"; }
+
+void diffusion_f32_box(int v, int box[3]) {
+    int i = 0;
+#define X(BY, RY, ZB, NS, MB) \
+    if (i++ == v) { box[0] = H32<BY, RY, ZB, NS>::TXP; box[1] = H32<BY, RY, ZB, NS>::ROWS; box[2] = 1; }
+    HEAT32_VARIANTS(X)
+#undef X
+}
+
+cudaError_t launch_diffusion_f32(const CUtensorMap *map, float *out, const Geom &g, const DiffCoef &dc, bool images,
+                                 unsigned *err, cudaStream_t s, int variant) {
+    const Coef32 c = coef32(dc);
+    const bool xv = xvec_ok(g);
+    int i = 0;
+    cudaError_t res = cudaErrorInvalidValue;
+#define X(BY, RY, ZB, NS, MB)                                                        \
+    if (i++ == variant)                                                              \
+        res = xv ? run<BY, RY, ZB, NS, MB, true>(map, out, g, c, images, err, s) \
+                 : run<BY, RY, ZB, NS, MB, false>(map, out, g, c, images, err, s);
+    HEAT32_VARIANTS(X)
+#undef X
+    return res;
+}
+
+// ------------------------------------------------------------------ batched (serving)
+
+// The tile shape of variant f32_by4_ry2_zb2_s8_m3.
+namespace {
+constexpr int DB_BY = 4, DB_RY = 2, DB_ZB = 2, DB_NSLOT = 8, DB_MINB = 2;
+using DbCfg = H32<DB_BY, DB_RY, DB_ZB, DB_NSLOT>;
+}  // namespace
+
+__global__ void __launch_bounds__(32 * DB_BY, DB_MINB)
+diffusion_batch_kernel(const BatchHeader *hdr, const BatchHeat *items, unsigned *err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float *ring = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    __shared__ __align__(8) uint64_t full[DB_NSLOT];
+    const int total = hdr->heat_ctas, n = hdr->n_heat;
+    for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (items[mid].cta_begin <= vb) lo = mid; else hi = mid - 1;
+        }
+        const BatchHeat &it = items[lo];
+        int r = vb - it.cta_begin;
+        const int tx = r % it.tiles_x;
+        r /= it.tiles_x;
+        const int ty = r % it.tiles_y, tz = r / it.tiles_y;
+        Coef32 c;
+        c.g0 = it.g0;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) c.ga[a][b] = it.ga[a][b];
+        const Geom g = it.g;
+        const bool ok = xvec_ok(g)
+                            ? heat32_tile<DB_BY, DB_RY, DB_ZB, DB_NSLOT, true>(it.map, it.out, g, c, tx, ty, tz, it.zc,
+                                                                               1, err, ring, full)
+                            : heat32_tile<DB_BY, DB_RY, DB_ZB, DB_NSLOT, false>(it.map, it.out, g, c, tx, ty, tz,
+                                                                                it.zc, 1, err, ring, full);
+        __syncthreads();
+        if (!ok) return;
+    }
+}
+
+int diffusion_batch_grid() {
+    static int grid[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return 152;
+    if (!grid[dev]) {
+        cudaFuncSetAttribute(diffusion_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DbCfg::SMEM);
+        int o = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, diffusion_batch_kernel, 32 * DB_BY, DbCfg::SMEM);
+        grid[dev] = std::max(o, 1) * device_sms();
+    }
+    return grid[dev];
+}
+
+void diffusion_batch_tile(int *tx, int *ty, int box[3]) {
+    *tx = DbCfg::TX;
+    *ty = DbCfg::TY;
+    box[0] = DbCfg::TXP;
+    box[1] = DbCfg::ROWS;
+    box[2] = 1;
+}
+
+cudaError_t launch_diffusion_batch(const BatchHeader *hdr, const BatchHeat *items, unsigned *err, int grid,
+                                   cudaStream_t s) {
+    diffusion_batch_kernel<<<grid, 32 * DB_BY, DbCfg::SMEM, s>>>(hdr, items, err);
+    return cudaGetLastError();
+}
+
+}  // namespace stn

@@ -38,6 +38,12 @@ cudaError_t launch_diffusion(int dtype, const CUtensorMap *map_in, void *out, co
 int diffusion_num_variants(int dtype);
 const char *diffusion_variant_name(int dtype, int variant);
 void diffusion_box(int dtype, int variant, int box[3]);  // TMA box (x, y, z) of a variant
+// The FP32 kernel family (diffusion_f32.cu), reached through the functions above for dtype 2.
+int diffusion_f32_num_variants();
+const char *diffusion_f32_variant_name(int variant);
+void diffusion_f32_box(int variant, int box[3]);
+cudaError_t launch_diffusion_f32(const CUtensorMap *map_in, float *out, const Geom &g, const DiffCoef &c,
+                                 bool images, unsigned *err, cudaStream_t s, int variant);
 
 // MHD8 (Eqs. A1-A4 + RK3).  Constants in the compute type are built inside mhd.cu.
 struct MhdConst {
