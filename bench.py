@@ -270,7 +270,7 @@ def xcorr_job(L, synth, dtype, warmup, reps, stream):
     return {"ms_job": ms}
 
 
-def run_serving_leg(n_requests=1024, load=0.7, fp64_subset=96):
+def run_serving_leg(n_requests=1024, load=0.7, fp64_subset=96, sweep=(0.5, 1.2)):
     """Serving configuration: 1024 requests (log-uniform 32^3..192^3, mixed kinds, 10-50
     steps, FP32) through the continuous-batching server under a 120 GB budget.
 
@@ -303,6 +303,16 @@ def run_serving_leg(n_requests=1024, load=0.7, fp64_subset=96):
     serving.poisson_arrivals(reqs, load * cap_rps)
     wall, peak, updates = serving.serve(reqs, templates)
     lat = serving.latency_stats(reqs)
+    # the same mix at other offered loads (below and above capacity)
+    sweep_out = []
+    for ld in sweep:
+        serving.poisson_arrivals(reqs, ld * cap_rps)
+        w2, p2, u2 = serving.serve(reqs, templates)
+        l2 = serving.latency_stats(reqs)
+        sweep_out.append({"load": ld, "rate_rps": round(ld * cap_rps, 1), "wall_s": round(w2, 3),
+                          "mcell_updates_per_s": round(u2 / w2 / 1e6, 1), "p50_ms": round(l2["p50_ms"], 2),
+                          "p99_ms": round(l2["p99_ms"], 2), "peak_gb": round(p2 / 1e9, 2)})
+    serving.poisson_arrivals(reqs, load * cap_rps)
     # 3. per-grid FP64 path on a subset, FIFO latencies under the same arrivals
     sub = sorted(reqs, key=lambda r: r.arrival)[:fp64_subset]
     arr = [r.arrival for r in sub]
@@ -333,6 +343,7 @@ def run_serving_leg(n_requests=1024, load=0.7, fp64_subset=96):
         "open_loop": {"load": load, "rate_rps": round(load * cap_rps, 1), "wall_s": round(wall, 3),
                       "mcell_updates_per_s": round(thr, 1), "p50_ms": round(lat["p50_ms"], 2),
                       "p99_ms": round(lat["p99_ms"], 2), "peak_gb": round(peak / 1e9, 2)},
+        "load_sweep": sweep_out,
         "per_grid_fp64_subset": {"requests": len(sub), "wall_s": round(wall64, 3),
                                  "mcell_updates_per_s": round(thr64, 1),
                                  "p50_ms": round(float(np.percentile(lat64, 50) * 1e3), 2),
@@ -519,6 +530,17 @@ def run_extras(L, synth, stream, hbm_peak, args):
     out["heat3d_256_fp32_100steps"] = {
         "ms_per_job": round(res["ms_job"], 4), "kernel_ms_avg": round(res["ms_kernel"], 5),
         "mcell_updates_per_s": round(cells * HEAT_STEPS / (res["ms_job"] / 1e3) / 1e6, 1),
+        "variant": res["variant"],
+        "roofline": _roof("hbm", gbs, hbm_peak, "GB/s", note="8 B/cell-update algorithmic")}
+    res["plan"].close()
+    # config 2 FP32 at 512^3: the two 540 MB fields far exceed the 126 MB L2
+    n5 = 2 * HEAT_N
+    res = heat_job(L, synth, L.STENCIL_F32, n5, HEAT_STEPS // 4, w, r, stream)
+    cells5 = n5 ** 3
+    gbs = cells5 * 8.0 / (res["ms_kernel"] / 1e3) / 1e9
+    out["heat3d_512_fp32_25steps"] = {
+        "ms_per_job": round(res["ms_job"], 4), "kernel_ms_avg": round(res["ms_kernel"], 5),
+        "mcell_updates_per_s": round(cells5 * (HEAT_STEPS // 4) / (res["ms_job"] / 1e3) / 1e6, 1),
         "variant": res["variant"],
         "roofline": _roof("hbm", gbs, hbm_peak, "GB/s", note="8 B/cell-update algorithmic")}
     res["plan"].close()

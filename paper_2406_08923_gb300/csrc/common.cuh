@@ -122,6 +122,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     }
 }
 
+// Programmatic dependent launch.  A kernel launched with programmatic stream serialization
+// lets the next such kernel in the stream start its preamble (barrier set-up, descriptor
+// prefetch) early; every thread then waits until the previous kernel has completed and its
+// memory operations are visible before it touches global memory.
+__device__ __forceinline__ void pdl_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // 3D tiled TMA load of one box into shared memory, completion signalled on `bar`.
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar,
                                             int x, int y, int z) {

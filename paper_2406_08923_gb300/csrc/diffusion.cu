@@ -22,6 +22,7 @@
 //     (mbarrier waits, the block barrier, refills) is amortised over VX x RY x ZB cells.
 //   * Outputs are stored once as vectors.  Threads whose cells lie within r of a face also
 //     store the periodic images (Eq. 2) on a slow path, so no separate halo pass is needed.
+//   * Consecutive steps are launched with programmatic dependent launch (see pdl_wait).
 //   * Waits are bounded (globaltimer); on expiry the CTA records ERR_TIMEOUT, drains its
 //     in-flight TMA loads (again bounded) and returns.
 #include <algorithm>
@@ -113,7 +114,7 @@ __device__ __forceinline__ void ld_vec(const T *p, T (&dst)[N]) {
 // One xy-tile of one z-chunk: the whole 2.5D pipeline of a CTA.  `map` may point at a
 // __grid_constant__ parameter or at a descriptor in global memory (batched launches).
 // Returns false if a bounded wait expired (ERR_TIMEOUT recorded, loads drained).
-template <typename T, int VP, int BY, int RY, int ZB, int NSLOT, bool PK>
+template <typename T, int VP, int BY, int RY, int ZB, int NSLOT, bool PK, bool PDL>
 __device__ __forceinline__ bool diffusion_tile(const CUtensorMap *map, T *__restrict__ out, const Geom &g,
                                                const DC<T> &c, int tile_x, int tile_y, int tile_z, int zc,
                                                int images, unsigned *err, T *ring, uint64_t *full) {
@@ -137,6 +138,10 @@ __device__ __forceinline__ bool diffusion_tile(const CUtensorMap *map, T *__rest
         mbar_fence_init();
     }
     __syncthreads();
+    if (PDL) {  // the input is the previous step's output: wait for that kernel to finish
+        pdl_launch_dependents();
+        pdl_wait();
+    }
 
     const int bx = (int)g.off[0] + x0 - Cfg::HX;
     const int by0 = (int)g.off[1] + y0 - R6;
@@ -359,8 +364,8 @@ diffusion_kernel(const __grid_constant__ CUtensorMap map_in, T *__restrict__ out
     // TMA destinations are kept 128-byte aligned (dynamic smem has 128 spare bytes)
     T *ring = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     __shared__ __align__(8) uint64_t full[NSLOT];
-    diffusion_tile<T, VP, BY, RY, ZB, NSLOT, PK>(&map_in, out, g, c, blockIdx.x, blockIdx.y, blockIdx.z, zc,
-                                                 images, err, ring, full);
+    diffusion_tile<T, VP, BY, RY, ZB, NSLOT, PK, true>(&map_in, out, g, c, blockIdx.x, blockIdx.y, blockIdx.z,
+                                                       zc, images, err, ring, full);
 }
 
 // ------------------------------------------------------------------ variants / launch
@@ -422,8 +427,8 @@ static cudaError_t run(const CUtensorMap *map, void *out, const Geom &g, const D
     const int chunks = choose_zchunks(tx * ty, nz, occ[dev] * device_sms(), sizeof(T) == 4 ? 0.5 : 0.05);
     const int zc = (nz + chunks - 1) / chunks;
     dim3 grid(tx, ty, (unsigned)((nz + zc - 1) / zc));
-    k<<<grid, 32 * BY, Cfg::SMEM, s>>>(*map, static_cast<T *>(out), g, c, zc, images ? 1 : 0, err);
-    return cudaGetLastError();
+    return launch_pdl(k, grid, dim3(32 * BY), Cfg::SMEM, s, *map, static_cast<T *>(out), g, c, zc, images ? 1 : 0,
+                      err);
 }
 
 // Variant table: (VP pairs per row, BY warps, RY rows, ZB planes, NSLOT, packed FP32x2)

@@ -20,6 +20,8 @@
 //     the row padding) or per-cell scalar stores otherwise; y- and z-images are behind one
 //     test that is uniform per warp row and per plane.  Tiles that overhang the interior
 //     store element-wise through an out-of-line path.
+//   * Consecutive steps are launched with programmatic dependent launch: a step's CTAs set up
+//     their barriers while the previous step drains, then wait for it before the first load.
 //   * Waits are bounded (globaltimer); on expiry the CTA records ERR_TIMEOUT, drains its
 //     in-flight TMA loads (again bounded) and returns.
 // The multiply-add order per cell is the same as the FP64 kernel's (x, y, z pairs of offset
@@ -67,7 +69,7 @@ __device__ __noinline__ void store4_bounded(float *out, const Geom &g, int image
 
 // One xy-tile of one z-chunk.  `map` may point at a __grid_constant__ parameter or at a
 // descriptor in global memory (batched launches).  Returns false if a bounded wait expired.
-template <int BY, int RY, int ZB, int NSLOT, bool XVEC>
+template <int BY, int RY, int ZB, int NSLOT, bool XVEC, bool PDL>
 __device__ __forceinline__ bool heat32_tile(const CUtensorMap *map, float *__restrict__ out, const Geom &g,
                                             const Coef32 &c, int tile_x, int tile_y, int tile_z, int zc, int images,
                                             unsigned *err, float *ring, uint64_t *full) {
@@ -86,6 +88,10 @@ __device__ __forceinline__ bool heat32_tile(const CUtensorMap *map, float *__res
         mbar_fence_init();
     }
     __syncthreads();
+    if (PDL) {  // the input is the previous step's output: wait for that kernel to finish
+        pdl_launch_dependents();
+        pdl_wait();
+    }
     const int bx = (int)g.off[0] + x0 - Cfg::HX, by0 = (int)g.off[1] + y0 - R6, bz0 = (int)g.off[2] + zc0 - R6;
     int issued = 0;
     auto issue = [&](int j) {  // plane j (0-based from zc0-3) into its ring slot
@@ -274,8 +280,8 @@ heat32_kernel(const __grid_constant__ CUtensorMap map_in, float *__restrict__ ou
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *ring = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     __shared__ __align__(8) uint64_t full[NSLOT];
-    heat32_tile<BY, RY, ZB, NSLOT, XVEC>(&map_in, out, g, c, blockIdx.x, blockIdx.y, blockIdx.z, zc, images, err,
-                                         ring, full);
+    heat32_tile<BY, RY, ZB, NSLOT, XVEC, true>(&map_in, out, g, c, blockIdx.x, blockIdx.y, blockIdx.z, zc, images,
+                                               err, ring, full);
 }
 
 // Vector x-images need nx a multiple of 4 and one spare padding element beyond each x halo.
@@ -312,8 +318,7 @@ cudaError_t run(const CUtensorMap *map, float *out, const Geom &g, const Coef32 
     const int chunks = choose_zchunks(tx * ty, nz, occ[dev] * device_sms(), 0.5);
     const int zc = (nz + chunks - 1) / chunks;
     dim3 grid(tx, ty, (unsigned)((nz + zc - 1) / zc));
-    k<<<grid, 32 * BY, Cfg::SMEM, s>>>(*map, out, g, c, zc, images ? 1 : 0, err);
-    return cudaGetLastError();
+    return launch_pdl(k, grid, dim3(32 * BY), Cfg::SMEM, s, *map, out, g, c, zc, images ? 1 : 0, err);
 }
 
 // Variant table: (BY warps, RY rows, ZB planes per iteration, NSLOT ring depth, MINB resident
@@ -388,9 +393,9 @@ diffusion_batch_kernel(const BatchHeader *hdr, const BatchHeat *items, unsigned 
             for (int b = 0; b < 3; ++b) c.ga[a][b] = it.ga[a][b];
         const Geom g = it.g;
         const bool ok = xvec_ok(g)
-                            ? heat32_tile<DB_BY, DB_RY, DB_ZB, DB_NSLOT, true>(it.map, it.out, g, c, tx, ty, tz, it.zc,
+                            ? heat32_tile<DB_BY, DB_RY, DB_ZB, DB_NSLOT, true, false>(it.map, it.out, g, c, tx, ty, tz, it.zc,
                                                                                1, err, ring, full)
-                            : heat32_tile<DB_BY, DB_RY, DB_ZB, DB_NSLOT, false>(it.map, it.out, g, c, tx, ty, tz,
+                            : heat32_tile<DB_BY, DB_RY, DB_ZB, DB_NSLOT, false, false>(it.map, it.out, g, c, tx, ty, tz,
                                                                                 it.zc, 1, err, ring, full);
         __syncthreads();
         if (!ok) return;
