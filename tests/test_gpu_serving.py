@@ -24,7 +24,9 @@ def _mix():
     spec = [(L.STENCIL_MHD8, 16, 3), (L.STENCIL_DIFFUSION, 24, 7), (L.STENCIL_XCORR, 16, 9),
             (L.STENCIL_DIFFUSION, 32, 4), (L.STENCIL_MHD8, 24, 2), (L.STENCIL_XCORR, 24, 5),
             (L.STENCIL_DIFFUSION, 16, 11), (L.STENCIL_MHD8, 8, 5), (L.STENCIL_XCORR, 32, 3),
-            (L.STENCIL_DIFFUSION, 40, 2), (L.STENCIL_MHD8, 32, 1), (L.STENCIL_XCORR, 8, 12)]
+            (L.STENCIL_DIFFUSION, 40, 2), (L.STENCIL_MHD8, 32, 1), (L.STENCIL_XCORR, 8, 12),
+            # sizes that are not multiples of 4: scalar x-image stores in the batched heat kernel
+            (L.STENCIL_DIFFUSION, 21, 3), (L.STENCIL_MHD8, 13, 2), (L.STENCIL_XCORR, 11, 4)]
     reqs = [serving.Request(i, k, n, s) for i, (k, n, s) in enumerate(spec)]
     for i, r in enumerate(reqs):
         r.arrival = 0.002 * (i % 4)  # some arrive while others are already stepping
