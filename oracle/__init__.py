@@ -59,6 +59,8 @@ def _load():
                 "oracle_derivs_box": (None, [P, I64, I64, I64, P, P]),
                 "oracle_diffusion_box": (None, [P, I64, I64, I64, D, D, P, P]),
                 "oracle_diffusion": (I, [P, I64, I64, I64, D, D, P, I, P]),
+                "oracle_diffusion_r_box": (I, [P, I64, I64, I64, I, D, D, P, P]),
+                "oracle_diffusion_r": (I, [P, I64, I64, I64, I, D, D, P, I, P]),
                 "oracle_mhd_rhs_box": (None, [P, I64, I64, I64, P, P]),
                 "oracle_mhd_rk3": (I, [P, I64, I64, I64, P, D, I]),
                 "oracle_mhd_rk3_box": (I, [P, I64, I64, I64, P, D, I]),
@@ -162,6 +164,28 @@ def diffusion_box(fhat: np.ndarray, dt: float, alpha: float, h, interior_shape) 
     nx, ny, nz = _dims3(interior_shape)
     out = np.empty(tuple(interior_shape), dtype=np.float64)
     _load().oracle_diffusion_box(_p(fhat), nx, ny, nz, dt, alpha, _p(_c(h, np.float64)), _p(out))
+    return out
+
+
+def diffusion_r_box(fhat: np.ndarray, r: int, dt: float, alpha: float, h, interior_shape) -> np.ndarray:
+    """One Euler step with the radius-r (order 2r) Laplacian on a padded box (halo r on every
+    axis of extent > 1); returns the interior."""
+    fhat = _c(fhat, np.float64)
+    nx, ny, nz = _dims3(interior_shape)
+    out = np.empty(tuple(interior_shape), dtype=np.float64)
+    rc = _load().oracle_diffusion_r_box(_p(fhat), nx, ny, nz, r, dt, alpha, _p(_c(h, np.float64)), _p(out))
+    assert rc == 0, "radius must be 1..4"
+    return out
+
+
+def diffusion_r(f: np.ndarray, r: int, dt: float, alpha: float, h, steps: int) -> np.ndarray:
+    """`steps` periodic forward-Euler steps with the radius-r Laplacian (radius sweep of the
+    diffusion equation, Sec. 5.3), in 1, 2 or 3 dimensions."""
+    f = _c(f, np.float64)
+    nx, ny, nz = _dims3(f.shape)
+    out = np.empty_like(f)
+    rc = _load().oracle_diffusion_r(_p(f), nx, ny, nz, r, dt, alpha, _p(_c(h, np.float64)), steps, _p(out))
+    assert rc == 0, "radius must be 1..4"
     return out
 
 

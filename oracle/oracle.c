@@ -15,6 +15,10 @@
  *   diffusion  one forward-Euler step of df/dt = alpha lap f, Eq. 4 (Sec. 3.2), evaluated
  *              literally as f + dt*alpha*(sum over axes of the 2nd-derivative stencil); the
  *              folded single-kernel form of Eqs. 5-7 is the CUDA path's business, not ours.
+ *   diffusion_r  the same step with the radius-r central 2nd derivative of order 2r (the
+ *              radius sweep of Sec. 5.3, r = 1..4, in 1, 2 or 3 dimensions).  The weights are
+ *              the classical maximal-order central ones, evaluated from their closed form
+ *              c_k = 2 (-1)^(k+1) (r!)^2 / (k^2 (r-k)! (r+k)!), k = 1..r, c_0 = -2 sum 1/k^2.
  *   derivs     6th-order central differences (Sec. 3.3 names the order; the weights are the
  *              textbook ones: 1st derivative (-1,9,-45,0,45,-9,1)/60, 2nd derivative
  *              (2,-27,270,-490,270,-27,2)/180, and the mixed derivative in the diagonal form
@@ -213,6 +217,77 @@ int oracle_diffusion(const double *in, int64_t nx, int64_t ny, int64_t nz, doubl
     for (int t = 0; t < steps; ++t) {
         pad_periodic(cur, nx, ny, nz, R, sizeof(double), hat);
         oracle_diffusion_box(hat, nx, ny, nz, dt, alpha, h, cur);
+    }
+    memcpy(out, cur, sizeof(double) * ncell);
+    free(cur); free(hat);
+    return 0;
+}
+
+/* ------------------------------------ radius-r diffusion (Eq. 4, radius sweep, Sec. 5.3) */
+
+#define RMAX 4
+
+static double factorial(int k) {
+    double f = 1.0;
+    for (int i = 2; i <= k; ++i) f *= (double)i;
+    return f;
+}
+
+/* Weights of the order-2r central second derivative on points -r..r (unit spacing):
+ * c[0] is the centre weight, c[k] the weight of each of the points at +-k. */
+static void d2_weights(int r, double *c) {
+    double centre = 0.0;
+    for (int k = 1; k <= r; ++k) {
+        double sign = (k % 2 == 1) ? 1.0 : -1.0;
+        c[k] = 2.0 * sign * factorial(r) * factorial(r) /
+               ((double)k * (double)k * factorial(r - k) * factorial(r + k));
+        centre += 1.0 / ((double)k * (double)k);
+    }
+    c[0] = -2.0 * centre;
+}
+
+static double der2_r(const double *f, int64_t p, int64_t s, double h, int r, const double *c) {
+    double acc = c[0] * f[p];
+    for (int k = 1; k <= r; ++k) acc += c[k] * (f[p + k * s] + f[p - k * s]);
+    return acc / (h * h);
+}
+
+/* One forward-Euler step f' = f + dt*alpha*lap f with the radius-r Laplacian over a padded
+ * box (halo r on every axis of extent > 1).  Returns -1 for r outside 1..RMAX. */
+int oracle_diffusion_r_box(const double *fhat, int64_t nx, int64_t ny, int64_t nz, int r,
+                           double dt, double alpha, const double *h, double *out) {
+    if (r < 1 || r > RMAX) return -1;
+    double c[RMAX + 1];
+    d2_weights(r, c);
+    int64_t hx = halo_of(nx, r), hy = halo_of(ny, r), hz = halo_of(nz, r);
+    int64_t px = nx + 2 * hx, py = ny + 2 * hy;
+    int64_t n[3] = {nx, ny, nz}, s[3] = {1, px, px * py};
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < nz; ++k)
+        for (int64_t j = 0; j < ny; ++j)
+            for (int64_t i = 0; i < nx; ++i) {
+                int64_t p = ((k + hz) * py + (j + hy)) * px + (i + hx);
+                double lap = 0.0;
+                for (int a = 0; a < 3; ++a)
+                    if (n[a] > 1) lap += der2_r(fhat, p, s[a], h[a], r, c);
+                out[(k * ny + j) * nx + i] = fhat[p] + dt * alpha * lap;
+            }
+    return 0;
+}
+
+/* `steps` periodic Euler steps with the radius-r Laplacian; in/out are dense interiors. */
+int oracle_diffusion_r(const double *in, int64_t nx, int64_t ny, int64_t nz, int r, double dt,
+                       double alpha, const double *h, int steps, double *out) {
+    if (r < 1 || r > RMAX) return -1;
+    int64_t hx = halo_of(nx, r), hy = halo_of(ny, r), hz = halo_of(nz, r);
+    size_t ncell = (size_t)(nx * ny * nz);
+    size_t npad = (size_t)((nx + 2 * hx) * (ny + 2 * hy) * (nz + 2 * hz));
+    double *cur = malloc(sizeof(double) * ncell), *hat = malloc(sizeof(double) * npad);
+    if (!cur || !hat) { free(cur); free(hat); return -1; }
+    memcpy(cur, in, sizeof(double) * ncell);
+    for (int t = 0; t < steps; ++t) {
+        pad_periodic(cur, nx, ny, nz, r, sizeof(double), hat);
+        oracle_diffusion_r_box(hat, nx, ny, nz, r, dt, alpha, h, cur);
     }
     memcpy(out, cur, sizeof(double) * ncell);
     free(cur); free(hat);
