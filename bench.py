@@ -270,6 +270,46 @@ def xcorr_job(L, synth, dtype, warmup, reps, stream):
     return {"ms_job": ms}
 
 
+def run_radius_sweep(L, synth, stream, hbm_peak):
+    """Diffusion equation at radius 1..4 (order-2r Laplacian) in 1D, 2D and 3D, FP32 and FP64
+    (Sec. 5.3, Figs. 10-11): 2^24 cells per problem (64 MiB FP32 / 128 MiB FP64, the paper's
+    sizes): 2^24 in 1D, 4096^2 in 2D, 256^3 in 3D.  Time per Euler step and its fraction of
+    HBM bandwidth at one read and one write per cell-step (1D runs up to 16 steps per launch in
+    shared memory, so its traffic is lower than that)."""
+    out = {}
+    shapes = {1: (1 << 24,), 2: (4096, 4096), 3: (256, 256, 256)}
+    steps = {1: 64, 2: 20, 3: 20}
+    for ndim, shape in shapes.items():
+        n = int(np.prod(shape))
+        base = synth.uniform(2406089237, ndim, n, -1.0, 1.0).reshape(shape)
+        for st, name, esize in ((L.STENCIL_F32, "fp32", 4), (L.STENCIL_F64, "fp64", 8)):
+            for r in (1, 2, 3, 4):
+                p = L.Plan(ndim, tuple(reversed(shape)), r, 1, L.STENCIL_BC_PERIODIC, L.STENCIL_DIFFUSION, st, st,
+                           params=L.heat_params(shape))
+                a, b = p.alloc(), p.alloc()
+                p.upload(a, [base])
+                if ndim == 3 and r == 3:
+                    p.autotune(a, b, nsteps=4, reps=2, stream=stream)
+                k = steps[ndim]
+                p.step(a, b, k, stream)
+                ms = _timed(lambda: p.step(a, b, k, stream), 3, stream) / k
+                gbs = n * 2.0 * esize / (ms / 1e3) / 1e9
+                ent = {"ms_per_step": round(ms, 5), "gcell_updates_per_s": round(n / (ms / 1e3) / 1e9, 2),
+                       "hbm_gbs_at_1r1w": round(gbs, 1), "frac_of_hbm": round(gbs / hbm_peak, 4),
+                       "variant": p.variant()[2]}
+                if st == L.STENCIL_F64:
+                    # FP64 is bound by the FP64 pipe: 1 + 2 d r instructions per cell (2 flop each;
+                    # 1D runs 2r + 1 FMAs through the folded cross-correlation)
+                    inst = (2 * r + 1) if ndim == 1 else (1 + 2 * ndim * r)
+                    tf = n * inst * 2.0 / (ms / 1e3) / 1e12
+                    ent["fp64_tflops"] = round(tf, 3)
+                    ent["frac_of_fp64_peak"] = round(tf / FP64_PEAK_TFLOPS, 4)
+                out[f"{ndim}d_{name}_r{r}"] = ent
+                p.close()
+                del a, b
+    return out
+
+
 def run_serving_leg(n_requests=1024, load=0.7, fp64_subset=96, sweep=(0.5, 1.2)):
     """Serving configuration: 1024 requests (log-uniform 32^3..192^3, mixed kinds, 10-50
     steps, FP32) through the continuous-batching server under a 120 GB budget.
@@ -478,6 +518,7 @@ def run_ours(args):
     extras = {}
     if not args.no_extras:
         extras = run_extras(L, synth, stream, hbm_peak, args)
+        extras["diffusion_radius_sweep"] = run_radius_sweep(L, synth, stream, hbm_peak)
         if world == 1:
             extras["serving"] = run_serving_leg()
 
@@ -628,6 +669,7 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="grid size for --case")
     ap.add_argument("--variant", type=int, default=0, help="kernel variant for --case")
     ap.add_argument("--serving", action="store_true", help="serving configuration only (one JSON line)")
+    ap.add_argument("--radius-sweep", action="store_true", help="diffusion radius sweep only (one JSON line)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -635,6 +677,15 @@ def main():
         return run_reference(args)
     if args.case:
         return run_case(args)
+    if args.radius_sweep:
+        import torch
+
+        from paper_2406_08923_gb300 import _lib as L
+        from paper_2406_08923_gb300 import synth
+        L.load()
+        res = run_radius_sweep(L, synth, torch.cuda.current_stream(), _peaks()[0])
+        print(json.dumps({"metric": "diffusion_radius_sweep_ms_per_step", "radius_sweep": res}), flush=True)
+        return 0
     if args.serving:
         print(json.dumps({"metric": "serving_p50_p99_latency_and_mcell_updates_per_s", "serving": run_serving_leg()}),
               flush=True)

@@ -321,12 +321,12 @@ class Plan:
         return t.view(self.padded[2], self.padded[1], self.padded[0])
 
     def interior(self, t):
-        """(nz, ny, nx) view of the interior (1D: (nx,))."""
+        """(nz, ny, nx) view of the interior (2D: (ny, nx); 1D: (nx,))."""
         v = self.view3(t)
         ox, oy, oz = self.origin
         nx, ny, nz = self.dims
         v = v[oz:oz + nz, oy:oy + ny, ox:ox + nx]
-        return v[0, 0] if self.ndim == 1 else v
+        return v[0, 0] if self.ndim == 1 else (v[0] if self.ndim == 2 else v)
 
     def upload(self, fields, arrays):
         """Copy host arrays (interior shape) into the interior of device fields."""
@@ -388,11 +388,13 @@ def mhd_params(n, dt=None, **kw) -> stencil_params:
 
 
 def heat_params(n, alpha=1.0, dt=None) -> stencil_params:
-    """stencil_params for the heat equation on a periodic (2 pi)^3 box; dt = 0.1 dx^2."""
-    nz, ny, nx = (n, n, n) if np.isscalar(n) else tuple(n)
+    """stencil_params for the heat equation on a periodic (2 pi)^d box; dt = 0.1 dx^2.  n is the
+    edge of a cube or the dense shape ((nz, ny, nx), (ny, nx) or (nx,)); absent axes get dx = 2 pi."""
+    nz, ny, nx = (n, n, n) if np.isscalar(n) else (1,) * (3 - len(tuple(n))) + tuple(n)
     p = stencil_params()
     tau = 2.0 * np.pi
     p.dx[0], p.dx[1], p.dx[2] = tau / nx, tau / ny, tau / nz
     p.alpha = alpha
-    p.dt = 0.1 * min(p.dx[0], p.dx[1], p.dx[2]) ** 2 if dt is None else dt
+    used = [d for d, m in zip((p.dx[0], p.dx[1], p.dx[2]), (nx, ny, nz)) if m > 1] or [p.dx[0]]
+    p.dt = 0.1 * min(used) ** 2 if dt is None else dt
     return p

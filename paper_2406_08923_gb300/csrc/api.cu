@@ -210,6 +210,21 @@ const char *stencil_last_error_detail(stencil_t p) {
     return p ? p->detail.c_str() : g_create_detail.c_str();
 }
 
+// Centred 2nd-derivative weights of order 2r on points -r..r (unit spacing): c[0] for the centre,
+// c[k] for each point at +-k; c_k = 2 (-1)^(k+1) (r!)^2 / (k^2 (r-k)! (r+k)!), c_0 = -2 sum 1/k^2.
+static void central_d2_weights(int r, double *c) {
+    auto fact = [](int k) {
+        double f = 1.0;
+        for (int i = 2; i <= k; ++i) f *= i;
+        return f;
+    };
+    c[0] = 0.0;
+    for (int k = 1; k <= r; ++k) {
+        c[k] = ((k & 1) ? 2.0 : -2.0) * fact(r) * fact(r) / ((double)k * k * fact(r - k) * fact(r + k));
+        c[0] -= 2.0 / ((double)k * k);
+    }
+}
+
 stencil_status stencil_create(int ndim, const int64_t dims[3], int radius, const void *coeffs,
                               int ncoeffs, int nfields, stencil_bc bc, stencil_kind kind,
                               stencil_dtype storage, stencil_dtype compute,
@@ -238,11 +253,13 @@ stencil_status stencil_create(int ndim, const int64_t dims[3], int radius, const
         if (storage != compute || storage == STENCIL_BF16)
             return fail(nullptr, STENCIL_EUNSUPPORTED, "XCORR supports I32/I32, F64/F64, F32/F32");
     } else {
-        if (radius != 3) return fail(nullptr, STENCIL_EINVAL, "DIFFUSION and MHD8 use radius 3");
+        if (kind == STENCIL_DIFFUSION && (radius < 1 || radius > 4))
+            return fail(nullptr, STENCIL_EUNSUPPORTED, "DIFFUSION supports radius 1..4");
+        if (kind == STENCIL_MHD8 && radius != 3) return fail(nullptr, STENCIL_EINVAL, "MHD8 uses radius 3");
         if (ncoeffs != 0) return fail(nullptr, STENCIL_EINVAL, "DIFFUSION and MHD8 take no coefficients");
         if (!params) return fail(nullptr, STENCIL_EINVAL, "params is NULL");
-        if (ndim != 3) return fail(nullptr, STENCIL_EUNSUPPORTED, "DIFFUSION and MHD8 support ndim = 3");
-        for (int a = 0; a < 3; ++a)
+        if (kind == STENCIL_MHD8 && ndim != 3) return fail(nullptr, STENCIL_EUNSUPPORTED, "MHD8 supports ndim = 3");
+        for (int a = 0; a < ndim; ++a)
             if (!(params->dx[a] > 0.0) || !std::isfinite(params->dx[a]))
                 return fail(nullptr, STENCIL_EINVAL, "grid spacing must be positive and finite");
         if (!std::isfinite(params->dt)) return fail(nullptr, STENCIL_EINVAL, "dt must be finite");
@@ -310,14 +327,25 @@ stencil_status stencil_create(int ndim, const int64_t dims[3], int radius, const
         static const double WM[3] = {270.0, -27.0, 2.0};
         const double *h = params->dx;
         if (kind == STENCIL_DIFFUSION) {
-            // Eq. 5/7: g = c1 + dt alpha (c2_x + c2_y + c2_z)
+            // Eq. 5/7: g = c1 + dt alpha (sum over the ndim axes of the order-2r Laplacian)
+            double c2[5];
+            central_d2_weights(radius, c2);
             const double s = params->dt * params->alpha;
             double g0 = 1.0;
-            for (int a = 0; a < 3; ++a) {
-                g0 += s * W2C / (h[a] * h[a]);
-                for (int i = 0; i < 3; ++i) p->dcoef.ga[a][i] = s * W2[i] / (h[a] * h[a]);
+            p->dcoef = DiffCoef{};
+            p->dcoef.r = radius;
+            for (int a = 0; a < ndim; ++a) {
+                g0 += s * c2[0] / (h[a] * h[a]);
+                for (int i = 0; i < radius; ++i) p->dcoef.ga[a][i] = s * c2[i + 1] / (h[a] * h[a]);
             }
             p->dcoef.g0 = g0;
+            if (ndim == 1) {  // 1D: the folded step is the cross-correlation of Eq. 3 with these weights
+                for (int j = -radius; j <= radius; ++j) {
+                    const double w = j == 0 ? g0 : p->dcoef.ga[0][std::abs(j) - 1];
+                    p->gd[j + radius] = w;
+                    p->gf[j + radius] = (float)w;
+                }
+            }
         } else {
             MhdConst &c = p->mconst;
             for (int a = 0; a < 3; ++a) {
@@ -435,15 +463,26 @@ static stencil_status run_pass(stencil_t p, void *const *src, void *const *dst, 
            "xcorr launch");
         return STENCIL_OK;
     }
+    if (p->kind == STENCIL_DIFFUSION && p->ndim == 1) {  // folded weights through the XCORR kernel
+        const void *cf = p->storage == STENCIL_F64 ? (const void *)p->gd : (const void *)p->gf;
+        CK(p, launch_xcorr(storage_code(p->storage), p->radius, src[0], dst[0], g, cf, sweeps, periodic, periodic, s),
+           "diffusion (1D) launch");
+        return STENCIL_OK;
+    }
     if (p->kind == STENCIL_DIFFUSION) {
         int box[3];
-        diffusion_box(storage_code(p->storage), p->variant, box);
+        if (p->ndim == 2) diffusion2d_box(storage_code(p->storage), p->radius, box);
+        else diffusion_box(storage_code(p->storage), p->radius, p->variant, box);
         CUtensorMap m;
         stencil_status st = tma_map(p, src[0], box, &m);
         if (st != STENCIL_OK) return st;
-        CK(p, launch_diffusion(storage_code(p->storage), &m, dst[0], g, p->dcoef, periodic, p->err, s,
-                               p->variant),
-           "diffusion launch");
+        if (p->ndim == 2)
+            CK(p, launch_diffusion2d(storage_code(p->storage), &m, dst[0], g, p->dcoef, periodic, p->err, s),
+               "diffusion (2D) launch");
+        else
+            CK(p, launch_diffusion(storage_code(p->storage), &m, dst[0], g, p->dcoef, periodic, p->err, s,
+                                   p->variant),
+               "diffusion launch");
         return STENCIL_OK;
     }
     int box[3];
@@ -483,9 +522,10 @@ stencil_status stencil_step(stencil_t p, void *const *fin, void *const *fout, in
     }
 
     // pass list
-    std::vector<int> sweeps;  // XCORR: sweeps per launch; others: one entry per pass
+    std::vector<int> sweeps;  // XCORR (and 1D DIFFUSION): sweeps per launch; others: one entry per pass
     int npass;
-    if (p->kind == STENCIL_XCORR) {
+    const bool xcorr_like = p->kind == STENCIL_XCORR || (p->kind == STENCIL_DIFFUSION && p->ndim == 1);
+    if (xcorr_like) {
         const int maxs = periodic ? xcorr_max_sweeps_per_launch() : 1;
         for (int left = nsteps; left > 0;) {
             int k = std::min(left, maxs);
@@ -497,7 +537,7 @@ stencil_status stencil_step(stencil_t p, void *const *fin, void *const *fout, in
         npass = p->kind == STENCIL_MHD8 ? 3 * nsteps : nsteps;
         sweeps.assign(npass, 1);
     }
-    if (periodic && p->kind != STENCIL_XCORR)
+    if (periodic && !xcorr_like)
         CK(p, launch_halo_fill(p->geom, p->radius, p->esize, ptrs(fin, p->nfields), p->nfields, s),
            "halo_fill launch");
     if (p->kind == STENCIL_MHD8 && p->storage != STENCIL_F64)
@@ -589,13 +629,16 @@ stencil_status stencil_field_norms(stencil_t p, void *const *fields, double *out
 }
 
 static int num_variants(stencil_t p) {
-    if (p->kind == STENCIL_DIFFUSION) return diffusion_num_variants(storage_code(p->storage));
+    if (p->kind == STENCIL_DIFFUSION)
+        return p->ndim == 3 ? diffusion_num_variants(storage_code(p->storage), p->radius) : 1;
     if (p->kind == STENCIL_MHD8) return mhd_num_variants(storage_code(p->storage));
     return 1;
 }
 
 static const char *variant_name(stencil_t p, int v) {
-    if (p->kind == STENCIL_DIFFUSION) return diffusion_variant_name(storage_code(p->storage), v);
+    if (p->kind == STENCIL_DIFFUSION && p->ndim == 1) return "xcorr_folded_chunk2048_temporal_blocking";
+    if (p->kind == STENCIL_DIFFUSION && p->ndim == 2) return "tile2d_32vx_by8_ry4";
+    if (p->kind == STENCIL_DIFFUSION) return diffusion_variant_name(storage_code(p->storage), p->radius, v);
     if (p->kind == STENCIL_MHD8) return mhd_variant_name(storage_code(p->storage), v);
     return "chunk2048_temporal_blocking";
 }

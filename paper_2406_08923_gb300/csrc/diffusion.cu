@@ -66,17 +66,17 @@ template <bool PK> struct PairOps<double, PK> {
 
 template <typename T> struct DC {
     T g0;
-    T ga[3][3];
+    T ga[3][4];  // [axis][a-1]
 };
 
-template <typename T, int VP, int BY, int RY, int ZB, int NSLOT>
+template <typename T, int VP, int BY, int RY, int ZB, int NSLOT, int R>
 struct DiffCfg {
     static constexpr int VX = 2 * VP;
     static constexpr int HX = 4;  // x halo kept in shared memory: 16 B aligned TMA box start
     static constexpr int TX = 32 * VX;
     static constexpr int TY = BY * RY;
     static constexpr int TXP = TX + 2 * HX;
-    static constexpr int ROWS = TY + 2 * R6;
+    static constexpr int ROWS = TY + 2 * R;
     static constexpr int SLOT_ELEMS = ((TXP * ROWS * (int)sizeof(T) + 127) / 128) * 128 / (int)sizeof(T);
     static constexpr uint32_t BOX_BYTES = TXP * ROWS * sizeof(T);
     static constexpr size_t SMEM = (size_t)NSLOT * SLOT_ELEMS * sizeof(T) + 128;
@@ -84,7 +84,8 @@ struct DiffCfg {
     static constexpr int LV = (VX * (int)sizeof(T) >= 16) ? 16 / (int)sizeof(T) : VX;
     static_assert((TXP * sizeof(T)) % 16 == 0, "TMA box inner extent must be a multiple of 16 B");
     static_assert(TXP <= 256 && ROWS <= 256, "TMA box extents are limited to 256");
-    static_assert(NSLOT >= ZB + 4, "ring must hold the ZB centre planes, the ZB leading planes and a refill");
+    static_assert(R >= 1 && R <= HX, "radius 1..4: the x window holds 4 neighbours per side");
+    static_assert(NSLOT >= ZB + R + 1, "ring: ZB + R planes in use plus one refill");
     static_assert((NSLOT & (NSLOT - 1)) == 0, "ring depth is a power of two (slot = j & (NSLOT-1))");
     static_assert(VX % LV == 0 && HX % LV == 0 && TXP % LV == 0, "vector loads must stay aligned");
 };
@@ -114,11 +115,11 @@ __device__ __forceinline__ void ld_vec(const T *p, T (&dst)[N]) {
 // One xy-tile of one z-chunk: the whole 2.5D pipeline of a CTA.  `map` may point at a
 // __grid_constant__ parameter or at a descriptor in global memory (batched launches).
 // Returns false if a bounded wait expired (ERR_TIMEOUT recorded, loads drained).
-template <typename T, int VP, int BY, int RY, int ZB, int NSLOT, bool PK, bool PDL>
+template <typename T, int VP, int BY, int RY, int ZB, int NSLOT, bool PK, bool PDL, int R>
 __device__ __forceinline__ bool diffusion_tile(const CUtensorMap *map, T *__restrict__ out, const Geom &g,
                                                const DC<T> &c, int tile_x, int tile_y, int tile_z, int zc,
                                                int images, unsigned *err, T *ring, uint64_t *full) {
-    using Cfg = DiffCfg<T, VP, BY, RY, ZB, NSLOT>;
+    using Cfg = DiffCfg<T, VP, BY, RY, ZB, NSLOT, R>;
     using O = PairOps<T, PK>;
     using P = typename O::P;
     constexpr int VX = Cfg::VX, LV = Cfg::LV;
@@ -128,7 +129,7 @@ __device__ __forceinline__ bool diffusion_tile(const CUtensorMap *map, T *__rest
     const int nx = (int)g.n[0], ny = (int)g.n[1], nz = (int)g.n[2];
     const int zend = min(nz, zc0 + zc);
     const int count = zend - zc0;
-    const int nplanes = count + 2 * R6;  // planes zc0-3 .. zend+2
+    const int nplanes = count + 2 * R;  // planes zc0-R .. zend+R-1
     const int x = x0 + lane * VX;       // first of this thread's VX cells
     const int yb = y0 + wy * RY;        // first of its RY rows
 
@@ -144,8 +145,8 @@ __device__ __forceinline__ bool diffusion_tile(const CUtensorMap *map, T *__rest
     }
 
     const int bx = (int)g.off[0] + x0 - Cfg::HX;
-    const int by0 = (int)g.off[1] + y0 - R6;
-    const int bz0 = (int)g.off[2] + zc0 - R6;
+    const int by0 = (int)g.off[1] + y0 - R;
+    const int bz0 = (int)g.off[2] + zc0 - R;
     auto issue = [&](int j) {  // plane j (0-based from zc0-3) into its ring slot
         const int s = slot_of<NSLOT>(j);
         mbar_arrive_expect_tx(&full[s], Cfg::BOX_BYTES);
@@ -156,21 +157,21 @@ __device__ __forceinline__ bool diffusion_tile(const CUtensorMap *map, T *__rest
         for (; issued < NSLOT && issued < nplanes; ++issued) issue(issued);
 
     // element offset of (row 0 of this thread, first cell) inside a slot
-    const int own = (wy * RY + R6) * Cfg::TXP + Cfg::HX + lane * VX;
+    const int own = (wy * RY + R) * Cfg::TXP + Cfg::HX + lane * VX;
 
     // weights as pairs
     const P G0 = O::make(c.g0, c.g0);
-    P GA[3][3];
+    P GA[3][R];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int b = 0; b < 3; ++b) GA[a][b] = O::make(c.ga[a][b], c.ga[a][b]);
+        for (int b = 0; b < R; ++b) GA[a][b] = O::make(c.ga[a][b], c.ga[a][b]);
 
-    // z queue: Q[k] holds plane z-3+k of the iteration's first output plane z (k < ZB + 6)
-    P Q[ZB + 6][RY][VP];
+    // z queue: Q[k] holds plane z-R+k of the iteration's first output plane z (k < ZB + 2R)
+    P Q[ZB + 2 * R][RY][VP];
     bool ok = true;
 #pragma unroll
-    for (int j = 0; j < 2 * R6; ++j) {  // prologue: planes zc0-3 .. zc0+2 into Q[0..5]
+    for (int j = 0; j < 2 * R; ++j) {  // prologue: planes zc0-R .. zc0+R-1 into Q[0..2R-1]
         ok = ok && mbar_wait_bounded(&full[slot_of<NSLOT>(j)], parity_of<NSLOT>(j));
         const T *sp = ring + slot_of<NSLOT>(j) * Cfg::SLOT_ELEMS + own;
 #pragma unroll
@@ -188,7 +189,7 @@ __device__ __forceinline__ bool diffusion_tile(const CUtensorMap *map, T *__rest
     bool bad = __syncthreads_or(!ok);
     // planes j = 0..2 are never read from shared memory again: refill their slots
     if (!bad && threadIdx.x == 0)
-        for (; issued < NSLOT + R6 && issued < nplanes; ++issued) issue(issued);
+        for (; issued < NSLOT + R && issued < nplanes; ++issued) issue(issued);
 
     // Periodic images (Eq. 2) of this thread's cells.  z- and y-images repeat the row's vector
     // store at a shifted plane/row (warp-uniform).  x-images: threads holding cells within 4 of
@@ -205,13 +206,13 @@ __device__ __forceinline__ bool diffusion_tile(const CUtensorMap *map, T *__rest
     } else {
 #pragma unroll
         for (int u = 0; u < VX; ++u) {
-            if (x + u < R6) { xmask |= 1 << u; xshift = nx; }
-            else if (x + u >= nx - R6) { xmask |= 1 << u; xshift = -nx; }
+            if (x + u < R) { xmask |= 1 << u; xshift = nx; }
+            else if (x + u >= nx - R) { xmask |= 1 << u; xshift = -nx; }
         }
     }
     int yshift[RY];
 #pragma unroll
-    for (int r = 0; r < RY; ++r) yshift[r] = (yb + r < R6) ? ny : (yb + r >= ny - R6) ? -ny : 0;
+    for (int r = 0; r < RY; ++r) yshift[r] = (yb + r < R) ? ny : (yb + r >= ny - R) ? -ny : 0;
     if (!images) {
         xshift = 0;
         xmask = 0;
@@ -222,10 +223,10 @@ __device__ __forceinline__ bool diffusion_tile(const CUtensorMap *map, T *__rest
     T *optr = out + g.idx(x, yb, zc0);
 
     for (int m = 0; !bad && m < count; m += ZB) {
-        // leading planes j = m+6 .. m+5+ZB (those that exist) enter the queue at Q[6..]
+        // leading planes j = m+2R .. m+2R+ZB-1 (those that exist) enter the queue at Q[2R..]
 #pragma unroll
         for (int b = 0; b < ZB; ++b) {
-            const int jl = m + 2 * R6 + b;
+            const int jl = m + 2 * R + b;
             if (jl < nplanes) {
                 ok = ok && mbar_wait_bounded(&full[slot_of<NSLOT>(jl)], parity_of<NSLOT>(jl));
                 if (ok && any_cell) {
@@ -235,7 +236,7 @@ __device__ __forceinline__ bool diffusion_tile(const CUtensorMap *map, T *__rest
                         T le[VX];
                         ld_vec<T, LV>(lp + r * Cfg::TXP, le);
 #pragma unroll
-                        for (int p = 0; p < VP; ++p) Q[6 + b][r][p] = O::make(le[2 * p], le[2 * p + 1]);
+                        for (int p = 0; p < VP; ++p) Q[2 * R + b][r][p] = O::make(le[2 * p], le[2 * p + 1]);
                     }
                 }
             }
@@ -245,13 +246,13 @@ __device__ __forceinline__ bool diffusion_tile(const CUtensorMap *map, T *__rest
             for (int b = 0; b < ZB; ++b) {
                 if (m + b < count) {
                     const int z = zc0 + m + b;
-                    const T *cp = ring + slot_of<NSLOT>(m + b + R6) * Cfg::SLOT_ELEMS + own;
+                    const T *cp = ring + slot_of<NSLOT>(m + b + R) * Cfg::SLOT_ELEMS + own;
                     // y column: rows -3 .. RY+2 of this thread's cells, as pairs
-                    P Y[RY + 6][VP];
+                    P Y[RY + 2 * R][VP];
 #pragma unroll
-                    for (int d = 0; d < RY + 6; ++d) {
+                    for (int d = 0; d < RY + 2 * R; ++d) {
                         T e[VX];
-                        ld_vec<T, LV>(cp + (d - R6) * Cfg::TXP, e);
+                        ld_vec<T, LV>(cp + (d - R) * Cfg::TXP, e);
 #pragma unroll
                         for (int p = 0; p < VP; ++p) Y[d][p] = O::make(e[2 * p], e[2 * p + 1]);
                     }
@@ -264,26 +265,24 @@ __device__ __forceinline__ bool diffusion_tile(const CUtensorMap *map, T *__rest
 #pragma unroll
                         for (int p = 0; p < VP; ++p) {
                             const int i0 = 4 + 2 * p;  // E index of the pair's first cell
-                            P acc = O::mul(G0, Y[r + R6][p]);
-                            // x: even offset from aligned pairs, odd offsets from scalar adds
-                            const P sx1 = O::make(E[i0 + 1] + E[i0 - 1], E[i0 + 2] + E[i0]);
-                            const P sx2 = O::add(O::make(E[i0 + 2], E[i0 + 3]), O::make(E[i0 - 2], E[i0 - 1]));
-                            const P sx3 = O::make(E[i0 + 3] + E[i0 - 3], E[i0 + 4] + E[i0 - 2]);
-                            acc = O::fma2(GA[0][0], sx1, acc);
-                            acc = O::fma2(GA[1][0], O::add(Y[r + R6 + 1][p], Y[r + R6 - 1][p]), acc);
-                            acc = O::fma2(GA[2][0], O::add(Q[b + 4][r][p], Q[b + 2][r][p]), acc);
-                            acc = O::fma2(GA[0][1], sx2, acc);
-                            acc = O::fma2(GA[1][1], O::add(Y[r + R6 + 2][p], Y[r + R6 - 2][p]), acc);
-                            acc = O::fma2(GA[2][1], O::add(Q[b + 5][r][p], Q[b + 1][r][p]), acc);
-                            acc = O::fma2(GA[0][2], sx3, acc);
-                            acc = O::fma2(GA[1][2], O::add(Y[r + R6 + 3][p], Y[r + R6 - 3][p]), acc);
-                            acc = O::fma2(GA[2][2], O::add(Q[b + 6][r][p], Q[b][r][p]), acc);
+                            P acc = O::mul(G0, Y[r + R][p]);
+                            // offset a: x pairs from E (even offsets aligned, odd offsets two
+                            // scalar adds), then the y and z pairs
+#pragma unroll
+                            for (int a = 1; a <= R; ++a) {
+                                const P sx = (a % 2 == 0)
+                                                 ? O::add(O::make(E[i0 + a], E[i0 + 1 + a]), O::make(E[i0 - a], E[i0 + 1 - a]))
+                                                 : O::make(E[i0 + a] + E[i0 - a], E[i0 + 1 + a] + E[i0 + 1 - a]);
+                                acc = O::fma2(GA[0][a - 1], sx, acc);
+                                acc = O::fma2(GA[1][a - 1], O::add(Y[r + R + a][p], Y[r + R - a][p]), acc);
+                                acc = O::fma2(GA[2][a - 1], O::add(Q[b + R + a][r][p], Q[b + R - a][r][p]), acc);
+                            }
                             res[r][p] = acc;
                         }
                     }
                     T *op = optr + b * pitch_z;
                     if (full_tile) {
-                        const int zshift = images ? ((z < R6) ? nz : (z >= nz - R6) ? -nz : 0) : 0;
+                        const int zshift = images ? ((z < R) ? nz : (z >= nz - R) ? -nz : 0) : 0;
 #pragma unroll
                         for (int zi = 0; zi < 2; ++zi) {
                             if (zi == 1 && zshift == 0) break;
@@ -326,14 +325,14 @@ __device__ __forceinline__ bool diffusion_tile(const CUtensorMap *map, T *__rest
 #pragma unroll
                                 for (int u = 0; u < 2; ++u)
                                     if (x + 2 * p + u < nx && yb + r < ny)
-                                        store_with_images(out, g, R6, images != 0, x + 2 * p + u, yb + r, z, v2[u]);
+                                        store_with_images(out, g, R, images != 0, x + 2 * p + u, yb + r, z, v2[u]);
                             }
                     }
                 }
             }
             // shift the queue by ZB planes
 #pragma unroll
-            for (int k = 0; k < 6; ++k)
+            for (int k = 0; k < 2 * R; ++k)
 #pragma unroll
                 for (int r = 0; r < RY; ++r)
 #pragma unroll
@@ -343,7 +342,7 @@ __device__ __forceinline__ bool diffusion_tile(const CUtensorMap *map, T *__rest
         bad = __syncthreads_or(!ok);
         // planes j < m + ZB + 3 are retired: refill the ring up to NSLOT planes ahead
         if (!bad && threadIdx.x == 0) {
-            const int lim = min(nplanes, m + ZB + R6 + NSLOT);
+            const int lim = min(nplanes, m + ZB + R + NSLOT);
             for (; issued < lim; ++issued) issue(issued);
         }
     }
@@ -356,7 +355,7 @@ __device__ __forceinline__ bool diffusion_tile(const CUtensorMap *map, T *__rest
     return !bad;
 }
 
-template <typename T, int VP, int BY, int RY, int ZB, int NSLOT, bool PK>
+template <typename T, int VP, int BY, int RY, int ZB, int NSLOT, bool PK, int R>
 __global__ void __launch_bounds__(32 * BY)
 diffusion_kernel(const __grid_constant__ CUtensorMap map_in, T *__restrict__ out, Geom g, DC<T> c,
                  int zc, int images, unsigned *err) {
@@ -364,8 +363,8 @@ diffusion_kernel(const __grid_constant__ CUtensorMap map_in, T *__restrict__ out
     // TMA destinations are kept 128-byte aligned (dynamic smem has 128 spare bytes)
     T *ring = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     __shared__ __align__(8) uint64_t full[NSLOT];
-    diffusion_tile<T, VP, BY, RY, ZB, NSLOT, PK, true>(&map_in, out, g, c, blockIdx.x, blockIdx.y, blockIdx.z,
-                                                       zc, images, err, ring, full);
+    diffusion_tile<T, VP, BY, RY, ZB, NSLOT, PK, true, R>(&map_in, out, g, c, blockIdx.x, blockIdx.y, blockIdx.z,
+                                                          zc, images, err, ring, full);
 }
 
 // ------------------------------------------------------------------ variants / launch
@@ -400,15 +399,15 @@ int device_sms() {
     return sms[dev];
 }
 
-template <typename T, int VP, int BY, int RY, int ZB, int NSLOT, bool PK>
+template <typename T, int VP, int BY, int RY, int ZB, int NSLOT, bool PK, int R>
 static cudaError_t run(const CUtensorMap *map, void *out, const Geom &g, const DiffCoef &dc, bool images,
                        unsigned *err, cudaStream_t s) {
-    using Cfg = DiffCfg<T, VP, BY, RY, ZB, NSLOT>;
+    using Cfg = DiffCfg<T, VP, BY, RY, ZB, NSLOT, R>;
     DC<T> c;
     c.g0 = (T)dc.g0;
     for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) c.ga[a][b] = (T)dc.ga[a][b];
-    auto k = diffusion_kernel<T, VP, BY, RY, ZB, NSLOT, PK>;
+        for (int b = 0; b < 4; ++b) c.ga[a][b] = (T)dc.ga[a][b];
+    auto k = diffusion_kernel<T, VP, BY, RY, ZB, NSLOT, PK, R>;
     static int occ[64] = {};  // resident CTAs per SM, per device
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -431,48 +430,74 @@ static cudaError_t run(const CUtensorMap *map, void *out, const Geom &g, const D
                       err);
 }
 
-// Variant table: (VP pairs per row, BY warps, RY rows, ZB planes, NSLOT, packed FP32x2)
-// per dtype.  The autotuner times each on the problem and keeps the fastest.
+// Variant table: (VP pairs per row, BY warps, RY rows, ZB planes, NSLOT, packed FP32x2).  The
+// autotuner times each on the problem and keeps the fastest.  Radius 3 (the 6th-order step)
+// carries the tuned set; the other radii of the sweep use its first shape.
 #define DIFF_VARIANTS_F64(X) \
     X(1, 8, 1, 2, 8, false)  \
     X(1, 4, 1, 2, 8, false)  \
     X(1, 8, 1, 1, 8, false)  \
     X(1, 4, 2, 2, 8, false)
+#define DIFF_VARIANTS_F64_OTHER(X) X(1, 8, 1, 2, 8, false)
 static const char *F64_NAMES[] = {"vx2_by8_ry1_zb2_s8", "vx2_by4_ry1_zb2_s8", "vx2_by8_ry1_zb1_s8",
                                   "vx2_by4_ry2_zb2_s8"};
-int diffusion_num_variants(int dtype) { return dtype == 1 ? 4 : diffusion_f32_num_variants(); }
+static const char *F64_NAMES_OTHER[] = {"?", "f64_r1_vx2_by8_ry1_zb2_s8", "f64_r2_vx2_by8_ry1_zb2_s8", "?",
+                                        "f64_r4_vx2_by8_ry1_zb2_s8"};
 
-const char *diffusion_variant_name(int dtype, int v) {
-    if (dtype != 1) return diffusion_f32_variant_name(v);
-    if (v < 0 || v >= diffusion_num_variants(dtype)) return "?";
-    return F64_NAMES[v];
+int diffusion_num_variants(int dtype, int r) {
+    if (dtype != 1) return diffusion_f32_num_variants(r);
+    return r == 3 ? 4 : (r >= 1 && r <= 4 ? 1 : 0);
 }
 
-void diffusion_box(int dtype, int v, int box[3]) {
-    if (dtype != 1) return diffusion_f32_box(v, box);
+const char *diffusion_variant_name(int dtype, int r, int v) {
+    if (dtype != 1) return diffusion_f32_variant_name(r, v);
+    if (v < 0 || v >= diffusion_num_variants(dtype, r)) return "?";
+    return r == 3 ? F64_NAMES[v] : F64_NAMES_OTHER[r];
+}
+
+void diffusion_box(int dtype, int r, int v, int box[3]) {
+    if (dtype != 1) return diffusion_f32_box(r, v, box);
     int i = 0;
     auto put = [&](int vp, int by, int ry) {
-        if (i++ == v) { box[0] = 64 * vp + 8; box[1] = by * ry + 2 * R6; box[2] = 1; }
+        if (i++ == v) { box[0] = 64 * vp + 8; box[1] = by * ry + 2 * r; box[2] = 1; }
     };
 #define X(VP, BY, RY, ZB, NS, PK) put(VP, BY, RY);
-    DIFF_VARIANTS_F64(X)
+    if (r == 3) {
+        DIFF_VARIANTS_F64(X)
+    } else {
+        DIFF_VARIANTS_F64_OTHER(X)
+    }
 #undef X
+}
+
+template <int R>
+static cudaError_t dispatch_f64(int variant, const CUtensorMap *map, void *out, const Geom &g, const DiffCoef &c,
+                                bool images, unsigned *err, cudaStream_t s) {
+    using T = double;
+    int i = 0;
+    cudaError_t res = cudaErrorInvalidValue;
+#define X(VP, BY, RY, ZB, NS, PK) \
+    if (i++ == variant) res = run<T, VP, BY, RY, ZB, NS, PK, R>(map, out, g, c, images, err, s);
+    if constexpr (R == 3) {
+        DIFF_VARIANTS_F64(X)
+    } else {
+        DIFF_VARIANTS_F64_OTHER(X)
+    }
+#undef X
+    return res;
 }
 
 cudaError_t launch_diffusion(int dtype, const CUtensorMap *map, void *out, const Geom &g, const DiffCoef &c,
                              bool images, unsigned *err, cudaStream_t s, int variant) {
-    int i = 0;
-    cudaError_t res = cudaErrorInvalidValue;
-#define X(VP, BY, RY, ZB, NS, PK) \
-    if (i++ == variant) res = run<T, VP, BY, RY, ZB, NS, PK>(map, out, g, c, images, err, s);
-    if (dtype == 1) {
-        using T = double;
-        DIFF_VARIANTS_F64(X)
-    } else if (dtype == 2) {
-        return launch_diffusion_f32(map, static_cast<float *>(out), g, c, images, err, s, variant);
+    if (dtype == 2) return launch_diffusion_f32(map, static_cast<float *>(out), g, c, images, err, s, variant);
+    if (dtype != 1) return cudaErrorInvalidValue;
+    switch (c.r) {
+    case 1: return dispatch_f64<1>(variant, map, out, g, c, images, err, s);
+    case 2: return dispatch_f64<2>(variant, map, out, g, c, images, err, s);
+    case 3: return dispatch_f64<3>(variant, map, out, g, c, images, err, s);
+    case 4: return dispatch_f64<4>(variant, map, out, g, c, images, err, s);
+    default: return cudaErrorInvalidValue;
     }
-#undef X
-    return res;
 }
 
 }  // namespace stn

@@ -1,20 +1,22 @@
 // diffusion_f32.cu -- FP32 forward-Euler step of the 3D heat equation (Sec. 3.2, Eqs. 4-7).
 //
-// The Euler update and the three axis Laplacians fold into one 19-point cross-correlation
-// (Eqs. 5 and 7): f' = g0 f + sum_axes sum_{a=1..3} g_{axis,a} (f(+a) + f(-a)).
+// The Euler update and the three axis Laplacians fold into one star-shaped cross-correlation
+// (Eqs. 5 and 7): f' = g0 f + sum_axes sum_{a=1..R} g_{axis,a} (f(+a) + f(-a)), with the
+// order-2R central Laplacian of radius R = 1..4 (R = 3 is the 6th-order, 19-point stencil;
+// the other radii serve the radius sweep of Sec. 5.3).
 //
 // FP32 is bandwidth-class work on GB300 (8 B per cell-update against ~10 packed FP32
 // instructions), so this kernel is built to spend as few issue slots per cell as possible:
 //   * 2.5D z-streaming as in the FP64 kernel: a CTA owns a 128 x (BY RY) tile of the
-//     xy-plane and marches along a chunk of z; each padded plane tile (136 x (BY RY + 6))
+//     xy-plane and marches along a chunk of z; each padded plane tile (136 x (BY RY + 2R))
 //     arrives by one TMA load into a ring of NSLOT shared-memory slots (one mbarrier each).
 //   * A thread owns 4 consecutive x cells (one float4) in RY rows.  The z-columns of its cells
-//     (planes z-3 .. z+ZB+2) live in a register queue.  The queue is never shifted: the
+//     (planes z-R .. z+ZB+R-1) live in a register queue.  The queue is never shifted: the
 //     z-loop is unrolled over the queue's period and each unrolled iteration addresses the
 //     queue with a compile-time rotation, so advancing by ZB planes costs no moves.
-//   * The centre row of a cell comes from the queue; shared memory supplies only the six y
+//   * The centre row of a cell comes from the queue; shared memory supplies only the 2R y
 //     rows around the thread's RY rows (shared by those rows) and two 16-byte x-neighbour
-//     loads per row.  Pairs of cells use Blackwell's packed FP32x2 FMA/ADD.
+//     loads per row (x-4 .. x-1 and x+4 .. x+7 cover any R <= 4).  Pairs of cells use Blackwell's packed FP32x2 FMA/ADD.
 //   * Stores are one 16-byte vector per row.  Periodic images (Eq. 2) cost one predicated
 //     vector store on the two x-face lanes (XVEC: nx a multiple of 4, the 4th element lands in
 //     the row padding) or per-cell scalar stores otherwise; y- and z-images are behind one
@@ -25,7 +27,7 @@
 //   * Waits are bounded (globaltimer); on expiry the CTA records ERR_TIMEOUT, drains its
 //     in-flight TMA loads (again bounded) and returns.
 // The multiply-add order per cell is the same as the FP64 kernel's (x, y, z pairs of offset
-// 1, then 2, then 3), so results do not depend on the variant.
+// 1, then 2, ..., then R), so results do not depend on the variant.
 #include <algorithm>
 #include <type_traits>
 
@@ -38,48 +40,57 @@ constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
 
 struct Coef32 {
     float g0;
-    float ga[3][3];  // [axis][a-1]
+    float ga[3][4];  // [axis][a-1]
 };
 
-template <int BY, int RY, int ZB, int NSLOT>
+template <int BY, int RY, int ZB, int NSLOT, int R>
 struct H32 {
     static constexpr int TX = 128, HX = 4, TXP = TX + 2 * HX;
-    static constexpr int TY = BY * RY, ROWS = TY + 2 * R6;
+    static constexpr int TY = BY * RY, ROWS = TY + 2 * R;
     static constexpr int SLOT = ((TXP * ROWS * 4 + 127) / 128) * 128 / 4;  // floats, 128 B aligned
     static constexpr uint32_t BOX_BYTES = TXP * ROWS * 4;
     static constexpr size_t SMEM = (size_t)NSLOT * SLOT * 4 + 128;
-    static constexpr int S = ZB + 2 * R6;       // queue length (planes)
+    static constexpr int S = ZB + 2 * R;        // queue length (planes)
     static constexpr int U = S / gcd_c(S, ZB);  // iterations per queue period
-    static_assert(NSLOT >= ZB + R6 + 1, "ring: ZB + 3 planes in use plus one refill");
+    static_assert(R >= 1 && R <= HX, "radius 1..4: the x window holds 4 neighbours per side");
+    static_assert(NSLOT >= ZB + R + 1, "ring: ZB + R planes in use plus one refill");
     static_assert((NSLOT & (NSLOT - 1)) == 0, "ring depth is a power of two (slot = j & (NSLOT-1))");
     static_assert(ROWS <= 256, "TMA box extents are limited to 256");
-    static_assert(U <= 4, "the z-loop is unrolled over one queue period");
+    static_assert(U <= 5, "the z-loop is unrolled over one queue period");
 };
+
+// Calls f(rotation, m + k ZB) for k = 0 .. U-1: one queue period of iterations, each with its
+// compile-time rotation (k ZB) mod S.
+template <int ZB, int S, typename F, int... K>
+__device__ __forceinline__ void queue_period(F &f, int m, std::integer_sequence<int, K...>) {
+    (f(std::integral_constant<int, (K * ZB) % S>{}, m + K * ZB), ...);
+}
 
 __device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 __device__ __forceinline__ void stg4(float *p, const float4 v) { *reinterpret_cast<float4 *>(p) = v; }
 
 // Element-wise store of a (possibly overhanging) group of 4 cells with all periodic images.
-__device__ __noinline__ void store4_bounded(float *out, const Geom &g, int images, int x, int y, int z, float4 v) {
+__device__ __noinline__ void store4_bounded(float *out, const Geom &g, int r, int images, int x, int y, int z,
+                                           float4 v) {
     const float e[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
     for (int u = 0; u < 4; ++u)
-        if (x + u < g.n[0] && y < g.n[1]) store_with_images(out, g, R6, images != 0, x + u, y, z, e[u]);
+        if (x + u < g.n[0] && y < g.n[1]) store_with_images(out, g, r, images != 0, x + u, y, z, e[u]);
 }
 
 // One xy-tile of one z-chunk.  `map` may point at a __grid_constant__ parameter or at a
 // descriptor in global memory (batched launches).  Returns false if a bounded wait expired.
-template <int BY, int RY, int ZB, int NSLOT, bool XVEC, bool PDL>
+template <int BY, int RY, int ZB, int NSLOT, int R, bool XVEC, bool PDL>
 __device__ __forceinline__ bool heat32_tile(const CUtensorMap *map, float *__restrict__ out, const Geom &g,
                                             const Coef32 &c, int tile_x, int tile_y, int tile_z, int zc, int images,
                                             unsigned *err, float *ring, uint64_t *full) {
-    using Cfg = H32<BY, RY, ZB, NSLOT>;
+    using Cfg = H32<BY, RY, ZB, NSLOT, R>;
     constexpr int TXP = Cfg::TXP, S = Cfg::S;
     const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
     const int x0 = tile_x * Cfg::TX, y0 = tile_y * Cfg::TY, zc0 = tile_z * zc;
     const int nx = (int)g.n[0], ny = (int)g.n[1], nz = (int)g.n[2];
     const int count = min(nz, zc0 + zc) - zc0;
-    const int nplanes = count + 2 * R6;  // planes zc0-3 .. zc0+count+2
+    const int nplanes = count + 2 * R;  // planes zc0-R .. zc0+count+R-1
     const int x = x0 + 4 * lane, yb = y0 + wy * RY;
 
     if (threadIdx.x == 0) {
@@ -92,9 +103,9 @@ __device__ __forceinline__ bool heat32_tile(const CUtensorMap *map, float *__res
         pdl_launch_dependents();
         pdl_wait();
     }
-    const int bx = (int)g.off[0] + x0 - Cfg::HX, by0 = (int)g.off[1] + y0 - R6, bz0 = (int)g.off[2] + zc0 - R6;
+    const int bx = (int)g.off[0] + x0 - Cfg::HX, by0 = (int)g.off[1] + y0 - R, bz0 = (int)g.off[2] + zc0 - R;
     int issued = 0;
-    auto issue = [&](int j) {  // plane j (0-based from zc0-3) into its ring slot
+    auto issue = [&](int j) {  // plane j (0-based from zc0-R) into its ring slot
         const int s = j & (NSLOT - 1);
         mbar_arrive_expect_tx(&full[s], Cfg::BOX_BYTES);
         tma_load_3d(ring + s * Cfg::SLOT, map, &full[s], bx, by0, bz0 + j);
@@ -105,31 +116,31 @@ __device__ __forceinline__ bool heat32_tile(const CUtensorMap *map, float *__res
         for (; issued < NSLOT && issued < nplanes; ++issued) issue(issued);
 
     // float offset of (row 0 of this thread, first cell) inside a slot
-    const int own = (wy * RY + R6) * TXP + Cfg::HX + 4 * lane;
+    const int own = (wy * RY + R) * TXP + Cfg::HX + 4 * lane;
     const float2 G0 = make_float2(c.g0, c.g0);
-    float2 GA[3][3];
+    float2 GA[3][R];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int b = 0; b < 3; ++b) GA[a][b] = make_float2(c.ga[a][b], c.ga[a][b]);
+        for (int b = 0; b < R; ++b) GA[a][b] = make_float2(c.ga[a][b], c.ga[a][b]);
 
     // z queue: logical entry k of an iteration with rotation ROT is Q[(ROT + k) % S]; entry k
-    // holds plane (first output plane of the iteration) - 3 + k.
+    // holds plane (first output plane of the iteration) - R + k.
     float4 Q[S][RY];
     bool ok = true;
 #pragma unroll
-    for (int j = 0; j < 2 * R6; ++j) {  // prologue: planes zc0-3 .. zc0+2
+    for (int j = 0; j < 2 * R; ++j) {  // prologue: planes zc0-R .. zc0+R-1
         ok = ok && mbar_wait_bounded(&full[j & (NSLOT - 1)], parity(j));
         const float *sp = slot(j) + own;
 #pragma unroll
         for (int r = 0; r < RY; ++r) Q[j][r] = ok ? lds4(sp + r * TXP) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     bool bad = __syncthreads_or(!ok);
-    // planes 0..2 are never read from shared memory again: refill their slots
+    // planes 0..R-1 are never read from shared memory again: refill their slots
     if (!bad && threadIdx.x == 0)
-        for (; issued < NSLOT + R6 && issued < nplanes; ++issued) issue(issued);
+        for (; issued < NSLOT + R && issued < nplanes; ++issued) issue(issued);
 
-    // Store targets.  x-images: lanes whose cells lie within 4 (XVEC) or 3 of an x face.
+    // Store targets.  x-images: lanes whose cells lie within 4 (XVEC) or R of an x face.
     const bool full_tile = x + 4 <= nx && yb + RY <= ny;
     int xs = 0, xmask = 0;
     int ys[RY];
@@ -141,12 +152,12 @@ __device__ __forceinline__ bool heat32_tile(const CUtensorMap *map, float *__res
         } else {
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                if (x + u < R6) { xmask |= 1 << u; xs = nx; }
-                else if (x + u >= nx - R6 && x + u < nx) { xmask |= 1 << u; xs = -nx; }
+                if (x + u < R) { xmask |= 1 << u; xs = nx; }
+                else if (x + u >= nx - R && x + u < nx) { xmask |= 1 << u; xs = -nx; }
             }
         }
 #pragma unroll
-        for (int r = 0; r < RY; ++r) ys[r] = (yb + r < R6) ? ny : (yb + r >= ny - R6 ? -ny : 0);
+        for (int r = 0; r < RY; ++r) ys[r] = (yb + r < R) ? ny : (yb + r >= ny - R ? -ny : 0);
     }
     const bool xi = XVEC ? xs != 0 : xmask != 0;
     const int pitch_y = (int)g.pad[0];
@@ -167,48 +178,54 @@ __device__ __forceinline__ bool heat32_tile(const CUtensorMap *map, float *__res
     auto iter = [&](auto rot_c, int m) {
         constexpr int ROT = decltype(rot_c)::value;
         if (bad || m >= count) return;
-        // leading planes j = m+6 .. m+5+ZB enter the queue at logical entries 6 .. 5+ZB
+        // leading planes j = m+2R .. m+2R+ZB-1 enter the queue at logical entries 2R .. 2R+ZB-1
 #pragma unroll
         for (int b = 0; b < ZB; ++b) {
-            const int jl = m + 2 * R6 + b;
+            const int jl = m + 2 * R + b;
             if (jl < nplanes) {
                 ok = ok && mbar_wait_bounded(&full[jl & (NSLOT - 1)], parity(jl));
                 const float *lp = slot(jl) + own;
 #pragma unroll
-                for (int r = 0; r < RY; ++r) Q[(ROT + 2 * R6 + b) % S][r] = lds4(lp + r * TXP);
+                for (int r = 0; r < RY; ++r) Q[(ROT + 2 * R + b) % S][r] = lds4(lp + r * TXP);
             }
         }
         if (ok) {
 #pragma unroll
             for (int b = 0; b < ZB; ++b) {
                 if (m + b < count) {
-                    const float *cp = slot(m + b + R6) + own;
-                    float4 Yn[3], Yp[3];  // rows -1, -2, -3 and RY, RY+1, RY+2
+                    const float *cp = slot(m + b + R) + own;
+                    float4 Yn[R], Yp[R];  // rows -1 .. -R and RY .. RY+R-1
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) {
+                    for (int a = 0; a < R; ++a) {
                         Yn[a] = lds4(cp - (a + 1) * TXP);
                         Yp[a] = lds4(cp + (RY + a) * TXP);
                     }
                     auto row = [&](int d) -> float4 {  // row d of the centre plane
-                        return d < 0 ? Yn[-d - 1] : (d >= RY ? Yp[d - RY] : Q[(ROT + b + R6) % S][d]);
+                        return d < 0 ? Yn[-d - 1] : (d >= RY ? Yp[d - RY] : Q[(ROT + b + R) % S][d]);
                     };
                     float4 res[RY];
 #pragma unroll
                     for (int r = 0; r < RY; ++r) {
-                        const float4 C = Q[(ROT + b + R6) % S][r];
-                        const float4 L = lds4(cp + r * TXP - 4), R = lds4(cp + r * TXP + 4);
-                        // x pairs: even offsets are aligned pairs, odd offsets two scalar adds
-                        float2 sx[2][3], sy[2][3], sz[2][3];
-                        sx[0][0] = make_float2(C.y + L.w, C.z + C.x);
-                        sx[0][1] = __fadd2_rn(make_float2(C.z, C.w), make_float2(L.z, L.w));
-                        sx[0][2] = make_float2(C.w + L.y, R.x + L.z);
-                        sx[1][0] = make_float2(C.w + C.y, R.x + C.z);
-                        sx[1][1] = __fadd2_rn(make_float2(R.x, R.y), make_float2(C.x, C.y));
-                        sx[1][2] = make_float2(R.y + L.w, R.z + C.x);
+                        const float4 C = Q[(ROT + b + R) % S][r];
+                        const float4 Lv = lds4(cp + r * TXP - 4), Rv = lds4(cp + r * TXP + 4);
+                        // x window E[k] = cell x-4+k, k = 0..11
+                        const float E[12] = {Lv.x, Lv.y, Lv.z, Lv.w, C.x, C.y, C.z, C.w, Rv.x, Rv.y, Rv.z, Rv.w};
+                        float2 sx[2][R], sy[2][R], sz[2][R];
 #pragma unroll
-                        for (int a = 1; a <= 3; ++a) {
+                        for (int p = 0; p < 2; ++p)
+#pragma unroll
+                            for (int a = 1; a <= R; ++a) {
+                                const int c0 = 4 + 2 * p;  // E index of the pair's first cell
+                                if (a % 2 == 0)  // even offsets: aligned pairs, one packed add
+                                    sx[p][a - 1] = __fadd2_rn(make_float2(E[c0 + a], E[c0 + 1 + a]),
+                                                              make_float2(E[c0 - a], E[c0 + 1 - a]));
+                                else  // odd offsets: two scalar adds
+                                    sx[p][a - 1] = make_float2(E[c0 + a] + E[c0 - a], E[c0 + 1 + a] + E[c0 + 1 - a]);
+                            }
+#pragma unroll
+                        for (int a = 1; a <= R; ++a) {
                             const float4 yp = row(r + a), ym = row(r - a);
-                            const float4 zp = Q[(ROT + b + R6 + a) % S][r], zm = Q[(ROT + b + R6 - a) % S][r];
+                            const float4 zp = Q[(ROT + b + R + a) % S][r], zm = Q[(ROT + b + R - a) % S][r];
                             sy[0][a - 1] = __fadd2_rn(make_float2(yp.x, yp.y), make_float2(ym.x, ym.y));
                             sy[1][a - 1] = __fadd2_rn(make_float2(yp.z, yp.w), make_float2(ym.z, ym.w));
                             sz[0][a - 1] = __fadd2_rn(make_float2(zp.x, zp.y), make_float2(zm.x, zm.y));
@@ -219,7 +236,7 @@ __device__ __forceinline__ bool heat32_tile(const CUtensorMap *map, float *__res
                         for (int p = 0; p < 2; ++p) {
                             float2 acc = __fmul2_rn(G0, p ? make_float2(C.z, C.w) : make_float2(C.x, C.y));
 #pragma unroll
-                            for (int a = 0; a < 3; ++a) {
+                            for (int a = 0; a < R; ++a) {
                                 acc = __ffma2_rn(GA[0][a], sx[p][a], acc);
                                 acc = __ffma2_rn(GA[1][a], sy[p][a], acc);
                                 acc = __ffma2_rn(GA[2][a], sz[p][a], acc);
@@ -229,7 +246,7 @@ __device__ __forceinline__ bool heat32_tile(const CUtensorMap *map, float *__res
                         res[r] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
                     }
                     const int z = zc0 + m + b;
-                    const int zs = images ? (z < R6 ? nz : (z >= nz - R6 ? -nz : 0)) : 0;
+                    const int zs = images ? (z < R ? nz : (z >= nz - R ? -nz : 0)) : 0;
                     float *op = optr + b * pitch_z;
                     if (full_tile) {
 #pragma unroll
@@ -245,25 +262,21 @@ __device__ __forceinline__ bool heat32_tile(const CUtensorMap *map, float *__res
                         }
                     } else {
 #pragma unroll
-                        for (int r = 0; r < RY; ++r) store4_bounded(out, g, images, x, yb + r, z, res[r]);
+                        for (int r = 0; r < RY; ++r) store4_bounded(out, g, R, images, x, yb + r, z, res[r]);
                     }
                 }
             }
         }
         optr += ZB * pitch_z;
         bad = __syncthreads_or(!ok);
-        // planes j < m + ZB + 3 are retired: refill the ring up to NSLOT planes ahead
+        // planes j < m + ZB + R are retired: refill the ring up to NSLOT planes ahead
         if (!bad && threadIdx.x == 0) {
-            const int lim = min(nplanes, m + ZB + R6 + NSLOT);
+            const int lim = min(nplanes, m + ZB + R + NSLOT);
             for (; issued < lim; ++issued) issue(issued);
         }
     };
-    for (int m = 0; !bad && m < count; m += Cfg::U * ZB) {
-        iter(std::integral_constant<int, 0>{}, m);
-        if constexpr (Cfg::U > 1) iter(std::integral_constant<int, (1 * ZB) % S>{}, m + ZB);
-        if constexpr (Cfg::U > 2) iter(std::integral_constant<int, (2 * ZB) % S>{}, m + 2 * ZB);
-        if constexpr (Cfg::U > 3) iter(std::integral_constant<int, (3 * ZB) % S>{}, m + 3 * ZB);
-    }
+    for (int m = 0; !bad && m < count; m += Cfg::U * ZB)
+        queue_period<ZB, S>(iter, m, std::make_integer_sequence<int, Cfg::U>{});
     if (bad && threadIdx.x == 0) {
         atomicOr(err, ERR_TIMEOUT);
         // drain loads still in flight before the CTA's shared memory is released
@@ -273,33 +286,35 @@ __device__ __forceinline__ bool heat32_tile(const CUtensorMap *map, float *__res
     return !bad;
 }
 
-template <int BY, int RY, int ZB, int NSLOT, int MINB, bool XVEC>
+template <int BY, int RY, int ZB, int NSLOT, int R, int MINB, bool XVEC>
 __global__ void __launch_bounds__(32 * BY, MINB)
 heat32_kernel(const __grid_constant__ CUtensorMap map_in, float *__restrict__ out, Geom g, Coef32 c, int zc,
               int images, unsigned *err) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *ring = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     __shared__ __align__(8) uint64_t full[NSLOT];
-    heat32_tile<BY, RY, ZB, NSLOT, XVEC, true>(&map_in, out, g, c, blockIdx.x, blockIdx.y, blockIdx.z, zc, images,
-                                               err, ring, full);
+    heat32_tile<BY, RY, ZB, NSLOT, R, XVEC, true>(&map_in, out, g, c, blockIdx.x, blockIdx.y, blockIdx.z, zc,
+                                                  images, err, ring, full);
 }
 
 // Vector x-images need nx a multiple of 4 and one spare padding element beyond each x halo.
-__host__ __device__ bool xvec_ok(const Geom &g) { return g.n[0] % 4 == 0 && g.n[0] >= 8 && g.off[0] >= 4 && g.pad[0] >= g.off[0] + g.n[0] + 4; }
+__host__ __device__ bool xvec_ok(const Geom &g) {
+    return g.n[0] % 4 == 0 && g.n[0] >= 8 && g.off[0] >= 4 && g.pad[0] >= g.off[0] + g.n[0] + 4;
+}
 
 Coef32 coef32(const DiffCoef &dc) {
     Coef32 c;
     c.g0 = (float)dc.g0;
     for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) c.ga[a][b] = (float)dc.ga[a][b];
+        for (int b = 0; b < 4; ++b) c.ga[a][b] = (float)dc.ga[a][b];
     return c;
 }
 
-template <int BY, int RY, int ZB, int NSLOT, int MINB, bool XVEC>
+template <int BY, int RY, int ZB, int NSLOT, int R, int MINB, bool XVEC>
 cudaError_t run(const CUtensorMap *map, float *out, const Geom &g, const Coef32 &c, bool images, unsigned *err,
                 cudaStream_t s) {
-    using Cfg = H32<BY, RY, ZB, NSLOT>;
-    auto k = heat32_kernel<BY, RY, ZB, NSLOT, MINB, XVEC>;
+    using Cfg = H32<BY, RY, ZB, NSLOT, R>;
+    auto k = heat32_kernel<BY, RY, ZB, NSLOT, R, MINB, XVEC>;
     static int occ[64] = {};  // resident CTAs per SM, per device
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -321,45 +336,74 @@ cudaError_t run(const CUtensorMap *map, float *out, const Geom &g, const Coef32 
     return launch_pdl(k, grid, dim3(32 * BY), Cfg::SMEM, s, *map, out, g, c, zc, images ? 1 : 0, err);
 }
 
-// Variant table: (BY warps, RY rows, ZB planes per iteration, NSLOT ring depth, MINB resident
-// CTAs the register budget is sized for).  The autotuner times each on the problem.
-#define HEAT32_VARIANTS(X) \
-    X(4, 2, 2, 8, 3)       \
-    X(4, 1, 2, 8, 4)       \
-    X(8, 1, 2, 8, 2)       \
+// Variant tables: (BY warps, RY rows, ZB planes per iteration, NSLOT ring depth, MINB resident
+// CTAs the register budget is sized for).  The autotuner times each on the problem.  Radius 3
+// (the 6th-order step) carries the tuned set; the other radii of the sweep use its first shape.
+#define HEAT32_VARIANTS_R3(X) \
+    X(4, 2, 2, 8, 3)          \
+    X(4, 1, 2, 8, 4)          \
+    X(8, 1, 2, 8, 2)          \
     X(4, 1, 2, 8, 3)
+#define HEAT32_VARIANTS_OTHER(X) X(4, 2, 2, 8, 3)
 
-const char *const NAMES[] = {"f32_by4_ry2_zb2_s8_m3", "f32_by4_ry1_zb2_s8_m4", "f32_by8_ry1_zb2_s8_m2",
-                             "f32_by4_ry1_zb2_s8_m3"};
-constexpr int NVAR = 4;
+const char *const NAMES_R3[] = {"f32_by4_ry2_zb2_s8_m3", "f32_by4_ry1_zb2_s8_m4", "f32_by8_ry1_zb2_s8_m2",
+                                "f32_by4_ry1_zb2_s8_m3"};
+const char *const NAMES_OTHER[] = {"?", "f32_r1_by4_ry2_zb2_s8_m3", "f32_r2_by4_ry2_zb2_s8_m3", "?",
+                                   "f32_r4_by4_ry2_zb2_s8_m3"};
+
+template <int R>
+cudaError_t dispatch(int variant, const CUtensorMap *map, float *out, const Geom &g, const Coef32 &c, bool images,
+                     unsigned *err, cudaStream_t s) {
+    const bool xv = xvec_ok(g);
+    int i = 0;
+    cudaError_t res = cudaErrorInvalidValue;
+#define X(BY, RY, ZB, NS, MB)                                                          \
+    if (i++ == variant)                                                                \
+        res = xv ? run<BY, RY, ZB, NS, R, MB, true>(map, out, g, c, images, err, s) \
+                 : run<BY, RY, ZB, NS, R, MB, false>(map, out, g, c, images, err, s);
+    if constexpr (R == 3) {
+        HEAT32_VARIANTS_R3(X)
+    } else {
+        HEAT32_VARIANTS_OTHER(X)
+    }
+#undef X
+    return res;
+}
 
 }  // namespace
 
-int diffusion_f32_num_variants() { return NVAR; }
+int diffusion_f32_num_variants(int r) { return r == 3 ? 4 : (r >= 1 && r <= 4 ? 1 : 0); }
 
-const char *diffusion_f32_variant_name(int v) { return (v >= 0 && v < NVAR) ? NAMES[v] : "?"; }
+const char *diffusion_f32_variant_name(int r, int v) {
+    if (v < 0 || v >= diffusion_f32_num_variants(r)) return "?";
+    return r == 3 ? NAMES_R3[v] : NAMES_OTHER[r];
+}
 
-void diffusion_f32_box(int v, int box[3]) {
+void diffusion_f32_box(int r, int v, int box[3]) {
+    (void)v;  // every variant has the 128-wide tile; the rows depend on BY RY
     int i = 0;
+    box[0] = H32<1, 1, 2, 8, 1>::TXP;
+    box[2] = 1;
 #define X(BY, RY, ZB, NS, MB) \
-    if (i++ == v) { box[0] = H32<BY, RY, ZB, NS>::TXP; box[1] = H32<BY, RY, ZB, NS>::ROWS; box[2] = 1; }
-    HEAT32_VARIANTS(X)
+    if (i++ == v) box[1] = BY * RY + 2 * r;
+    if (r == 3) {
+        HEAT32_VARIANTS_R3(X)
+    } else {
+        HEAT32_VARIANTS_OTHER(X)
+    }
 #undef X
 }
 
 cudaError_t launch_diffusion_f32(const CUtensorMap *map, float *out, const Geom &g, const DiffCoef &dc, bool images,
                                  unsigned *err, cudaStream_t s, int variant) {
     const Coef32 c = coef32(dc);
-    const bool xv = xvec_ok(g);
-    int i = 0;
-    cudaError_t res = cudaErrorInvalidValue;
-#define X(BY, RY, ZB, NS, MB)                                                        \
-    if (i++ == variant)                                                              \
-        res = xv ? run<BY, RY, ZB, NS, MB, true>(map, out, g, c, images, err, s) \
-                 : run<BY, RY, ZB, NS, MB, false>(map, out, g, c, images, err, s);
-    HEAT32_VARIANTS(X)
-#undef X
-    return res;
+    switch (dc.r) {
+    case 1: return dispatch<1>(variant, map, out, g, c, images, err, s);
+    case 2: return dispatch<2>(variant, map, out, g, c, images, err, s);
+    case 3: return dispatch<3>(variant, map, out, g, c, images, err, s);
+    case 4: return dispatch<4>(variant, map, out, g, c, images, err, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 // ------------------------------------------------------------------ batched (serving)
@@ -367,7 +411,7 @@ cudaError_t launch_diffusion_f32(const CUtensorMap *map, float *out, const Geom 
 // The tile shape of variant f32_by4_ry2_zb2_s8_m3.
 namespace {
 constexpr int DB_BY = 4, DB_RY = 2, DB_ZB = 2, DB_NSLOT = 8, DB_MINB = 2;
-using DbCfg = H32<DB_BY, DB_RY, DB_ZB, DB_NSLOT>;
+using DbCfg = H32<DB_BY, DB_RY, DB_ZB, DB_NSLOT, R6>;
 }  // namespace
 
 __global__ void __launch_bounds__(32 * DB_BY, DB_MINB)
@@ -389,13 +433,15 @@ diffusion_batch_kernel(const BatchHeader *hdr, const BatchHeat *items, unsigned 
         const int ty = r % it.tiles_y, tz = r / it.tiles_y;
         Coef32 c;
         c.g0 = it.g0;
-        for (int a = 0; a < 3; ++a)
+        for (int a = 0; a < 3; ++a) {
             for (int b = 0; b < 3; ++b) c.ga[a][b] = it.ga[a][b];
+            c.ga[a][3] = 0.f;
+        }
         const Geom g = it.g;
         const bool ok = xvec_ok(g)
-                            ? heat32_tile<DB_BY, DB_RY, DB_ZB, DB_NSLOT, true, false>(it.map, it.out, g, c, tx, ty, tz, it.zc,
+                            ? heat32_tile<DB_BY, DB_RY, DB_ZB, DB_NSLOT, R6, true, false>(it.map, it.out, g, c, tx, ty, tz, it.zc,
                                                                                1, err, ring, full)
-                            : heat32_tile<DB_BY, DB_RY, DB_ZB, DB_NSLOT, false, false>(it.map, it.out, g, c, tx, ty, tz,
+                            : heat32_tile<DB_BY, DB_RY, DB_ZB, DB_NSLOT, R6, false, false>(it.map, it.out, g, c, tx, ty, tz,
                                                                                 it.zc, 1, err, ring, full);
         __syncthreads();
         if (!ok) return;

@@ -44,23 +44,31 @@ cudaError_t launch_xcorr(int dtype, int r, const void *in, void *out, const Geom
 int choose_zchunks(int tiles, int nz, int slots, double reread_weight);
 int device_sms();
 
-// DIFFUSION (Eqs. 4-7): one folded 19-point step, 3D, radius 3, read through TMA.
+// DIFFUSION (Eqs. 4-7): one folded forward-Euler step with the order-2r central Laplacian of
+// radius r = 1..4 (r = 3: the 6th-order, 19-point stencil in 3D).  1D runs through the XCORR
+// kernel with the folded weights; 2D and 3D have their own kernels, reading through TMA.
 struct DiffCoef {
-    double g0;       // centre weight 1 + dt*alpha*sum_axes c0/h^2
-    double ga[3][3]; // [axis][a-1] weight of the pair at offset +-a along axis
+    double g0;        // centre weight 1 + dt*alpha*sum_axes c0/h^2
+    double ga[3][4];  // [axis][a-1] weight of the pair at offset +-a along axis (0 beyond r)
+    int r;            // radius 1..4
 };
+// 3D
 cudaError_t launch_diffusion(int dtype, const CUtensorMap *map_in, void *out, const Geom &g,
                              const DiffCoef &c, bool images, unsigned *err, cudaStream_t s,
                              int variant);
-int diffusion_num_variants(int dtype);
-const char *diffusion_variant_name(int dtype, int variant);
-void diffusion_box(int dtype, int variant, int box[3]);  // TMA box (x, y, z) of a variant
+int diffusion_num_variants(int dtype, int r);
+const char *diffusion_variant_name(int dtype, int r, int variant);
+void diffusion_box(int dtype, int r, int variant, int box[3]);  // TMA box (x, y, z) of a variant
 // The FP32 kernel family (diffusion_f32.cu), reached through the functions above for dtype 2.
-int diffusion_f32_num_variants();
-const char *diffusion_f32_variant_name(int variant);
-void diffusion_f32_box(int variant, int box[3]);
+int diffusion_f32_num_variants(int r);
+const char *diffusion_f32_variant_name(int r, int variant);
+void diffusion_f32_box(int r, int variant, int box[3]);
 cudaError_t launch_diffusion_f32(const CUtensorMap *map_in, float *out, const Geom &g, const DiffCoef &c,
                                  bool images, unsigned *err, cudaStream_t s, int variant);
+// 2D (diffusion2d.cu): one TMA tile per CTA, no streaming axis.
+cudaError_t launch_diffusion2d(int dtype, const CUtensorMap *map_in, void *out, const Geom &g, const DiffCoef &c,
+                               bool images, unsigned *err, cudaStream_t s);
+void diffusion2d_box(int dtype, int r, int box[3]);
 
 // MHD8 (Eqs. A1-A4 + RK3).  Constants in the compute type are built inside mhd.cu.
 struct MhdConst {

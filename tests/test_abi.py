@@ -67,14 +67,17 @@ def _create(lib, ndim=3, dims=(16, 16, 16), radius=3, coeffs=None, nfields=1, bc
     (dict(ndim=4), _lib.STENCIL_EINVAL),
     (dict(dims=(0, 16, 16)), _lib.STENCIL_EINVAL),
     (dict(radius=-1), _lib.STENCIL_EINVAL),
-    (dict(radius=2), _lib.STENCIL_EINVAL),                      # diffusion is radius 3
+    (dict(radius=5), _lib.STENCIL_EUNSUPPORTED),                # diffusion radius 1..4
+    (dict(radius=0), _lib.STENCIL_EUNSUPPORTED),
+    (dict(kind=2, nfields=8, radius=2), _lib.STENCIL_EINVAL),   # MHD8 is radius 3
     (dict(dims=(6, 16, 16)), _lib.STENCIL_EINVAL),              # periodic extent < 2r+1
     (dict(params=False), _lib.STENCIL_EINVAL),
     (dict(nfields=2), _lib.STENCIL_EINVAL),
     (dict(kind=7), _lib.STENCIL_EINVAL),
     (dict(storage=9), _lib.STENCIL_EINVAL),
     (dict(storage=3, compute=2), _lib.STENCIL_EUNSUPPORTED),    # BF16 diffusion
-    (dict(ndim=2), _lib.STENCIL_EUNSUPPORTED),
+    (dict(kind=2, nfields=8, ndim=2, dims=(16, 16, 1)), _lib.STENCIL_EUNSUPPORTED),  # MHD8 is 3D
+    (dict(ndim=2, dims=(16, 6, 1), radius=3), _lib.STENCIL_EINVAL),  # periodic extent < 2r+1
     (dict(kind=2, nfields=8, bc=1), _lib.STENCIL_EUNSUPPORTED),  # MHD8 needs periodic
     (dict(kind=2, nfields=8, storage=0, compute=0), _lib.STENCIL_EUNSUPPORTED),
     (dict(kind=0, ndim=1, dims=(64, 1, 1), radius=3, nfields=1, coeffs=[1] * 6, storage=0, compute=0), _lib.STENCIL_EINVAL),
@@ -95,6 +98,17 @@ def test_null_plan_calls_are_rejected(lib):
     assert lib.stencil_sync(None, None) == _lib.STENCIL_EINVAL
     assert lib.stencil_set_variant(None, 0) == _lib.STENCIL_EINVAL
     lib.stencil_destroy(None)
+
+
+@pytest.mark.parametrize("ndim,dims,radius", [(1, (64, 1, 1), 1), (1, (9, 1, 1), 4), (2, (16, 9, 1), 4),
+                                              (2, (32, 32, 1), 2), (3, (16, 16, 16), 1), (3, (9, 9, 9), 4)])
+def test_diffusion_radius_sweep_plans_are_accepted(lib, ndim, dims, radius):
+    for storage in (1, 2):
+        st, plan, detail = _create(lib, ndim=ndim, dims=dims, radius=radius, storage=storage, compute=storage)
+        # argument validation accepts the plan; without a GPU the device allocation then fails
+        assert st in (0, _lib.STENCIL_ECUDA), detail
+        if st == 0:
+            lib.stencil_destroy(plan)
 
 
 def test_create_null_out_and_dims(lib):
