@@ -6,9 +6,11 @@
  * Graphics Processors: Performance and Tuning Strategies" (Pekkila et al., arXiv 2406.08923):
  *
  *   STENCIL_XCORR      1D cross-correlation f'_i = sum_{j=-r..r} g_j f^_{i+j}       (Sec. 3.1, Eq. 3)
- *   STENCIL_DIFFUSION  forward-Euler step of df/dt = alpha lap f with the 6th-order
- *                      central 2nd-derivative stencil per axis, folded into one
- *                      19-point cross-correlation                                  (Sec. 3.2, Eqs. 4-7)
+ *   STENCIL_DIFFUSION  forward-Euler step of df/dt = alpha lap f with the central
+ *                      2nd-derivative stencil of order 2r per axis (r = 1..4; r = 3 is
+ *                      the 6th-order case) in 1, 2 or 3 dimensions, folded into one
+ *                      star-shaped cross-correlation                               (Sec. 3.2, Eqs. 4-7;
+ *                                                                                   radius sweep, Sec. 5.3)
  *   STENCIL_MHD8       one 3-stage Runge-Kutta step of the 8-field non-ideal MHD system
  *                      in non-conservative form, 6th-order central 1st, 2nd and mixed
  *                      derivatives fused with the nonlinear right-hand side          (Sec. 3.3, Eqs. 8-9,
@@ -67,7 +69,7 @@ typedef enum stencil_bc {
 
 typedef enum stencil_kind {
     STENCIL_XCORR = 0,     /* Eq. 3, ndim = 1, radius 0..4, caller weights g_{-r..r} */
-    STENCIL_DIFFUSION = 1, /* Eqs. 4-7, ndim = 3, radius 3 */
+    STENCIL_DIFFUSION = 1, /* Eqs. 4-7, ndim = 1..3, radius 1..4 (order-2r Laplacian) */
     STENCIL_MHD8 = 2       /* Eqs. A1-A4 + RK3, ndim = 3, radius 3, 8 fields */
 } stencil_kind;
 
@@ -93,10 +95,12 @@ enum { STENCIL_MHD_LNRHO = 0, STENCIL_MHD_UX, STENCIL_MHD_UY, STENCIL_MHD_UZ,
 /*
  * stencil_create -- validate a problem and build a plan (Sec. 2.4 Eq. 2 for the layout).
  *
- *   ndim     1 (XCORR) or 3 (DIFFUSION, MHD8).
+ *   ndim     1 (XCORR), 1..3 (DIFFUSION) or 3 (MHD8).
  *   dims     interior extents (nx, ny, nz); entries beyond ndim are ignored.  With periodic
  *            boundaries each used extent must be >= 2*radius + 1.
- *   radius   stencil radius r: 0..4 for XCORR, 3 for DIFFUSION and MHD8.
+ *   radius   stencil radius r: 0..4 for XCORR; 1..4 for DIFFUSION (the central Laplacian of
+ *            order 2r; r = 3 is the 6th-order, 19-point step of Eq. 7; the other radii serve the
+ *            radius sweep of Sec. 5.3); 3 for MHD8.
  *   coeffs   XCORR only: 2r+1 weights g_{-r..r}, int32_t for STENCIL_I32, double otherwise
  *            (rounded to FP32 for STENCIL_F32).  Copied; may be freed after the call.
  *            NULL for the other kinds.
