@@ -60,6 +60,10 @@ def _load():
                 "oracle_diffusion_box": (None, [P, I64, I64, I64, D, D, P, P]),
                 "oracle_diffusion": (I, [P, I64, I64, I64, D, D, P, I, P]),
                 "oracle_diffusion_r_box": (I, [P, I64, I64, I64, I, D, D, P, P]),
+                "oracle_maxfilter1d_box_f64": (None, [P, I64, I, P]),
+                "oracle_maxfilter1d_box_i32": (None, [P, I64, I, P]),
+                "oracle_maxfilter1d_f64": (I, [P, I64, I, I, P]),
+                "oracle_maxfilter1d_i32": (I, [P, I64, I, I, P]),
                 "oracle_diffusion_r": (I, [P, I64, I64, I64, I, D, D, P, I, P]),
                 "oracle_mhd_rhs_box": (None, [P, I64, I64, I64, P, P]),
                 "oracle_mhd_rk3": (I, [P, I64, I64, I64, P, D, I]),
@@ -142,6 +146,37 @@ def xcorr1d(data: np.ndarray, g: np.ndarray, sweeps: int = 1) -> np.ndarray:
 
 
 # -------------------------------------------------- Sec. 3.3 (central differences)
+
+
+def maxfilter1d_box(fhat: np.ndarray, r: int) -> np.ndarray:
+    """One max-filter sweep f'_i = max_{j=-r..r} f^_{i+j} over a padded 1D array (caller halo of
+    width r).  int32 data stay int32; anything else is evaluated in FP64."""
+    fhat = np.asarray(fhat)
+    n = len(fhat) - 2 * r
+    if fhat.dtype.kind in "iu":
+        fh = _c(fhat, np.int32)
+        out = np.empty(n, dtype=np.int32)
+        _load().oracle_maxfilter1d_box_i32(_p(fh), n, r, _p(out))
+        return out
+    fh = _c(fhat, np.float64)
+    out = np.empty(n, dtype=np.float64)
+    _load().oracle_maxfilter1d_box_f64(_p(fh), n, r, _p(out))
+    return out
+
+
+def maxfilter1d(data: np.ndarray, r: int, sweeps: int = 1) -> np.ndarray:
+    """`sweeps` periodic max-filter sweeps (the nonlinear stencil of Sec. 2.1)."""
+    data = np.asarray(data)
+    n = len(data)
+    if data.dtype.kind in "iu":
+        d = _c(data, np.int32)
+        out = np.empty(n, dtype=np.int32)
+        assert _load().oracle_maxfilter1d_i32(_p(d), n, r, sweeps, _p(out)) == 0
+        return out
+    d = _c(data, np.float64)
+    out = np.empty(n, dtype=np.float64)
+    assert _load().oracle_maxfilter1d_f64(_p(d), n, r, sweeps, _p(out)) == 0
+    return out
 
 
 def derivs_box(fhat: np.ndarray, h) -> np.ndarray:

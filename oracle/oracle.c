@@ -12,6 +12,8 @@
  *              the halo of width r holds the periodic image of the interior (Sec. 2.4).
  *   zeta       the discrete cross-correlation f'_i = sum_{j=-r..r} g_j f^_{i+j}, Eq. 3
  *              (Sec. 3.1).
+ *   maxfilter  the nonlinear 1D stencil f'_i = max_{j=-r..r} f^_{i+j} (max filtering, Sec. 2.1),
+ *              evaluated as the plain maximum over each window.
  *   diffusion  one forward-Euler step of df/dt = alpha lap f, Eq. 4 (Sec. 3.2), evaluated
  *              literally as f + dt*alpha*(sum over axes of the 2nd-derivative stencil); the
  *              folded single-kernel form of Eqs. 5-7 is the CUDA path's business, not ours.
@@ -126,6 +128,55 @@ int oracle_xcorr1d_u32(const uint32_t *in, int64_t n, const int32_t *g, int r, i
         oracle_xcorr1d_box_u32(hat, n, g, r, cur);
     }
     memcpy(out, cur, sizeof(uint32_t) * n);
+    free(cur); free(hat);
+    return 0;
+}
+
+/* ------------------------------------------ max filtering (nonlinear stencil, Sec. 2.1) */
+
+void oracle_maxfilter1d_box_f64(const double *fhat, int64_t n, int r, double *out) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double m = fhat[i];
+        for (int j = 1; j <= 2 * r; ++j)
+            if (fhat[i + j] > m) m = fhat[i + j];
+        out[i] = m;
+    }
+}
+
+void oracle_maxfilter1d_box_i32(const int32_t *fhat, int64_t n, int r, int32_t *out) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        int32_t m = fhat[i];
+        for (int j = 1; j <= 2 * r; ++j)
+            if (fhat[i + j] > m) m = fhat[i + j];
+        out[i] = m;
+    }
+}
+
+/* `sweeps` periodic max-filter sweeps, each feeding the next. */
+int oracle_maxfilter1d_f64(const double *in, int64_t n, int r, int sweeps, double *out) {
+    double *cur = malloc(sizeof(double) * n), *hat = malloc(sizeof(double) * (n + 2 * r));
+    if (!cur || !hat) { free(cur); free(hat); return -1; }
+    memcpy(cur, in, sizeof(double) * n);
+    for (int s = 0; s < sweeps; ++s) {
+        pad_periodic(cur, n, 1, 1, r, sizeof(double), hat);
+        oracle_maxfilter1d_box_f64(hat, n, r, cur);
+    }
+    memcpy(out, cur, sizeof(double) * n);
+    free(cur); free(hat);
+    return 0;
+}
+
+int oracle_maxfilter1d_i32(const int32_t *in, int64_t n, int r, int sweeps, int32_t *out) {
+    int32_t *cur = malloc(sizeof(int32_t) * n), *hat = malloc(sizeof(int32_t) * (n + 2 * r));
+    if (!cur || !hat) { free(cur); free(hat); return -1; }
+    memcpy(cur, in, sizeof(int32_t) * n);
+    for (int s = 0; s < sweeps; ++s) {
+        pad_periodic(cur, n, 1, 1, r, sizeof(int32_t), hat);
+        oracle_maxfilter1d_box_i32(hat, n, r, cur);
+    }
+    memcpy(out, cur, sizeof(int32_t) * n);
     free(cur); free(hat);
     return 0;
 }
