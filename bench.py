@@ -310,6 +310,44 @@ def run_radius_sweep(L, synth, stream, hbm_peak):
     return out
 
 
+FP32_MEASURED_TFLOPS = 74.3  # FP32 FMA probe on GB300 (152 SMs x 128 lanes at ~1.9 GHz under load)
+
+
+def run_xcorr_radius_sweep(L, synth, stream, hbm_peak):
+    """1D cross-correlation (Eq. 3) and max filter (Sec. 2.1) over the radius sweep of Sec. 5.2
+    (Fig. 8): 2^24 cells (64 MiB FP32, 128 MiB FP64), r = 0 .. 1024.  Radius <= 4 runs the
+    temporally blocked kernel (16 sweeps per launch); larger radii one sweep per launch.
+    Cross-correlation at large radius is FMA bound: 2 (2r+1) flop per output."""
+    out = {}
+    n = 1 << 24
+    radii = (0, 1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024)
+    base = synth.uniform(2406089239, 1, n, 0.0, 1.0)
+    for st, name, esize, peak in ((L.STENCIL_F32, "fp32", 4, FP32_MEASURED_TFLOPS), (L.STENCIL_F64, "fp64", 8, FP64_PEAK_TFLOPS)):
+        for kind, kname in ((L.STENCIL_XCORR, "xcorr"), (L.STENCIL_MAXFILTER, "maxfilter")):
+            for r in radii:
+                g = None
+                if kind == L.STENCIL_XCORR:
+                    g = synth.uniform(2406089239, 10 + r, 2 * r + 1, 0.0, 1.0)
+                    g = g / g.sum()
+                p = L.Plan(1, (n,), r, 1, L.STENCIL_BC_PERIODIC, kind, st, st, coeffs=g)
+                a, b = p.alloc(), p.alloc()
+                p.upload(a, [base])
+                k = 16 if (kind == L.STENCIL_XCORR and r <= 4) else (1 if (st == L.STENCIL_F64 and r >= 256) else 4)
+                p.step(a, b, k, stream)
+                ms = _timed(lambda: p.step(a, b, k, stream), 2, stream) / k
+                gbs = n * 2.0 * esize / (ms / 1e3) / 1e9
+                ent = {"ms_per_sweep": round(ms, 5), "gcell_per_s": round(n / (ms / 1e3) / 1e9, 2),
+                       "hbm_gbs_at_1r1w": round(gbs, 1), "frac_of_hbm": round(gbs / hbm_peak, 4)}
+                if kind == L.STENCIL_XCORR:
+                    tf = n * 2.0 * (2 * r + 1) / (ms / 1e3) / 1e12
+                    ent["tflops"] = round(tf, 3)
+                    ent["frac_of_fma_peak"] = round(tf / peak, 4)
+                out[f"{kname}_{name}_r{r}"] = ent
+                p.close()
+                del a, b
+    return out
+
+
 def run_serving_leg(n_requests=1024, load=0.7, fp64_subset=96, sweep=(0.5, 1.2)):
     """Serving configuration: 1024 requests (log-uniform 32^3..192^3, mixed kinds, 10-50
     steps, FP32) through the continuous-batching server under a 120 GB budget.
@@ -519,6 +557,7 @@ def run_ours(args):
     if not args.no_extras:
         extras = run_extras(L, synth, stream, hbm_peak, args)
         extras["diffusion_radius_sweep"] = run_radius_sweep(L, synth, stream, hbm_peak)
+        extras["xcorr_maxfilter_radius_sweep"] = run_xcorr_radius_sweep(L, synth, stream, hbm_peak)
         if world == 1:
             extras["serving"] = run_serving_leg()
 
@@ -683,8 +722,11 @@ def main():
         from paper_2406_08923_gb300 import _lib as L
         from paper_2406_08923_gb300 import synth
         L.load()
-        res = run_radius_sweep(L, synth, torch.cuda.current_stream(), _peaks()[0])
-        print(json.dumps({"metric": "diffusion_radius_sweep_ms_per_step", "radius_sweep": res}), flush=True)
+        st, hbm = torch.cuda.current_stream(), _peaks()[0]
+        res = run_radius_sweep(L, synth, st, hbm)
+        res1 = run_xcorr_radius_sweep(L, synth, st, hbm)
+        print(json.dumps({"metric": "radius_sweep_ms_per_step", "diffusion": res, "xcorr_maxfilter_1d": res1}),
+              flush=True)
         return 0
     if args.serving:
         print(json.dumps({"metric": "serving_p50_p99_latency_and_mcell_updates_per_s", "serving": run_serving_leg()}),

@@ -15,6 +15,8 @@
  *                      in non-conservative form, 6th-order central 1st, 2nd and mixed
  *                      derivatives fused with the nonlinear right-hand side          (Sec. 3.3, Eqs. 8-9,
  *                                                                                   Appendix A, Eqs. A1-A4)
+ *   STENCIL_MAXFILTER  1D max filter f'_i = max_{j=-r..r} f^_{i+j}, the nonlinear
+ *                      stencil example                                             (Sec. 2.1)
  *
  * Arrays are "augmented" arrays f^ (Sec. 2.4, Eq. 2): the interior is surrounded by a halo of
  * width r whose values are the boundary function beta.  With STENCIL_BC_PERIODIC the library
@@ -68,9 +70,10 @@ typedef enum stencil_bc {
 } stencil_bc;
 
 typedef enum stencil_kind {
-    STENCIL_XCORR = 0,     /* Eq. 3, ndim = 1, radius 0..4, caller weights g_{-r..r} */
+    STENCIL_XCORR = 0,     /* Eq. 3, ndim = 1, radius 0..1024, caller weights g_{-r..r} */
     STENCIL_DIFFUSION = 1, /* Eqs. 4-7, ndim = 1..3, radius 1..4 (order-2r Laplacian) */
-    STENCIL_MHD8 = 2       /* Eqs. A1-A4 + RK3, ndim = 3, radius 3, 8 fields */
+    STENCIL_MHD8 = 2,      /* Eqs. A1-A4 + RK3, ndim = 3, radius 3, 8 fields */
+    STENCIL_MAXFILTER = 3  /* Sec. 2.1 nonlinear stencil max_{j=-r..r} f^_{i+j}, ndim = 1, radius 0..1024 */
 } stencil_kind;
 
 /* Physical constants.  Unused members are ignored by kinds that do not need them. */
@@ -95,27 +98,30 @@ enum { STENCIL_MHD_LNRHO = 0, STENCIL_MHD_UX, STENCIL_MHD_UY, STENCIL_MHD_UZ,
 /*
  * stencil_create -- validate a problem and build a plan (Sec. 2.4 Eq. 2 for the layout).
  *
- *   ndim     1 (XCORR), 1..3 (DIFFUSION) or 3 (MHD8).
+ *   ndim     1 (XCORR, MAXFILTER), 1..3 (DIFFUSION) or 3 (MHD8).
  *   dims     interior extents (nx, ny, nz); entries beyond ndim are ignored.  With periodic
  *            boundaries each used extent must be >= 2*radius + 1.
- *   radius   stencil radius r: 0..4 for XCORR; 1..4 for DIFFUSION (the central Laplacian of
+ *   radius   stencil radius r: 0..1024 for XCORR (radius > 4: F64 and F32 only; the radius
+ *            sweep of Sec. 5.2) and MAXFILTER; 1..4 for DIFFUSION (the central Laplacian of
  *            order 2r; r = 3 is the 6th-order, 19-point step of Eq. 7; the other radii serve the
  *            radius sweep of Sec. 5.3); 3 for MHD8.
  *   coeffs   XCORR only: 2r+1 weights g_{-r..r}, int32_t for STENCIL_I32, double otherwise
  *            (rounded to FP32 for STENCIL_F32).  Copied; may be freed after the call.
  *            NULL for the other kinds.
  *   ncoeffs  2r+1 for XCORR, 0 otherwise.
- *   nfields  1 for XCORR and DIFFUSION, 8 for MHD8.
+ *   nfields  1 for XCORR, MAXFILTER and DIFFUSION, 8 for MHD8.
  *   storage  element type of the caller's arrays; compute = arithmetic type:
- *              XCORR:     I32/I32, F64/F64, F32/F32
+ *              XCORR:     I32/I32 (radius <= 4), F64/F64, F32/F32
+ *              MAXFILTER: I32/I32, F64/F64, F32/F32 (exact: the result equals the definition)
  *              DIFFUSION: F64/F64, F32/F32
  *              MHD8:      F64/F64, F32/F32, BF16/F32 (F32 and BF16 storage use
  *                         Kahan-compensated RK accumulation)
- *   params   physical constants (may be NULL for XCORR).
+ *   params   physical constants (may be NULL for XCORR and MAXFILTER).
  *   out      receives the plan.
  *
  * The only call that allocates device memory: library-owned scratch (one extra field set for
- * ping-pong, the RK register and Kahan compensation arrays for MHD8, reduction buffers).
+ * ping-pong, the RK register and Kahan compensation arrays for MHD8, reduction buffers, and
+ * for XCORR of radius > 4 a device copy of the weights).
  * Returns EINVAL on invalid arguments, EUNSUPPORTED on valid but unimplemented
  * combinations, ENOMEM/ECUDA if the scratch allocation fails (nothing is leaked).
  */
@@ -144,6 +150,7 @@ stencil_status stencil_layout(stencil_t plan, int64_t padded[3], int64_t pitch[3
  * stencil_step -- advance `nsteps` iterations (Sec. 2.4: f'_i = zeta(f^, i) for all i).
  *
  *   XCORR      nsteps sweeps of Eq. 3 (each sweep feeds the next).
+ *   MAXFILTER  nsteps max-filter sweeps (each sweep feeds the next).
  *   DIFFUSION  nsteps forward-Euler steps of Eqs. 4-7.
  *   MHD8       nsteps RK3 steps (3 substeps each) of Eqs. A1-A4.
  *
@@ -152,7 +159,7 @@ stencil_status stencil_layout(stencil_t plan, int64_t padded[3], int64_t pitch[3
  * interior of fields_in is not modified.  With STENCIL_BC_PERIODIC the halo of fields_in
  * is (re)filled first and the halo of fields_out is valid on return; with
  * STENCIL_BC_CALLER the halo of fields_in must be filled by the caller, nsteps must be 1
- * and the kind must be XCORR or DIFFUSION.  Asynchronous on `stream`: no host sync, no
+ * and the kind must be XCORR, MAXFILTER or DIFFUSION.  Asynchronous on `stream`: no host sync, no
  * allocation, safe to capture in a CUDA graph.  Bounded device waits that expire are
  * reported by the next stencil_sync / stencil_field_norms on the plan.
  */

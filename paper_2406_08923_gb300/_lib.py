@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(HERE, "libstencil.so")
 STENCIL_OK, STENCIL_EINVAL, STENCIL_ENOMEM, STENCIL_ECUDA, STENCIL_EUNSUPPORTED, STENCIL_ETIMEOUT = range(6)
 STENCIL_I32, STENCIL_F64, STENCIL_F32, STENCIL_BF16 = range(4)
 STENCIL_BC_PERIODIC, STENCIL_BC_CALLER = range(2)
-STENCIL_XCORR, STENCIL_DIFFUSION, STENCIL_MHD8 = range(3)
+STENCIL_XCORR, STENCIL_DIFFUSION, STENCIL_MHD8, STENCIL_MAXFILTER = range(4)
 
 EXPORTED = (
     "stencil_create", "stencil_destroy", "stencil_layout", "stencil_step", "stencil_halo_fill",

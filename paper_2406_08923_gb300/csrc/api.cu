@@ -82,6 +82,7 @@ struct stencil_plan {
     double *partials = nullptr;
     double *red_out = nullptr;
     unsigned *err = nullptr;
+    void *wdev = nullptr;  // XCORR of radius > 4: the 2r+1 weights on the device (storage type)
     int variant = 0;
     std::vector<TmaEntry> tma;
     std::string detail;
@@ -135,8 +136,10 @@ static void free_scratch(stencil_t p) {
     if (p->partials) cudaFree(p->partials);
     if (p->red_out) cudaFree(p->red_out);
     if (p->err) cudaFree(p->err);
+    if (p->wdev) cudaFree(p->wdev);
     p->partials = p->red_out = nullptr;
     p->err = nullptr;
+    p->wdev = nullptr;
 }
 
 // Encode (or fetch from the per-plan cache) the TMA descriptor of a field for a box shape.
@@ -233,7 +236,7 @@ stencil_status stencil_create(int ndim, const int64_t dims[3], int radius, const
     if (!out) return fail(nullptr, STENCIL_EINVAL, "out is NULL");
     *out = nullptr;
     if (!dims) return fail(nullptr, STENCIL_EINVAL, "dims is NULL");
-    if ((int)kind < 0 || (int)kind > 2) return fail(nullptr, STENCIL_EINVAL, "unknown kind");
+    if ((int)kind < 0 || (int)kind > 3) return fail(nullptr, STENCIL_EINVAL, "unknown kind");
     if ((int)bc < 0 || (int)bc > 1) return fail(nullptr, STENCIL_EINVAL, "unknown boundary condition");
     if ((int)storage < 0 || (int)storage > 3 || (int)compute < 0 || (int)compute > 3)
         return fail(nullptr, STENCIL_EINVAL, "unknown dtype");
@@ -246,12 +249,21 @@ stencil_status stencil_create(int ndim, const int64_t dims[3], int radius, const
     // kind-specific rules
     if (kind == STENCIL_XCORR) {
         if (ndim != 1) return fail(nullptr, STENCIL_EUNSUPPORTED, "XCORR supports ndim = 1");
-        if (radius > 4) return fail(nullptr, STENCIL_EUNSUPPORTED, "XCORR supports radius 0..4");
+        if (radius > 1024) return fail(nullptr, STENCIL_EUNSUPPORTED, "XCORR supports radius 0..1024");
         if (ncoeffs != 2 * radius + 1 || !coeffs)
             return fail(nullptr, STENCIL_EINVAL, "XCORR needs 2*radius+1 coefficients");
         if (nfields != 1) return fail(nullptr, STENCIL_EINVAL, "XCORR needs nfields = 1");
         if (storage != compute || storage == STENCIL_BF16)
             return fail(nullptr, STENCIL_EUNSUPPORTED, "XCORR supports I32/I32, F64/F64, F32/F32");
+        if (radius > 4 && storage == STENCIL_I32)
+            return fail(nullptr, STENCIL_EUNSUPPORTED, "XCORR of radius > 4 supports F64/F64 and F32/F32");
+    } else if (kind == STENCIL_MAXFILTER) {
+        if (ndim != 1) return fail(nullptr, STENCIL_EUNSUPPORTED, "MAXFILTER supports ndim = 1");
+        if (radius > 1024) return fail(nullptr, STENCIL_EUNSUPPORTED, "MAXFILTER supports radius 0..1024");
+        if (ncoeffs != 0) return fail(nullptr, STENCIL_EINVAL, "MAXFILTER takes no coefficients");
+        if (nfields != 1) return fail(nullptr, STENCIL_EINVAL, "MAXFILTER needs nfields = 1");
+        if (storage != compute || storage == STENCIL_BF16)
+            return fail(nullptr, STENCIL_EUNSUPPORTED, "MAXFILTER supports I32/I32, F64/F64, F32/F32");
     } else {
         if (kind == STENCIL_DIFFUSION && (radius < 1 || radius > 4))
             return fail(nullptr, STENCIL_EUNSUPPORTED, "DIFFUSION supports radius 1..4");
@@ -312,7 +324,11 @@ stencil_status stencil_create(int ndim, const int64_t dims[3], int radius, const
     p->bytes_per_field = g.pad[0] * g.pad[1] * g.pad[2] * p->esize;
 
     // coefficients / constants
-    if (kind == STENCIL_XCORR) {
+    std::vector<double> wide_w;  // XCORR radius > 4: weights copied to the device below
+    if (kind == STENCIL_XCORR && radius > 4) {
+        wide_w.assign(static_cast<const double *>(coeffs), static_cast<const double *>(coeffs) + ncoeffs);
+    } else if (kind == STENCIL_MAXFILTER) {
+    } else if (kind == STENCIL_XCORR) {
         for (int j = 0; j < ncoeffs; ++j) {
             if (storage == STENCIL_I32) p->gi[j] = static_cast<const int32_t *>(coeffs)[j];
             else {
@@ -400,6 +416,15 @@ stencil_status stencil_create(int ndim, const int64_t dims[3], int radius, const
     if (okay) okay = alloc((void **)&p->partials, sizeof(double) * norms_blocks() * nfields * 4, "cudaMalloc(norm partials)");
     if (okay) okay = alloc((void **)&p->red_out, sizeof(double) * nfields * 4, "cudaMalloc(norm result)");
     if (okay) okay = alloc((void **)&p->err, sizeof(unsigned), "cudaMalloc(error word)");
+    if (okay && !wide_w.empty()) {
+        okay = alloc(&p->wdev, wide_w.size() * p->esize, "cudaMalloc(weights)");
+        if (okay) {
+            std::vector<float> wf(wide_w.begin(), wide_w.end());
+            const void *src = storage == STENCIL_F64 ? (const void *)wide_w.data() : (const void *)wf.data();
+            e = cudaMemcpy(p->wdev, src, wide_w.size() * p->esize, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) { cuda_fail(nullptr, e, "cudaMemcpy(weights)"); okay = false; }
+        }
+    }
     if (okay) {
         e = cudaMemset(p->err, 0, sizeof(unsigned));
         if (e != cudaSuccess) { cuda_fail(nullptr, e, "cudaMemset(error word)"); okay = false; }
@@ -455,6 +480,16 @@ static stencil_status run_pass(stencil_t p, void *const *src, void *const *dst, 
                                cudaStream_t s) {
     const bool periodic = p->bc == STENCIL_BC_PERIODIC;
     const Geom &g = p->geom;
+    if (p->kind == STENCIL_MAXFILTER) {
+        CK(p, launch_maxfilter(storage_code(p->storage), p->radius, src[0], dst[0], g, periodic, periodic, s),
+           "maxfilter launch");
+        return STENCIL_OK;
+    }
+    if (p->kind == STENCIL_XCORR && p->radius > 4) {
+        CK(p, launch_xcorr_wide(storage_code(p->storage), p->radius, src[0], dst[0], g, p->wdev, periodic, periodic, s),
+           "xcorr (wide) launch");
+        return STENCIL_OK;
+    }
     if (p->kind == STENCIL_XCORR) {
         const void *cf = p->storage == STENCIL_I32 ? (const void *)p->gi
                          : p->storage == STENCIL_F64 ? (const void *)p->gd : (const void *)p->gf;
@@ -524,9 +559,12 @@ stencil_status stencil_step(stencil_t p, void *const *fin, void *const *fout, in
     // pass list
     std::vector<int> sweeps;  // XCORR (and 1D DIFFUSION): sweeps per launch; others: one entry per pass
     int npass;
-    const bool xcorr_like = p->kind == STENCIL_XCORR || (p->kind == STENCIL_DIFFUSION && p->ndim == 1);
+    const bool xcorr_like = p->kind == STENCIL_XCORR || p->kind == STENCIL_MAXFILTER ||
+                            (p->kind == STENCIL_DIFFUSION && p->ndim == 1);
     if (xcorr_like) {
-        const int maxs = periodic ? xcorr_max_sweeps_per_launch() : 1;
+        // temporal blocking for the radius <= 4 kernel; one sweep per launch otherwise
+        const bool single = !periodic || p->kind == STENCIL_MAXFILTER || p->radius > 4;
+        const int maxs = single ? 1 : xcorr_max_sweeps_per_launch();
         for (int left = nsteps; left > 0;) {
             int k = std::min(left, maxs);
             sweeps.push_back(k);
@@ -636,6 +674,8 @@ static int num_variants(stencil_t p) {
 }
 
 static const char *variant_name(stencil_t p, int v) {
+    if (p->kind == STENCIL_MAXFILTER) return "doubling_chunk4096";
+    if (p->kind == STENCIL_XCORR && p->radius > 4) return "wide_register_blocked";
     if (p->kind == STENCIL_DIFFUSION && p->ndim == 1) return "xcorr_folded_chunk2048_temporal_blocking";
     if (p->kind == STENCIL_DIFFUSION && p->ndim == 2) return "tile2d_32vx_by8_ry4";
     if (p->kind == STENCIL_DIFFUSION) return diffusion_variant_name(storage_code(p->storage), p->radius, v);

@@ -39,6 +39,15 @@ cudaError_t launch_xcorr(int dtype, int r, const void *in, void *out, const Geom
                          const void *coeffs, int sweeps, bool periodic, bool images,
                          cudaStream_t s);
 
+// XCORR of radius 5..1024 (register-blocked, weights in device memory `wdev`, dtype 1 = f64,
+// 2 = f32) and the max filter (radius 0..1024, dtype 0 = int32, 1 = f64, 2 = f32); one sweep
+// per launch (xcorr_wide.cu).
+int xcorr_wide_max_radius();
+cudaError_t launch_xcorr_wide(int dtype, int r, const void *in, void *out, const Geom &g, const void *wdev,
+                              bool periodic, bool images, cudaStream_t s);
+cudaError_t launch_maxfilter(int dtype, int r, const void *in, void *out, const Geom &g, bool periodic, bool images,
+                             cudaStream_t s);
+
 // Grid sizing shared by the z-streaming kernels: number of z-chunks that best fills whole
 // waves of `slots` resident CTAs (see diffusion.cu), and the SM count of the current device.
 int choose_zchunks(int tiles, int nz, int slots, double reread_weight);

@@ -83,6 +83,12 @@ def _create(lib, ndim=3, dims=(16, 16, 16), radius=3, coeffs=None, nfields=1, bc
     (dict(kind=0, ndim=1, dims=(64, 1, 1), radius=3, nfields=1, coeffs=[1] * 6, storage=0, compute=0), _lib.STENCIL_EINVAL),
     (dict(kind=0, ndim=1, dims=(64, 1, 1), radius=5, nfields=1, coeffs=[1] * 11, storage=0, compute=0), _lib.STENCIL_EUNSUPPORTED),
     (dict(kind=0, ndim=3, radius=1, coeffs=[1, 2, 3], storage=0, compute=0), _lib.STENCIL_EUNSUPPORTED),
+    (dict(kind=0, ndim=1, dims=(4096, 1, 1), radius=1025, coeffs=[1.0] * 2051), _lib.STENCIL_EUNSUPPORTED),
+    (dict(kind=3, ndim=1, dims=(4096, 1, 1), radius=1025, params=False), _lib.STENCIL_EUNSUPPORTED),
+    (dict(kind=3, ndim=1, dims=(64, 1, 1), radius=2, coeffs=[1.0] * 5, params=False), _lib.STENCIL_EINVAL),
+    (dict(kind=3, ndim=2, dims=(64, 64, 1), radius=2, params=False), _lib.STENCIL_EUNSUPPORTED),
+    (dict(kind=3, ndim=1, dims=(64, 1, 1), radius=2, storage=3, compute=3, params=False), _lib.STENCIL_EUNSUPPORTED),
+    (dict(kind=3, ndim=1, dims=(8, 1, 1), radius=4, params=False), _lib.STENCIL_EINVAL),  # n < 2r+1
     (dict(kind=0, ndim=1, dims=(64, 1, 1), radius=1, coeffs=[1, 2, 3], storage=1, compute=2), _lib.STENCIL_EUNSUPPORTED),
 ])
 def test_create_rejects_invalid_arguments(lib, kw, expect):
@@ -109,6 +115,18 @@ def test_diffusion_radius_sweep_plans_are_accepted(lib, ndim, dims, radius):
         assert st in (0, _lib.STENCIL_ECUDA), detail
         if st == 0:
             lib.stencil_destroy(plan)
+
+
+@pytest.mark.parametrize("kw", [dict(kind=0, ndim=1, dims=(2049, 1, 1), radius=1024, coeffs=[0.5] * 2049, storage=2,
+                                     compute=2, params=False),
+                                dict(kind=0, ndim=1, dims=(99, 1, 1), radius=17, coeffs=[0.5] * 35, params=False),
+                                dict(kind=3, ndim=1, dims=(2049, 1, 1), radius=1024, storage=0, compute=0, params=False),
+                                dict(kind=3, ndim=1, dims=(5, 1, 1), radius=0, params=False)])
+def test_wide_xcorr_and_maxfilter_plans_are_accepted(lib, kw):
+    st, plan, detail = _create(lib, **kw)
+    assert st in (0, _lib.STENCIL_ECUDA), detail
+    if st == 0:
+        lib.stencil_destroy(plan)
 
 
 def test_create_null_out_and_dims(lib):
