@@ -252,6 +252,7 @@ class MhdParams:
     eta: float = 5e-3
     zeta: float = 0.0
     mu0: float = 1.0
+    K: float = 0.0  # heat conductivity of A3 (0: the benchmark configuration)
 
     @classmethod
     def for_grid(cls, n, **kw):
@@ -261,7 +262,7 @@ class MhdParams:
 
     def array(self) -> np.ndarray:
         return np.array([self.dx, self.dy, self.dz, self.cs0, self.gamma, self.cp, self.lnrho0,
-                         self.nu, self.eta, self.zeta, self.mu0], dtype=np.float64)
+                         self.nu, self.eta, self.zeta, self.mu0, self.K], dtype=np.float64)
 
     def dt_default(self) -> float:
         """dt = 0.1 * min grid spacing (Table B2, PyTorch MHD row)."""

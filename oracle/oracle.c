@@ -27,7 +27,11 @@
  *              [270 D(1) - 27 D(2) + 2 D(3)] / (720 dx dy) with
  *              D(a) = f(a,a) - f(a,-a) + f(-a,-a) - f(-a,a)).
  *   mhd_rhs    the right-hand side of the non-ideal MHD equations A1-A4 (Appendix A,
- *              Table A1), with heating, cooling and conduction switched off (H = C = K = 0).
+ *              Table A1), with heating and cooling switched off (H = C = 0).  The conduction
+ *              term div(K grad T) of A3 takes a constant K and is evaluated through the
+ *              identity T = T0 exp(phi), phi = gamma s/cp + (gamma-1)(lnrho - lnrho0):
+ *              div(K grad T) / (rho T) = (K / rho) (lap phi + |grad phi|^2), with the
+ *              6th-order derivatives of lnrho and s.
  *   rk3        the 3-stage explicit Runge-Kutta step of Sec. 3.3.  The paper does not print
  *              its coefficients; the reading taken is Williamson's 2N-storage 3rd-order
  *              scheme: w <- alpha_s w + dt RHS(f); f <- f + beta_s w, with
@@ -352,8 +356,8 @@ enum { LNRHO = 0, UX, UY, UZ, AX, AY, AZ, SS, NF };
 
 /* Physical parameters, passed as an array so no struct crosses the ABI:
  * par[0..2] = dx, dy, dz; par[3] = cs0; par[4] = gamma; par[5] = cp; par[6] = lnrho0;
- * par[7] = nu; par[8] = eta; par[9] = zeta; par[10] = mu0. */
-enum { P_DX = 0, P_DY, P_DZ, P_CS0, P_GAMMA, P_CP, P_LNRHO0, P_NU, P_ETA, P_ZETA, P_MU0, NPAR };
+ * par[7] = nu; par[8] = eta; par[9] = zeta; par[10] = mu0; par[11] = K (heat conductivity). */
+enum { P_DX = 0, P_DY, P_DZ, P_CS0, P_GAMMA, P_CP, P_LNRHO0, P_NU, P_ETA, P_ZETA, P_MU0, P_K, NPAR };
 
 /* RHS of Eqs. A1-A4 at every interior cell of 8 padded boxes (halo R), written to rhs[f]
  * (dense interiors). fhat[f] and rhs[f] are separate arrays per field. */
@@ -364,6 +368,7 @@ void oracle_mhd_rhs_box(const double *const *fhat, int64_t nx, int64_t ny, int64
     const double h[3] = {par[P_DX], par[P_DY], par[P_DZ]};
     const double cs0 = par[P_CS0], gam = par[P_GAMMA], cp = par[P_CP], lnrho0 = par[P_LNRHO0];
     const double nu = par[P_NU], eta = par[P_ETA], zeta = par[P_ZETA], mu0 = par[P_MU0];
+    const double K = par[P_K];
 #pragma omp parallel for schedule(static)
     for (int64_t k = 0; k < nz; ++k)
         for (int64_t j = 0; j < ny; ++j)
@@ -437,7 +442,8 @@ void oracle_mhd_rhs_box(const double *const *fhat, int64_t nx, int64_t ny, int64
                                      nu * (lapu[c] + graddivu[c] / 3.0 + 2.0 * Sg) +
                                      zeta * graddivu[c];
                 }
-                /* A3: rho T Ds/Dt = eta mu0 j^2 + 2 rho nu S:S + zeta rho (div u)^2 (H=C=K=0) */
+                /* A3: rho T Ds/Dt = div(K grad T) + eta mu0 j^2 + 2 rho nu S:S + zeta rho (div u)^2
+                 * (H = C = 0) */
                 double j2 = jj[0] * jj[0] + jj[1] * jj[1] + jj[2] * jj[2];
                 double SS2 = 0.0;
                 for (int a = 0; a < 3; ++a)
@@ -445,6 +451,17 @@ void oracle_mhd_rhs_box(const double *const *fhat, int64_t nx, int64_t ny, int64
                 double ugrads = u[0] * gss[0] + u[1] * gss[1] + u[2] * gss[2];
                 rhs[SS][o] = -ugrads + (eta * mu0 * j2 + 2.0 * rho * nu * SS2 +
                                         zeta * rho * divu * divu) / (rho * TT);
+                if (K != 0.0) {
+                    /* div(K grad T) / (rho T) with T = T0 exp(phi): (K / rho)(lap phi + |grad phi|^2) */
+                    double lapphi = 0.0, gphi2 = 0.0;
+                    for (int a = 0; a < 3; ++a) {
+                        double gphi = gam / cp * gss[a] + (gam - 1.0) * glnrho[a];
+                        gphi2 += gphi * gphi;
+                        lapphi += gam / cp * der2(fhat[SS], p, st[a], h[a]) +
+                                  (gam - 1.0) * der2(fhat[LNRHO], p, st[a], h[a]);
+                    }
+                    rhs[SS][o] += K / rho * (lapphi + gphi2);
+                }
                 /* A4: dA/dt = u x B + eta lap A */
                 for (int c = 0; c < 3; ++c) rhs[AX + c][o] = uxB[c] + eta * lapA[c];
             }

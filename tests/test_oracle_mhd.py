@@ -202,3 +202,40 @@ def test_box_step_matches_periodic_step():
     out = oracle.mhd_rk3_box(box, p, dt, 3)
     np.testing.assert_allclose(out[:, 9, 9, 9], ref[:, c[0], c[1], c[2]], rtol=1e-13, atol=1e-16)
     assert out.shape[1] == m
+
+
+def test_heat_conduction_from_an_entropy_mode():
+    # u = A = 0, lnrho uniform, s = eps sin(k y): only A3 changes; with phi = gamma s/cp,
+    # div(K grad T)/(rho T) = (K/rho)(lap phi + |grad phi|^2) and every derivative is a symbol.
+    p = _par(K=0.7)
+    (Z, Y, X), h = grid(N)
+    k, eps, lr = 3, 2e-2, 0.4
+    f = np.zeros((8, N, N, N))
+    f[LNRHO] = lr
+    f[SS] = eps * np.sin(k * Y)
+    g = p.gamma / p.cp
+    rho = np.exp(lr)
+    cs2, _ = _temp(p, lr, f[SS])
+    exp = np.zeros_like(f)
+    exp[UY] = -cs2 * (lam1(k, h) * eps * np.cos(k * Y)) / p.cp   # the pressure term (already pinned)
+    lap_phi = g * lam2(k, h) * eps * np.sin(k * Y)
+    grad_phi2 = (g * lam1(k, h) * eps * np.cos(k * Y)) ** 2
+    exp[SS] = p.K / rho * (lap_phi + grad_phi2)
+    _check(oracle.mhd_rhs(f, p), exp)
+    # K = 0 leaves A3 without the term
+    assert np.abs(oracle.mhd_rhs(f, _par(K=0.0))[SS]).max() < 1e-15
+
+
+def test_heat_conduction_from_a_density_mode():
+    # lnrho = lr + eps sin(k z): phi = (gamma-1)(lnrho - lnrho0), rho varies cell by cell
+    p = _par(K=0.25)
+    (Z, Y, X), h = grid(N)
+    k, eps, lr = 2, 3e-2, -0.2
+    f = np.zeros((8, N, N, N))
+    f[LNRHO] = lr + eps * np.sin(k * Z)
+    gm1 = p.gamma - 1.0
+    rho = np.exp(f[LNRHO])
+    lap_phi = gm1 * lam2(k, h) * eps * np.sin(k * Z)
+    grad_phi2 = (gm1 * lam1(k, h) * eps * np.cos(k * Z)) ** 2
+    got = oracle.mhd_rhs(f, p)
+    np.testing.assert_allclose(got[SS], p.K / rho * (lap_phi + grad_phi2), rtol=0, atol=1e-12)
