@@ -89,6 +89,8 @@ typedef struct stencil_params {
     double eta;    /* MHD8: magnetic diffusivity */
     double zeta;   /* MHD8: bulk viscosity */
     double mu0;    /* MHD8: vacuum permeability */
+    double K;      /* MHD8: radiative heat conductivity of Eq. A3 (constant; 0 switches the
+                      conduction term off) */
 } stencil_params;
 
 /* Field order of STENCIL_MHD8 (Table A1 symbols). */

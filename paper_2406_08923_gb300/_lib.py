@@ -40,7 +40,7 @@ class stencil_params(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("alpha", ctypes.c_double), ("dx", ctypes.c_double * 3),
                 ("cs0", ctypes.c_double), ("gamma", ctypes.c_double), ("cp", ctypes.c_double),
                 ("lnrho0", ctypes.c_double), ("nu", ctypes.c_double), ("eta", ctypes.c_double),
-                ("zeta", ctypes.c_double), ("mu0", ctypes.c_double)]
+                ("zeta", ctypes.c_double), ("mu0", ctypes.c_double), ("K", ctypes.c_double)]
 
 
 class stencil_request(ctypes.Structure):
@@ -379,7 +379,7 @@ def mhd_params(n, dt=None, **kw) -> stencil_params:
     p = stencil_params()
     tau = 2.0 * np.pi
     p.dx[0], p.dx[1], p.dx[2] = tau / nx, tau / ny, tau / nz
-    vals = dict(cs0=1.0, gamma=5.0 / 3.0, cp=1.0, lnrho0=0.0, nu=5e-3, eta=5e-3, zeta=0.0, mu0=1.0)
+    vals = dict(cs0=1.0, gamma=5.0 / 3.0, cp=1.0, lnrho0=0.0, nu=5e-3, eta=5e-3, zeta=0.0, mu0=1.0, K=0.0)
     vals.update(kw)
     for k, v in vals.items():
         setattr(p, k, v)

@@ -290,6 +290,8 @@ stencil_status stencil_create(int ndim, const int64_t dims[3], int radius, const
                 return fail(nullptr, STENCIL_EUNSUPPORTED, "MHD8 supports F64/F64, F32/F32, BF16/F32");
             if (!(params->cp > 0.0) || !(params->gamma > 1.0) || !(params->mu0 > 0.0))
                 return fail(nullptr, STENCIL_EINVAL, "MHD8 needs cp > 0, gamma > 1, mu0 > 0");
+            if (!(params->K >= 0.0) || !std::isfinite(params->K))
+                return fail(nullptr, STENCIL_EINVAL, "MHD8 needs a finite heat conductivity K >= 0");
         }
     }
     if (bc == STENCIL_BC_PERIODIC)
@@ -385,6 +387,7 @@ stencil_status stencil_create(int ndim, const int64_t dims[3], int radius, const
             c.mu0 = params->mu0;
             c.inv_mu0 = 1.0 / params->mu0;
             c.cp_gm1 = params->cp * (params->gamma - 1.0);
+            c.K = params->K;
             c.dt = params->dt;
         }
     }

@@ -445,7 +445,7 @@ stencil_status stencil_server_submit(stencil_server_t s, const stencil_request *
             }
             c.cs0sq = p.cs0 * p.cs0; c.gamma = p.gamma; c.inv_cp = 1.0 / p.cp; c.lnrho0 = p.lnrho0;
             c.nu = p.nu; c.eta = p.eta; c.zeta = p.zeta; c.mu0 = p.mu0; c.inv_mu0 = 1.0 / p.mu0;
-            c.cp_gm1 = p.cp * (p.gamma - 1.0); c.dt = p.dt;
+            c.cp_gm1 = p.cp * (p.gamma - 1.0); c.K = p.K; c.dt = p.dt;
             mhd_scaled_constants(c, &r->k);
             mhd_batch_tile(&tx, &ty, box);
         }

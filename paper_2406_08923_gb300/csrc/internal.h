@@ -83,6 +83,7 @@ void diffusion2d_box(int dtype, int r, int box[3]);
 struct MhdConst {
     double d1[3][3], d2c[3], d2[3][3], dm[3][3];  // scaled stencil weights
     double cs0sq, gamma, inv_cp, lnrho0, nu, eta, zeta, mu0, inv_mu0, cp_gm1;
+    double K;  // heat conductivity of Eq. A3 (0: no conduction term)
     double dt;
 };
 struct MhdMaps {
@@ -118,6 +119,7 @@ cudaError_t launch_norms_noalloc(int storage, const Ptrs8 &f, int nfields, const
 template <typename C> struct MK {
     C d1[3][3], d2c[3], d2[3][3], dm[3][3];
     C cs0sq, gamma, inv_cp, lnrho0, nu, eta, zeta, mu0, inv_mu0, cp_gm1;
+    C K;
     C dt, alpha, beta;
 };
 

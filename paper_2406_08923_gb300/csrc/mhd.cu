@@ -91,7 +91,10 @@ template <typename C> __device__ __forceinline__ C exp_c(C v);
 template <> __device__ __forceinline__ double exp_c<double>(double v) { return exp(v); }
 template <> __device__ __forceinline__ float exp_c<float>(float v) { return expf(v); }
 
-// The right-hand side of Eqs. A1-A4 at one cell (H = C = K = 0); val[q] = f_q at the cell.
+// The right-hand side of Eqs. A1-A4 at one cell (H = C = 0); val[q] = f_q at the cell.  The
+// conduction term of A3 with constant K uses T = T0 exp(phi), phi = gamma s/cp +
+// (gamma-1)(lnrho - lnrho0): div(K grad T)/(rho T) = (K/rho)(lap phi + |grad phi|^2); its two
+// extra Laplacians are evaluated only when K != 0.
 template <typename C, typename W>
 __device__ __forceinline__ void mhd_rhs_cell(const W &w, const MK<C> &k, C *rhs, C *val) {
 #pragma unroll
@@ -188,6 +191,17 @@ __device__ __forceinline__ void mhd_rhs_cell(const W &w, const MK<C> &k, C *rhs,
     const C j2 = jx * jx + jy * jy + jz * jz;
     rhs[F_SS] = -(ux * gs[0] + uy * gs[1] + uz * gs[2]) +
                 (k.eta * k.mu0 * j2 + C(2) * rho * k.nu * s2 + k.zeta * rho * divu * divu) * inv_rhoT;
+    if (k.K != C(0)) {
+        const C gp = k.gamma * k.inv_cp, gm1 = k.gamma - C(1);
+        C lapphi = C(0), gphi2 = C(0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const C gphi = gp * gs[a] + gm1 * glr[a];
+            gphi2 = fma(gphi, gphi, gphi2);
+            lapphi += gp * d2(w, F_SS, a, k.d2c[a], k.d2[a]) + gm1 * d2(w, F_LNRHO, a, k.d2c[a], k.d2[a]);
+        }
+        rhs[F_SS] += k.K * inv_rho * (lapphi + gphi2);
+    }
     // A4
     rhs[F_AX] = (uy * bz - uz * by) + k.eta * lapa[0];
     rhs[F_AY] = (uz * bx - ux * bz) + k.eta * lapa[1];
@@ -340,7 +354,7 @@ static MK<C> make_k(const MhdConst &c, double alpha, double beta) {
     }
     k.cs0sq = (C)c.cs0sq; k.gamma = (C)c.gamma; k.inv_cp = (C)c.inv_cp; k.lnrho0 = (C)c.lnrho0;
     k.nu = (C)c.nu; k.eta = (C)c.eta; k.zeta = (C)c.zeta; k.mu0 = (C)c.mu0; k.inv_mu0 = (C)c.inv_mu0;
-    k.cp_gm1 = (C)c.cp_gm1; k.dt = (C)c.dt; k.alpha = (C)alpha; k.beta = (C)beta;
+    k.cp_gm1 = (C)c.cp_gm1; k.K = (C)c.K; k.dt = (C)c.dt; k.alpha = (C)alpha; k.beta = (C)beta;
     return k;
 }
 

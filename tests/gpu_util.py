@@ -59,4 +59,4 @@ def oracle_mhd_params(par):
     import oracle
     return oracle.MhdParams(dx=par.dx[0], dy=par.dx[1], dz=par.dx[2], cs0=par.cs0, gamma=par.gamma,
                             cp=par.cp, lnrho0=par.lnrho0, nu=par.nu, eta=par.eta, zeta=par.zeta,
-                            mu0=par.mu0)
+                            mu0=par.mu0, K=par.K)

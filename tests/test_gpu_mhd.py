@@ -9,6 +9,7 @@
 * Full benchmark sizes (256^3 FP64, 384^3 FP32/BF16): one step on sampled cells against the
   oracle's neighbourhood-box evaluation.
 * Closed form: a uniform state stays uniform (all derivatives vanish).
+* The heat-conduction term of A3 (K != 0): RHS and RK3 steps against the oracle.
 """
 import numpy as np
 import pytest
@@ -129,3 +130,39 @@ def test_full_size_step_sampled(cuda_lib, storage, n):
         scale = np.abs(fin).reshape(8, -1).max(axis=1)
         tol = TOL[storage]
         assert np.all(np.abs(g - ref) <= tol * scale + 1e-300), (cell, g, ref)
+
+
+@pytest.mark.parametrize("storage", STORAGE)
+def test_heat_conduction_rhs_against_oracle(cuda_lib, storage):
+    shape = (20, 17, 35)
+    f8 = synth.mhd_fields(shape, seed=31) * 20.0
+    p, par = mhd_plan(shape, storage, K=0.05)
+    a = p.alloc()
+    p.upload(a, f8)
+    ref = oracle.mhd_rhs(_rounded(f8, storage), oracle_mhd_params(par))
+    ref0 = oracle.mhd_rhs(_rounded(f8, storage), oracle_mhd_params(L.mhd_params(shape)))
+    assert rel_l2(ref[7] - ref0[7], ref0[7]) > 1e-3  # the term is not negligible in this case
+    ctype = torch.float64 if storage == L.STENCIL_F64 else torch.float32
+    tol = 1e-12 if storage == L.STENCIL_F64 else 2e-5
+    for v in range(p.variant()[1]):
+        p.set_variant(v)
+        rhs = [torch.zeros(shape, dtype=ctype, device="cuda") for _ in range(8)]
+        p.mhd_rhs(a, rhs)
+        p.sync()
+        for q in range(8):
+            assert_close(rhs[q].double().cpu().numpy(), ref[q], tol, f"K, variant {v} field {q}")
+
+
+def test_heat_conduction_steps_against_oracle(cuda_lib):
+    shape = (24, 24, 24)
+    f8 = synth.mhd_fields(shape, seed=32) * 20.0
+    for storage in (L.STENCIL_F64, L.STENCIL_F32):
+        p, par = mhd_plan(shape, storage, K=0.05)
+        ref = oracle.mhd_rk3(_rounded(f8, storage), oracle_mhd_params(par), par.dt, 3)
+        a, b = p.alloc(), p.alloc()
+        p.upload(a, f8)
+        p.step(a, b, 3)
+        p.sync()
+        got = p.download(b)
+        for q in range(8):
+            assert_close(got[q], ref[q], TOL[storage], f"K, storage {storage} field {q}")
