@@ -123,6 +123,15 @@ template <typename C> struct MK {
     C dt, alpha, beta;
 };
 
+// The field-pair MHD kernel family for FP32/BF16 storage (mhd_pairs.cu), reached through
+// launch_mhd's variants 3.. for those storage types.
+int mhd_pairs_num_variants();
+const char *mhd_pairs_variant_name(int variant);
+void mhd_pairs_box(int storage, int variant, int box[3]);
+cudaError_t launch_mhd_pairs(int storage, int mode, int sub, const MhdMaps &maps, const Ptrs8 &fo, const Ptrs8 &w,
+                             const Ptrs8 &kc, const Ptrs8 &rhs, const Geom &g, const MK<float> &k, bool images,
+                             unsigned *err, cudaStream_t s, int variant);
+
 // Work items of one batched launch.  Every item owns a contiguous range of virtual CTAs
 // [cta_begin, cta_begin + tiles); a persistent grid strides over the virtual CTAs and finds
 // the item by binary search on cta_begin.  All pointers are device pointers; descriptors are

@@ -25,11 +25,9 @@
 //     in-flight loads before returning.
 #include <algorithm>
 
-#include "internal.h"
+#include "mhd_rhs.cuh"
 
 namespace stn {
-
-enum { F_LNRHO = 0, F_UX, F_UY, F_UZ, F_AX, F_AY, F_AZ, F_SS };
 
 template <typename S, int TX, int TY, int NSLOT>
 struct MhdCfg {
@@ -87,55 +85,58 @@ __device__ __forceinline__ C dmix(const W &w, int q, int pair, const C *m) {
     return fma(m[2], (f(3, 3) + f(-3, -3)) - (f(3, -3) + f(-3, 3)), acc);
 }
 
-template <typename C> __device__ __forceinline__ C exp_c(C v);
-template <> __device__ __forceinline__ double exp_c<double>(double v) { return exp(v); }
-template <> __device__ __forceinline__ float exp_c<float>(float v) { return expf(v); }
-
 // The right-hand side of Eqs. A1-A4 at one cell (H = C = 0); val[q] = f_q at the cell.  The
-// conduction term of A3 with constant K uses T = T0 exp(phi), phi = gamma s/cp +
-// (gamma-1)(lnrho - lnrho0): div(K grad T)/(rho T) = (K/rho)(lap phi + |grad phi|^2); its two
-// extra Laplacians are evaluated only when K != 0.
+// derivatives are evaluated field by field, only those some term uses (lnrho and s: gradients,
+// plus Laplacians when K != 0; A: the off-diagonal first derivatives and the Hessian), then
+// assembled by mhd_rhs_assemble.
 template <typename C, typename W>
 __device__ __forceinline__ void mhd_rhs_cell(const W &w, const MK<C> &k, C *rhs, C *val) {
+    MhdDerivs<C> d;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) val[q] = w.at(q, 3, 0, 0);
-    // gradients of lnrho and s
-    C glr[3], gs[3];
+    for (int q = 0; q < 8; ++q) d.val[q] = w.at(q, 3, 0, 0);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        glr[a] = d1(w, F_LNRHO, a, k.d1[a]);
-        gs[a] = d1(w, F_SS, a, k.d1[a]);
+        d.glr[a] = d1(w, F_LNRHO, a, k.d1[a]);
+        d.gs[a] = d1(w, F_SS, a, k.d1[a]);
     }
+    d.laplr = d.laps = C(0);
+    if (k.K != C(0)) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            d.laplr += d2(w, F_LNRHO, a, k.d2c[a], k.d2[a]);
+            d.laps += d2(w, F_SS, a, k.d2c[a], k.d2[a]);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) d.gdivu[c] = d.gdiva[c] = C(0);
     // velocity: gu[i][a] = d u_i / d x_a; lap u; grad div u accumulated per component
-    C gu[3][3], lapu[3], gdivu[3] = {C(0), C(0), C(0)};
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const int q = F_UX + c;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) gu[c][a] = d1(w, q, a, k.d1[a]);
+        for (int a = 0; a < 3; ++a) d.gu[c][a] = d1(w, q, a, k.d1[a]);
         C hxx = d2(w, q, 0, k.d2c[0], k.d2[0]);
         C hyy = d2(w, q, 1, k.d2c[1], k.d2[1]);
         C hzz = d2(w, q, 2, k.d2c[2], k.d2[2]);
         C hxy = dmix(w, q, 0, k.dm[0]);
         C hxz = dmix(w, q, 1, k.dm[1]);
         C hyz = dmix(w, q, 2, k.dm[2]);
-        lapu[c] = hxx + hyy + hzz;
+        d.lapu[c] = hxx + hyy + hzz;
         // grad(div u)_x += d_x d_c u_c, etc.
         const C hc[3] = {c == 0 ? hxx : c == 1 ? hxy : hxz, c == 0 ? hxy : c == 1 ? hyy : hyz,
                          c == 0 ? hxz : c == 1 ? hyz : hzz};
-        gdivu[0] += hc[0];
-        gdivu[1] += hc[1];
-        gdivu[2] += hc[2];
+        d.gdivu[0] += hc[0];
+        d.gdivu[1] += hc[1];
+        d.gdivu[2] += hc[2];
     }
     // vector potential: B = curl A (off-diagonal first derivatives only), j = (grad div A - lap A)/mu0
-    C bx, by, bz, lapa[3], gdiva[3] = {C(0), C(0), C(0)};
     {
         const C ax_y = d1(w, F_AX, 1, k.d1[1]), ax_z = d1(w, F_AX, 2, k.d1[2]);
         const C ay_x = d1(w, F_AY, 0, k.d1[0]), ay_z = d1(w, F_AY, 2, k.d1[2]);
         const C az_x = d1(w, F_AZ, 0, k.d1[0]), az_y = d1(w, F_AZ, 1, k.d1[1]);
-        bx = az_y - ay_z;
-        by = ax_z - az_x;
-        bz = ay_x - ax_y;
+        d.bx = az_y - ay_z;
+        d.by = ax_z - az_x;
+        d.bz = ay_x - ax_y;
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -146,66 +147,16 @@ __device__ __forceinline__ void mhd_rhs_cell(const W &w, const MK<C> &k, C *rhs,
         C hxy = dmix(w, q, 0, k.dm[0]);
         C hxz = dmix(w, q, 1, k.dm[1]);
         C hyz = dmix(w, q, 2, k.dm[2]);
-        lapa[c] = hxx + hyy + hzz;
+        d.lapa[c] = hxx + hyy + hzz;
         const C hc[3] = {c == 0 ? hxx : c == 1 ? hxy : hxz, c == 0 ? hxy : c == 1 ? hyy : hyz,
                          c == 0 ? hxz : c == 1 ? hyz : hzz};
-        gdiva[0] += hc[0];
-        gdiva[1] += hc[1];
-        gdiva[2] += hc[2];
+        d.gdiva[0] += hc[0];
+        d.gdiva[1] += hc[1];
+        d.gdiva[2] += hc[2];
     }
-    const C jx = (gdiva[0] - lapa[0]) * k.inv_mu0;
-    const C jy = (gdiva[1] - lapa[1]) * k.inv_mu0;
-    const C jz = (gdiva[2] - lapa[2]) * k.inv_mu0;
-
-    const C lnrho = val[F_LNRHO], ss = val[F_SS];
-    const C ux = val[F_UX], uy = val[F_UY], uz = val[F_UZ];
-    const C divu = gu[0][0] + gu[1][1] + gu[2][2];
-    // traceless rate of shear
-    const C third = C(1) / C(3);
-    const C sxx = gu[0][0] - third * divu, syy = gu[1][1] - third * divu, szz = gu[2][2] - third * divu;
-    const C sxy = C(0.5) * (gu[0][1] + gu[1][0]);
-    const C sxz = C(0.5) * (gu[0][2] + gu[2][0]);
-    const C syz = C(0.5) * (gu[1][2] + gu[2][1]);
-    const C s2 = sxx * sxx + syy * syy + szz * szz + C(2) * (sxy * sxy + sxz * sxz + syz * syz);
-
-    // closure: rho = exp(lnrho), cs^2 = cs0^2 exp(gamma s/cp + (gamma-1)(lnrho - lnrho0)),
-    // T = cs^2 / (cp (gamma - 1))
-    const C rho = exp_c<C>(lnrho);
-    const C inv_rho = C(1) / rho;
-    const C cs2 = k.cs0sq * exp_c<C>(k.gamma * ss * k.inv_cp + (k.gamma - C(1)) * (lnrho - k.lnrho0));
-    const C inv_rhoT = k.cp_gm1 * inv_rho / cs2;
-
-    // A1
-    rhs[F_LNRHO] = -(ux * glr[0] + uy * glr[1] + uz * glr[2]) - divu;
-    // A2
-    const C jxb[3] = {jy * bz - jz * by, jz * bx - jx * bz, jx * by - jy * bx};
-    const C sg[3] = {sxx * glr[0] + sxy * glr[1] + sxz * glr[2], sxy * glr[0] + syy * glr[1] + syz * glr[2],
-                     sxz * glr[0] + syz * glr[1] + szz * glr[2]};
+    mhd_rhs_assemble(d, k, rhs);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const C adv = ux * gu[c][0] + uy * gu[c][1] + uz * gu[c][2];
-        rhs[F_UX + c] = -adv - cs2 * (gs[c] * k.inv_cp + glr[c]) + jxb[c] * inv_rho +
-                        k.nu * (lapu[c] + third * gdivu[c] + C(2) * sg[c]) + k.zeta * gdivu[c];
-    }
-    // A3
-    const C j2 = jx * jx + jy * jy + jz * jz;
-    rhs[F_SS] = -(ux * gs[0] + uy * gs[1] + uz * gs[2]) +
-                (k.eta * k.mu0 * j2 + C(2) * rho * k.nu * s2 + k.zeta * rho * divu * divu) * inv_rhoT;
-    if (k.K != C(0)) {
-        const C gp = k.gamma * k.inv_cp, gm1 = k.gamma - C(1);
-        C lapphi = C(0), gphi2 = C(0);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const C gphi = gp * gs[a] + gm1 * glr[a];
-            gphi2 = fma(gphi, gphi, gphi2);
-            lapphi += gp * d2(w, F_SS, a, k.d2c[a], k.d2[a]) + gm1 * d2(w, F_LNRHO, a, k.d2c[a], k.d2[a]);
-        }
-        rhs[F_SS] += k.K * inv_rho * (lapphi + gphi2);
-    }
-    // A4
-    rhs[F_AX] = (uy * bz - uz * by) + k.eta * lapa[0];
-    rhs[F_AY] = (uz * bx - ux * bz) + k.eta * lapa[1];
-    rhs[F_AZ] = (ux * by - uy * bx) + k.eta * lapa[2];
+    for (int q = 0; q < 8; ++q) val[q] = d.val[q];
 }
 
 // One xy-tile of one z-chunk of one RK substep (or RHS evaluation): the whole pipeline of a
@@ -401,14 +352,17 @@ static const char *MHD_F64_NAMES[] = {"tx32_ty4_s8_b1", "tx16_ty8_s8_b1"};
 static const char *MHD_F32_NAMES[] = {"tx32_ty8_s8_b1", "tx32_ty4_s8_b2", "tx16_ty8_s8_b2"};
 static const char *MHD_BF16_NAMES[] = {"tx32_ty8_s8_b1", "tx32_ty8_s8_b2", "tx32_ty4_s8_b3"};
 
-int mhd_num_variants(int storage) { return storage == 1 ? 2 : 3; }
+// FP32 and BF16 storage: the scalar variants, then the field-pair kernel's (mhd_pairs.cu).
+int mhd_num_variants(int storage) { return storage == 1 ? 2 : 3 + mhd_pairs_num_variants(); }
 
 const char *mhd_variant_name(int storage, int v) {
     if (v < 0 || v >= mhd_num_variants(storage)) return "?";
+    if (storage != 1 && v >= 3) return mhd_pairs_variant_name(v - 3);
     return storage == 1 ? MHD_F64_NAMES[v] : storage == 2 ? MHD_F32_NAMES[v] : MHD_BF16_NAMES[v];
 }
 
 void mhd_box(int storage, int v, int box[3]) {
+    if (storage != 1 && v >= 3) return mhd_pairs_box(storage, v - 3, box);
     int i = 0;
     auto put = [&](int tx, int ty, int hx) {
         if (i++ == v) { box[0] = tx + 2 * hx; box[1] = ty + 2 * R6; box[2] = 1; }
@@ -423,6 +377,9 @@ void mhd_box(int storage, int v, int box[3]) {
 cudaError_t launch_mhd(int storage, int mode, int sub, const MhdMaps &maps, const Ptrs8 &fo, const Ptrs8 &w,
                        const Ptrs8 &kc, const Ptrs8 &rhs, const Geom &g, const MhdConst &c, bool images,
                        unsigned *err, cudaStream_t s, int variant) {
+    if (storage != 1 && variant >= 3)
+        return launch_mhd_pairs(storage, mode, sub, maps, fo, w, kc, rhs, g, make_k<float>(c, RK_A[sub], RK_B[sub]),
+                                images, err, s, variant - 3);
     int i = 0;
     cudaError_t res = cudaErrorInvalidValue;
 #define X(TX, TY, NS, MB)                                                                             \
