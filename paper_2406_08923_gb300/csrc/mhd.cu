@@ -361,6 +361,12 @@ const char *mhd_variant_name(int storage, int v) {
     return storage == 1 ? MHD_F64_NAMES[v] : storage == 2 ? MHD_F32_NAMES[v] : MHD_BF16_NAMES[v];
 }
 
+bool mhd_variant_uses_io(int storage, int v, int *rows) {
+    if (storage == 1 || v < 3 || !mhd_pairs_variant_uses_io(v - 3)) return false;
+    if (rows) *rows = mhd_pairs_io_box_rows(v - 3);
+    return true;
+}
+
 void mhd_box(int storage, int v, int box[3]) {
     if (storage != 1 && v >= 3) return mhd_pairs_box(storage, v - 3, box);
     int i = 0;
@@ -376,10 +382,10 @@ void mhd_box(int storage, int v, int box[3]) {
 
 cudaError_t launch_mhd(int storage, int mode, int sub, const MhdMaps &maps, const Ptrs8 &fo, const Ptrs8 &w,
                        const Ptrs8 &kc, const Ptrs8 &rhs, const Geom &g, const MhdConst &c, bool images,
-                       unsigned *err, cudaStream_t s, int variant) {
+                       unsigned *err, cudaStream_t s, int variant, const MhdIoMaps *io) {
     if (storage != 1 && variant >= 3)
-        return launch_mhd_pairs(storage, mode, sub, maps, fo, w, kc, rhs, g, make_k<float>(c, RK_A[sub], RK_B[sub]),
-                                images, err, s, variant - 3);
+        return launch_mhd_pairs(storage, mode, sub, maps, io, fo, w, kc, rhs, g,
+                                make_k<float>(c, RK_A[sub], RK_B[sub]), images, err, s, variant - 3);
     int i = 0;
     cudaError_t res = cudaErrorInvalidValue;
 #define X(TX, TY, NS, MB)                                                                             \

@@ -18,6 +18,14 @@
 // converted is never in the current 7-plane window), one barrier, refill the raw slot, compute
 // one cell per thread.  Waits are bounded; on expiry ERR_TIMEOUT is recorded and in-flight
 // loads are drained before the CTA returns.
+//
+// TMA-I/O variant: the RK register w and the Kahan term c of the next plane arrive by 16 TMA
+// box loads into double-buffered shared staging; each thread updates its w and c in place and
+// writes its new field values to a staging tile; after a proxy fence and a barrier one thread
+// stores the plane's 24 boxes (fields through an interior view of each output array, so tiles
+// that overhang the interior are clipped) with TMA.  This replaces 40 scalar global accesses per
+// cell, whose issue queue and latency bound the plain variants at 8 warps per SM.  Periodic
+// images of edge cells are still written by scalar stores.
 #include <algorithm>
 
 #include "mhd_rhs.cuh"
@@ -25,7 +33,7 @@
 namespace stn {
 namespace {
 
-template <typename S, int TY, int NR>
+template <typename S, int TY, int NR, bool TMAIO = false>
 struct MpCfg {
     static constexpr int TX = 32;
     static constexpr int HX = 16 / (int)sizeof(S) >= 4 ? 16 / (int)sizeof(S) : 4;  // raw tile x halo (TMA)
@@ -38,7 +46,12 @@ struct MpCfg {
     static constexpr int PAIR_SLOT = 4 * PAIR_FIELD;
     static constexpr uint32_t BOX_BYTES = TXP * ROWS * sizeof(S);
     static constexpr size_t RAW_BYTES = (size_t)NR * RAW_SLOT * sizeof(S);
-    static constexpr size_t SMEM = RAW_BYTES + (size_t)8 * PAIR_SLOT * 8 + 128;
+    static constexpr size_t PAIR_BYTES = (size_t)8 * PAIR_SLOT * 8;
+    // TMA-I/O staging per buffer: 16 boxes of w and c, then 8 boxes of new field values
+    static constexpr int CELLS = TX * TY;
+    static constexpr size_t STAGE_BYTES = TMAIO ? (size_t)24 * CELLS * sizeof(S) : 0;
+    static constexpr size_t SMEM = RAW_BYTES + PAIR_BYTES + 2 * STAGE_BYTES + 128;
+    static_assert((CELLS * sizeof(S)) % 128 == 0, "staging boxes stay 128-byte aligned");
     static_assert((TXP * sizeof(S)) % 16 == 0, "TMA box inner extent must be a multiple of 16 B");
     static_assert((NR & (NR - 1)) == 0 && NR >= 2, "raw ring depth is a power of two >= 2");
     static_assert(RAW_BYTES % 128 == 0, "pair ring stays 128-byte aligned");
@@ -161,12 +174,15 @@ __device__ __forceinline__ void mhdp_rhs_cell(const W &w, const MK<float> &k, fl
 }
 
 // One xy-tile of one z-chunk of one RK substep (MODE 0) or RHS evaluation (MODE 1).
-template <typename S, int TY, int NR, int MODE>
-__device__ __forceinline__ bool mhdp_tile(const CUtensorMap *maps, const Ptrs8 &fout, const Ptrs8 &wbuf,
-                                          const Ptrs8 &kbuf, const Ptrs8 &rbuf, const Geom &g, const MK<float> &k,
-                                          int tile_x, int tile_y, int tile_z, int zc, int first, int last, int images,
-                                          unsigned *err, S *raw, float2 *pairs, uint64_t *full) {
-    using Cfg = MpCfg<S, TY, NR>;
+template <typename S, int TY, int NR, int MODE, bool TMAIO>
+__device__ __forceinline__ bool mhdp_tile(const CUtensorMap *maps, const MhdIoMaps *io, const Ptrs8 &fout,
+                                          const Ptrs8 &wbuf, const Ptrs8 &kbuf, const Ptrs8 &rbuf, const Geom &g,
+                                          const MK<float> &k, int tile_x, int tile_y, int tile_z, int zc, int first,
+                                          int last, int images, unsigned *err, S *raw, float2 *pairs, S *stage,
+                                          uint64_t *full, uint64_t *wcbar) {
+    static_assert(!TMAIO || MODE == 0, "TMA I/O serves the RK substep");
+    using Cfg = MpCfg<S, TY, NR, TMAIO>;
+    constexpr int CELLS = Cfg::CELLS;
     using W = PWin<Cfg::PAIR_FIELD, Cfg::PX>;
     constexpr int TX = Cfg::TX;
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
@@ -181,9 +197,28 @@ __device__ __forceinline__ bool mhdp_tile(const CUtensorMap *maps, const Ptrs8 &
     if (threadIdx.x == 0) {
         for (int q = 0; q < 8; ++q) tma_prefetch_desc(&maps[q]);
         for (int s = 0; s < NR; ++s) mbar_init(&full[s], 1);
+        if (TMAIO) {
+            mbar_init(&wcbar[0], 1);
+            mbar_init(&wcbar[1], 1);
+        }
         mbar_fence_init();
     }
     __syncthreads();
+    // TMA I/O: staging buffer b holds w_0..w_7, c_0..c_7, f'_0..f'_7 boxes of CELLS elements
+    auto stg = [&](int b, int q) { return stage + (size_t)(b * 24 + q) * CELLS; };
+    int wc_issued = 0;              // planes whose w/c loads thread 0 has issued
+    auto load_wc = [&](int m) {  // w (unless first) and c of plane zc0 + m into buffer m & 1
+        const int b = m & 1, z = zc0 + m;
+        wc_issued = m + 1;
+        const uint32_t boxb = (uint32_t)(CELLS * sizeof(S));
+        mbar_arrive_expect_tx(&wcbar[b], (first ? 8u : 16u) * boxb);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (!first) tma_load_3d(stg(b, q), &io->w[q], &wcbar[b], x0, y0, z);
+            tma_load_3d(stg(b, 8 + q), &io->c[q], &wcbar[b], x0, y0, z);
+        }
+    };
+    if (TMAIO && threadIdx.x == 0 && zc0 < zend) load_wc(0);
     const int bx = (int)g.off[0] + x0 - Cfg::HX;
     const int by0 = (int)g.off[1] + y0 - R6;
     const int bz0 = (int)g.off[2] + zc0 - R6;
@@ -230,7 +265,7 @@ __device__ __forceinline__ bool mhdp_tile(const CUtensorMap *maps, const Ptrs8 &
             kpre[q] = (MODE == 0) ? to_c<float>(static_cast<const S *>(kbuf.p[q])[c]) : 0.f;
         }
     };
-    if (active && zc0 < zend) prefetch(cell);
+    if (!TMAIO && active && zc0 < zend) prefetch(cell);
 
     // prologue: planes 0 .. 5 into the pair ring
     bool ok = true, bad = false;
@@ -246,16 +281,32 @@ __device__ __forceinline__ bool mhdp_tile(const CUtensorMap *maps, const Ptrs8 &
         ok = convert(jl);
         bad = __syncthreads_or(!ok);
         if (bad) break;
-        if (threadIdx.x == 0 && issued < nplanes && issued == jl + NR) issue(issued++);
-        if (active) {
+        if (threadIdx.x == 0) {
+            if (issued < nplanes && issued == jl + NR) issue(issued++);
+            if (TMAIO && m + 1 < zend - zc0) {
+                bulk_wait_read<0>();  // plane m-1's stores have read buffer (m+1) & 1
+                load_wc(m + 1);
+            }
+        }
+        const int b = m & 1;
+        if (TMAIO && active) ok = mbar_wait_bounded(&wcbar[b], ((unsigned)m >> 1) & 1u);
+        if (active && ok) {
             const int z = zc0 + m;
             W w;
 #pragma unroll
             for (int kk = 0; kk < 7; ++kk) w.p[kk] = pairs + ((m + kk) & 7) * Cfg::PAIR_SLOT + own;
             float wcur[8], kcur[8];
+            if (TMAIO) {
 #pragma unroll
-            for (int q = 0; q < 8; ++q) { wcur[q] = wpre[q]; kcur[q] = kpre[q]; }
-            if (m + 1 < zend - zc0) prefetch(cell + nxy);  // next plane, overlapped with compute
+                for (int q = 0; q < 8; ++q) {
+                    wcur[q] = first ? 0.f : to_c<float>(stg(b, q)[threadIdx.x]);
+                    kcur[q] = to_c<float>(stg(b, 8 + q)[threadIdx.x]);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) { wcur[q] = wpre[q]; kcur[q] = kpre[q]; }
+                if (m + 1 < zend - zc0) prefetch(cell + nxy);  // next plane, overlapped with compute
+            }
             float rhs[8], val[8];
             mhdp_rhs_cell(w, k, rhs, val);
             if (MODE == 1) {
@@ -266,12 +317,26 @@ __device__ __forceinline__ bool mhdp_tile(const CUtensorMap *maps, const Ptrs8 &
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     const float wv = first ? k.dt * rhs[q] : fmaf(k.alpha, wcur[q], k.dt * rhs[q]);
-                    if (!last) static_cast<S *>(wbuf.p[q])[cell] = to_s<S>(wv);
                     const float yv = k.beta * wv - kcur[q];
                     fnew[q] = to_s<S>(val[q] + yv);
-                    static_cast<S *>(kbuf.p[q])[cell] = to_s<S>((to_c<float>(fnew[q]) - val[q]) - yv);
+                    const S cnew = to_s<S>((to_c<float>(fnew[q]) - val[q]) - yv);
+                    if (TMAIO) {
+                        stg(b, q)[threadIdx.x] = to_s<S>(wv);
+                        stg(b, 8 + q)[threadIdx.x] = cnew;
+                        stg(b, 16 + q)[threadIdx.x] = fnew[q];
+                    } else {
+                        if (!last) static_cast<S *>(wbuf.p[q])[cell] = to_s<S>(wv);
+                        static_cast<S *>(kbuf.p[q])[cell] = cnew;
+                    }
                 }
-                if (images && (edge_xy || z < R6 || z >= nz - R6)) {
+                if (TMAIO) {
+                    // the interior values go out with the plane's TMA stores; edge cells add images
+                    if (images && (edge_xy || z < R6 || z >= nz - R6)) {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q)
+                            store_with_images(static_cast<S *>(fout.p[q]), g, R6, true, x, y, z, fnew[q]);
+                    }
+                } else if (images && (edge_xy || z < R6 || z >= nz - R6)) {
 #pragma unroll
                     for (int q = 0; q < 8; ++q)
                         store_with_images(static_cast<S *>(fout.p[q]), g, R6, true, x, y, z, fnew[q]);
@@ -281,36 +346,57 @@ __device__ __forceinline__ bool mhdp_tile(const CUtensorMap *maps, const Ptrs8 &
                 }
             }
         }
+        if (TMAIO) {
+            fence_proxy_async();  // the staging writes above, before the TMA stores read them
+            bad = __syncthreads_or(!ok);
+            if (!bad && threadIdx.x == 0) {
+                const int z = zc0 + m;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    tma_store_3d(&io->fo[q], stg(b, 16 + q), x0, y0, z);
+                    if (!last) tma_store_3d(&io->w[q], stg(b, q), x0, y0, z);
+                    tma_store_3d(&io->c[q], stg(b, 8 + q), x0, y0, z);
+                }
+                bulk_commit();
+            }
+        }
         cell += nxy;
         oidx += opitch;
     }
+    if (TMAIO && threadIdx.x == 0) bulk_wait_all();  // staging stays valid until the stores are done
     if (bad && threadIdx.x == 0) {
         atomicOr(err, ERR_TIMEOUT);
         for (int j = max(0, issued - NR); j < issued; ++j)
             (void)mbar_wait_bounded(&full[j & (NR - 1)], ((unsigned)j / NR) & 1u, 100000000ull);
+        if (TMAIO)  // and the w/c loads still in flight (at most the last two planes)
+            for (int j = max(0, wc_issued - 2); j < wc_issued; ++j)
+                (void)mbar_wait_bounded(&wcbar[j & 1], ((unsigned)j >> 1) & 1u, 100000000ull);
     }
     return !bad;
 }
 
-template <typename S, int TY, int NR, int MODE>
+template <typename S, int TY, int NR, int MODE, bool TMAIO>
 __global__ void __launch_bounds__(32 * TY, 1)
-mhdp_kernel(const __grid_constant__ MhdMaps maps, Ptrs8 fout, Ptrs8 wbuf, Ptrs8 kbuf, Ptrs8 rbuf, Geom g,
-            MK<float> k, int zc, int first, int last, int images, unsigned *err) {
-    using Cfg = MpCfg<S, TY, NR>;
+mhdp_kernel(const __grid_constant__ MhdMaps maps, const __grid_constant__ MhdIoMaps io, Ptrs8 fout, Ptrs8 wbuf,
+            Ptrs8 kbuf, Ptrs8 rbuf, Geom g, MK<float> k, int zc, int first, int last, int images, unsigned *err) {
+    using Cfg = MpCfg<S, TY, NR, TMAIO>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     S *raw = reinterpret_cast<S *>(base);
     float2 *pairs = reinterpret_cast<float2 *>(base + Cfg::RAW_BYTES);
+    S *stage = reinterpret_cast<S *>(base + Cfg::RAW_BYTES + Cfg::PAIR_BYTES);
     __shared__ __align__(8) uint64_t full[NR];
-    mhdp_tile<S, TY, NR, MODE>(maps.m, fout, wbuf, kbuf, rbuf, g, k, blockIdx.x, blockIdx.y, blockIdx.z, zc, first,
-                               last, images, err, raw, pairs, full);
+    __shared__ __align__(8) uint64_t wcbar[2];
+    mhdp_tile<S, TY, NR, MODE, TMAIO>(maps.m, &io, fout, wbuf, kbuf, rbuf, g, k, blockIdx.x, blockIdx.y, blockIdx.z,
+                                      zc, first, last, images, err, raw, pairs, stage, full, wcbar);
 }
 
-template <typename S, int TY, int NR, int MODE>
-cudaError_t runp(int sub, const MhdMaps &maps, const Ptrs8 &fo, const Ptrs8 &w, const Ptrs8 &kc, const Ptrs8 &rhs,
-                 const Geom &g, const MK<float> &k, bool images, unsigned *err, cudaStream_t s) {
-    using Cfg = MpCfg<S, TY, NR>;
-    auto kern = mhdp_kernel<S, TY, NR, MODE>;
+template <typename S, int TY, int NR, int MODE, bool TMAIO = false>
+cudaError_t runp(int sub, const MhdMaps &maps, const MhdIoMaps *io, const Ptrs8 &fo, const Ptrs8 &w,
+                 const Ptrs8 &kc, const Ptrs8 &rhs, const Geom &g, const MK<float> &k, bool images, unsigned *err,
+                 cudaStream_t s) {
+    using Cfg = MpCfg<S, TY, NR, TMAIO>;
+    auto kern = mhdp_kernel<S, TY, NR, MODE, TMAIO>;
     static int occ[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -329,26 +415,30 @@ cudaError_t runp(int sub, const MhdMaps &maps, const Ptrs8 &fo, const Ptrs8 &w, 
     const int chunks = choose_zchunks(tx * ty, nz, occ[dev] * device_sms(), 0.5);
     const int zc = (nz + chunks - 1) / chunks;
     dim3 grid(tx, ty, (unsigned)((nz + zc - 1) / zc));
-    kern<<<grid, 32 * TY, Cfg::SMEM, s>>>(maps, fo, w, kc, rhs, g, k, zc, sub == 0 ? 1 : 0, sub == 2 ? 1 : 0,
-                                          images ? 1 : 0, err);
+    static const MhdIoMaps none{};
+    kern<<<grid, 32 * TY, Cfg::SMEM, s>>>(maps, io ? *io : none, fo, w, kc, rhs, g, k, zc, sub == 0 ? 1 : 0,
+                                          sub == 2 ? 1 : 0, images ? 1 : 0, err);
     return cudaGetLastError();
 }
 
-// Variants: (TY rows of 32 cells, NR raw planes).
-#define MHDP_VARIANTS(X) X(8, 4) X(8, 2)
+// Variants: (TY rows of 32 cells, NR raw planes, TMA I/O).
+#define MHDP_VARIANTS(X) X(8, 4, false) X(8, 2, false) X(8, 2, true)
 
 }  // namespace
 
-int mhd_pairs_num_variants() { return 2; }
+int mhd_pairs_num_variants() { return 3; }
 
 const char *mhd_pairs_variant_name(int v) {
-    static const char *names[] = {"pairs_tx32_ty8_raw4", "pairs_tx32_ty8_raw2"};
-    return (v >= 0 && v < 2) ? names[v] : "?";
+    static const char *names[] = {"pairs_tx32_ty8_raw4", "pairs_tx32_ty8_raw2", "pairs_tx32_ty8_raw2_tmaio"};
+    return (v >= 0 && v < 3) ? names[v] : "?";
 }
+
+bool mhd_pairs_variant_uses_io(int v) { return v == 2; }
+int mhd_pairs_io_box_rows(int v) { (void)v; return 8; }
 
 void mhd_pairs_box(int storage, int v, int box[3]) {
     int i = 0;
-#define X(TY, NR)                                                                                     \
+#define X(TY, NR, IO)                                                                                 \
     if (i++ == v) {                                                                                   \
         box[0] = storage == 3 ? MpCfg<__nv_bfloat16, TY, NR>::TXP : MpCfg<float, TY, NR>::TXP;        \
         box[1] = TY + 2 * R6;                                                                         \
@@ -358,17 +448,25 @@ void mhd_pairs_box(int storage, int v, int box[3]) {
 #undef X
 }
 
-cudaError_t launch_mhd_pairs(int storage, int mode, int sub, const MhdMaps &maps, const Ptrs8 &fo, const Ptrs8 &w,
-                             const Ptrs8 &kc, const Ptrs8 &rhs, const Geom &g, const MK<float> &k, bool images,
-                             unsigned *err, cudaStream_t s, int variant) {
+cudaError_t launch_mhd_pairs(int storage, int mode, int sub, const MhdMaps &maps, const MhdIoMaps *io,
+                             const Ptrs8 &fo, const Ptrs8 &w, const Ptrs8 &kc, const Ptrs8 &rhs, const Geom &g,
+                             const MK<float> &k, bool images, unsigned *err, cudaStream_t s, int variant) {
     int i = 0;
     cudaError_t res = cudaErrorInvalidValue;
-#define X(TY, NR)                                                                               \
-    if (i++ == variant) {                                                                       \
-        if (mode == 0)                                                                          \
-            res = runp<S, TY, NR, 0>(sub, maps, fo, w, kc, rhs, g, k, images, err, s);          \
-        else                                                                                    \
-            res = runp<S, TY, NR, 1>(sub, maps, fo, w, kc, rhs, g, k, images, err, s);          \
+    // the TMA-I/O variant needs its descriptors and serves the RK substep; otherwise its plain twin
+    const bool io_ok = io != nullptr && mode == 0;
+#define X(TY, NR, IO)                                                                                       \
+    if (i++ == variant) {                                                                                   \
+        bool done = false;                                                                                  \
+        if constexpr (IO) {                                                                                 \
+            if (mode == 0 && io_ok) {                                                                       \
+                res = runp<S, TY, NR, 0, true>(sub, maps, io, fo, w, kc, rhs, g, k, images, err, s);        \
+                done = true;                                                                                \
+            }                                                                                               \
+        }                                                                                                   \
+        if (!done)                                                                                          \
+            res = mode == 0 ? runp<S, TY, NR, 0>(sub, maps, nullptr, fo, w, kc, rhs, g, k, images, err, s)  \
+                            : runp<S, TY, NR, 1>(sub, maps, nullptr, fo, w, kc, rhs, g, k, images, err, s); \
     }
     if (storage == 2) {
         using S = float;
