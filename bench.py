@@ -668,6 +668,7 @@ def run_case(args):
     from paper_2406_08923_gb300 import synth
     kind, storage, n0, steps = CASES[args.case]
     n = args.n or n0
+    steps = args.job_steps or steps
     stream = torch.cuda.current_stream()
     if kind == "heat":
         par = L.heat_params(n)
@@ -707,6 +708,7 @@ def main():
                     help="run one workload only (no autotune), e.g. for an ncu capture")
     ap.add_argument("--n", type=int, default=None, help="grid size for --case")
     ap.add_argument("--variant", type=int, default=0, help="kernel variant for --case")
+    ap.add_argument("--job-steps", type=int, default=None, help="steps per job for --case")
     ap.add_argument("--serving", action="store_true", help="serving configuration only (one JSON line)")
     ap.add_argument("--radius-sweep", action="store_true", help="diffusion radius sweep only (one JSON line)")
     args = ap.parse_args()

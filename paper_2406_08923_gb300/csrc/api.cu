@@ -21,7 +21,6 @@ thread_local std::string g_create_detail;
 struct TmaEntry {
     const void *ptr;
     int box[3];
-    int64_t dims0;  // 0 for a map of the whole padded field, else the view's x extent
     CUtensorMap map;
 };
 
@@ -146,7 +145,7 @@ static void free_scratch(stencil_t p) {
 // Encode (or fetch from the per-plan cache) the TMA descriptor of a field for a box shape.
 static stencil_status tma_map(stencil_t p, const void *ptr, const int box[3], CUtensorMap *out) {
     for (auto &e : p->tma)
-        if (e.ptr == ptr && e.dims0 == 0 && e.box[0] == box[0] && e.box[1] == box[1] && e.box[2] == box[2]) {
+        if (e.ptr == ptr && e.box[0] == box[0] && e.box[1] == box[1] && e.box[2] == box[2]) {
             *out = e.map;
             return STENCIL_OK;
         }
@@ -166,45 +165,12 @@ static stencil_status tma_map(stencil_t p, const void *ptr, const int box[3], CU
     cuuint32_t es[3] = {1, 1, 1};
     TmaEntry ent;
     ent.ptr = ptr;
-    ent.dims0 = 0;
     std::memcpy(ent.box, box, sizeof(ent.box));
     CUresult r = fn(&ent.map, dt, 3, const_cast<void *>(ptr), dims, strides, bx, es,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS)
         return fail(p, STENCIL_ECUDA, "cuTensorMapEncodeTiled failed with CUresult " + std::to_string((int)r));
-    if (p->tma.size() >= 96) p->tma.erase(p->tma.begin());
-    p->tma.push_back(ent);
-    *out = ent.map;
-    return STENCIL_OK;
-}
-
-// TMA descriptor of a 3D view (extents dims, row and plane strides in bytes) of the plan's
-// storage type at ptr, for boxes of `box` elements; cached like tma_map.
-static stencil_status tma_map_view(stencil_t p, const void *ptr, const int64_t dims[3], const int64_t strides[2],
-                                   const int box[3], CUtensorMap *out) {
-    for (auto &e : p->tma)
-        if (e.ptr == ptr && e.dims0 == dims[0] && e.box[0] == box[0] && e.box[1] == box[1] && e.box[2] == box[2]) {
-            *out = e.map;
-            return STENCIL_OK;
-        }
-    auto fn = encode_fn();
-    if (!fn) return fail(p, STENCIL_ECUDA, "cuTensorMapEncodeTiled entry point unavailable");
-    const CUtensorMapDataType dt = p->storage == STENCIL_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
-                                   : p->storage == STENCIL_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                                               : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    cuuint64_t d[3] = {(cuuint64_t)dims[0], (cuuint64_t)dims[1], (cuuint64_t)dims[2]};
-    cuuint64_t st[2] = {(cuuint64_t)strides[0], (cuuint64_t)strides[1]};
-    cuuint32_t bx[3] = {(cuuint32_t)box[0], (cuuint32_t)box[1], (cuuint32_t)box[2]};
-    cuuint32_t es[3] = {1, 1, 1};
-    TmaEntry ent;
-    ent.ptr = ptr;
-    ent.dims0 = dims[0];
-    std::memcpy(ent.box, box, sizeof(ent.box));
-    CUresult r = fn(&ent.map, dt, 3, const_cast<void *>(ptr), d, st, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS)
-        return fail(p, STENCIL_ECUDA, "cuTensorMapEncodeTiled (view) failed with CUresult " + std::to_string((int)r));
     if (p->tma.size() >= 96) p->tma.erase(p->tma.begin());
     p->tma.push_back(ent);
     *out = ent.map;
@@ -565,27 +531,8 @@ static stencil_status run_pass(stencil_t p, void *const *src, void *const *dst, 
         if (st != STENCIL_OK) return st;
     }
     Ptrs8 none{};
-    // TMA-I/O variants: interior views of the outputs and views of the dense RK register and Kahan
-    // terms (whose rows must be whole 16-byte multiples for TMA; otherwise the kernel falls back)
-    MhdIoMaps io;
-    const MhdIoMaps *iop = nullptr;
-    int rows = 0;
-    if (mhd_variant_uses_io(storage_code(p->storage), p->variant, &rows) && (g.n[0] * p->esize) % 16 == 0) {
-        const int iobox[3] = {32, rows, 1};
-        const int64_t idims[3] = {g.n[0], g.n[1], g.n[2]};
-        const int64_t fstr[2] = {g.pad[0] * p->esize, g.pad[0] * g.pad[1] * p->esize};
-        const int64_t dstr[2] = {g.n[0] * p->esize, g.n[0] * g.n[1] * p->esize};
-        for (int q = 0; q < 8; ++q) {
-            const void *fo = static_cast<const char *>(dst[q]) + g.idx(0, 0, 0) * p->esize;
-            stencil_status st = tma_map_view(p, fo, idims, fstr, iobox, &io.fo[q]);
-            if (st == STENCIL_OK) st = tma_map_view(p, p->w[q], idims, dstr, iobox, &io.w[q]);
-            if (st == STENCIL_OK) st = tma_map_view(p, p->kc[q], idims, dstr, iobox, &io.c[q]);
-            if (st != STENCIL_OK) return st;
-        }
-        iop = &io;
-    }
     CK(p, launch_mhd(storage_code(p->storage), 0, sub, maps, ptrs(dst, 8), ptrs(p->w, 8), ptrs(p->kc, 8), none,
-                     g, p->mconst, true, p->err, s, p->variant, iop),
+                     g, p->mconst, true, p->err, s, p->variant),
        "mhd launch");
     return STENCIL_OK;
 }

@@ -89,21 +89,13 @@ struct MhdConst {
 struct MhdMaps {
     CUtensorMap m[8];
 };
-// TMA descriptors for the substep's outputs and RK state: the interior of each output field
-// (dims nx x ny x nz within the padded array), and the dense RK register w and Kahan term c.
-struct MhdIoMaps {
-    CUtensorMap fo[8], w[8], c[8];
-};
+
 // mode 0: RK substep `sub` (0..2) writing f_out (+images), w and (for Kahan) c;
 // mode 1: right-hand side only, written densely to rhs (compute type).
-struct MhdIoMaps;
 cudaError_t launch_mhd(int storage, int mode, int sub, const MhdMaps &maps, const Ptrs8 &fout,
                        const Ptrs8 &w, const Ptrs8 &kc, const Ptrs8 &rhs, const Geom &g,
                        const MhdConst &k, bool images, unsigned *err, cudaStream_t s,
-                       int variant, const MhdIoMaps *io = nullptr);
-// Whether an MHD variant stores its outputs with TMA (it then wants MhdIoMaps with boxes of
-// 32 x rows x 1), and the box rows.
-bool mhd_variant_uses_io(int storage, int variant, int *rows);
+                       int variant);
 void mhd_box(int storage, int variant, int box[3]);
 int mhd_num_variants(int storage);
 const char *mhd_variant_name(int storage, int variant);
@@ -131,18 +123,6 @@ template <typename C> struct MK {
     C K;
     C dt, alpha, beta;
 };
-
-// The field-pair MHD kernel family for FP32/BF16 storage (mhd_pairs.cu), reached through
-// launch_mhd's variants 3.. for those storage types.
-int mhd_pairs_num_variants();
-const char *mhd_pairs_variant_name(int variant);
-void mhd_pairs_box(int storage, int variant, int box[3]);
-// io: descriptors for the TMA-I/O variant (NULL: that variant falls back to its plain twin).
-bool mhd_pairs_variant_uses_io(int variant);
-int mhd_pairs_io_box_rows(int variant);
-cudaError_t launch_mhd_pairs(int storage, int mode, int sub, const MhdMaps &maps, const MhdIoMaps *io,
-                             const Ptrs8 &fo, const Ptrs8 &w, const Ptrs8 &kc, const Ptrs8 &rhs, const Geom &g,
-                             const MK<float> &k, bool images, unsigned *err, cudaStream_t s, int variant);
 
 // Work items of one batched launch.  Every item owns a contiguous range of virtual CTAs
 // [cta_begin, cta_begin + tiles); a persistent grid strides over the virtual CTAs and finds

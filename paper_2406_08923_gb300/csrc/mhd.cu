@@ -89,7 +89,7 @@ __device__ __forceinline__ C dmix(const W &w, int q, int pair, const C *m) {
 // derivatives are evaluated field by field, only those some term uses (lnrho and s: gradients,
 // plus Laplacians when K != 0; A: the off-diagonal first derivatives and the Hessian), then
 // assembled by mhd_rhs_assemble.
-template <typename C, typename W>
+template <bool CONDUCT, typename C, typename W>
 __device__ __forceinline__ void mhd_rhs_cell(const W &w, const MK<C> &k, C *rhs, C *val) {
     MhdDerivs<C> d;
 #pragma unroll
@@ -100,7 +100,7 @@ __device__ __forceinline__ void mhd_rhs_cell(const W &w, const MK<C> &k, C *rhs,
         d.gs[a] = d1(w, F_SS, a, k.d1[a]);
     }
     d.laplr = d.laps = C(0);
-    if (k.K != C(0)) {
+    if constexpr (CONDUCT) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             d.laplr += d2(w, F_LNRHO, a, k.d2c[a], k.d2[a]);
@@ -154,7 +154,7 @@ __device__ __forceinline__ void mhd_rhs_cell(const W &w, const MK<C> &k, C *rhs,
         d.gdiva[1] += hc[1];
         d.gdiva[2] += hc[2];
     }
-    mhd_rhs_assemble(d, k, rhs);
+    mhd_rhs_assemble<CONDUCT>(d, k, rhs);
 #pragma unroll
     for (int q = 0; q < 8; ++q) val[q] = d.val[q];
 }
@@ -162,7 +162,7 @@ __device__ __forceinline__ void mhd_rhs_cell(const W &w, const MK<C> &k, C *rhs,
 // One xy-tile of one z-chunk of one RK substep (or RHS evaluation): the whole pipeline of a
 // CTA.  `maps` points at 8 consecutive descriptors (parameter or global memory); `k` may live
 // in parameter or shared memory.  Returns false if a bounded wait expired.
-template <typename S, typename C, bool KAHAN, int MODE, int TX, int TY, int NSLOT>
+template <typename S, typename C, bool KAHAN, int MODE, int TX, int TY, int NSLOT, bool CONDUCT>
 __device__ __forceinline__ bool mhd_tile(const CUtensorMap *maps, const Ptrs8 &fout, const Ptrs8 &wbuf,
                                          const Ptrs8 &kbuf, const Ptrs8 &rbuf, const Geom &g, const MK<C> &k,
                                          int tile_x, int tile_y, int tile_z, int zc, int first, int last,
@@ -235,7 +235,7 @@ __device__ __forceinline__ bool mhd_tile(const CUtensorMap *maps, const Ptrs8 &f
             for (int q = 0; q < 8; ++q) { wcur[q] = wpre[q]; kcur[q] = kpre[q]; }
             if (m + 1 < zend - zc0) prefetch(cell + nxy);  // next plane, overlapped with compute
             C rhs[8], val[8];
-            mhd_rhs_cell<C>(w, k, rhs, val);
+            mhd_rhs_cell<CONDUCT, C>(w, k, rhs, val);
             if (MODE == 1) {
 #pragma unroll
                 for (int q = 0; q < 8; ++q) static_cast<C *>(rbuf.p[q])[cell] = rhs[q];
@@ -277,7 +277,7 @@ __device__ __forceinline__ bool mhd_tile(const CUtensorMap *maps, const Ptrs8 &f
     return !bad;
 }
 
-template <typename S, typename C, bool KAHAN, int MODE, int TX, int TY, int NSLOT, int MINB>
+template <typename S, typename C, bool KAHAN, int MODE, int TX, int TY, int NSLOT, int MINB, bool CONDUCT>
 __global__ void __launch_bounds__(TX *TY, MINB)
 mhd_kernel(const __grid_constant__ MhdMaps maps, Ptrs8 fout, Ptrs8 wbuf, Ptrs8 kbuf, Ptrs8 rbuf, Geom g,
            MK<C> k, int zc, int first, int last, int images, unsigned *err) {
@@ -286,7 +286,7 @@ mhd_kernel(const __grid_constant__ MhdMaps maps, Ptrs8 fout, Ptrs8 wbuf, Ptrs8 k
     S *ring = reinterpret_cast<S *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     __shared__ __align__(8) uint64_t full[NSLOT];
     (void)Cfg::SMEM;
-    mhd_tile<S, C, KAHAN, MODE, TX, TY, NSLOT>(maps.m, fout, wbuf, kbuf, rbuf, g, k, blockIdx.x, blockIdx.y,
+    mhd_tile<S, C, KAHAN, MODE, TX, TY, NSLOT, CONDUCT>(maps.m, fout, wbuf, kbuf, rbuf, g, k, blockIdx.x, blockIdx.y,
                                                blockIdx.z, zc, first, last, images, err, ring, full);
 }
 
@@ -313,12 +313,12 @@ static MK<C> make_k(const MhdConst &c, double alpha, double beta) {
 static const double RK_A[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0};
 static const double RK_B[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
 
-template <typename S, typename C, bool KAHAN, int MODE, int TX, int TY, int NSLOT, int MINB>
+template <typename S, typename C, bool KAHAN, int MODE, int TX, int TY, int NSLOT, int MINB, bool CONDUCT>
 static cudaError_t run(int sub, const MhdMaps &maps, const Ptrs8 &fo, const Ptrs8 &w, const Ptrs8 &kc,
                        const Ptrs8 &rhs, const Geom &g, const MhdConst &c, bool images, unsigned *err,
                        cudaStream_t s) {
     using Cfg = MhdCfg<S, TX, TY, NSLOT>;
-    auto kern = mhd_kernel<S, C, KAHAN, MODE, TX, TY, NSLOT, MINB>;
+    auto kern = mhd_kernel<S, C, KAHAN, MODE, TX, TY, NSLOT, MINB, CONDUCT>;
     static int occ[64] = {};  // resident CTAs per SM, per device
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -352,23 +352,14 @@ static const char *MHD_F64_NAMES[] = {"tx32_ty4_s8_b1", "tx16_ty8_s8_b1"};
 static const char *MHD_F32_NAMES[] = {"tx32_ty8_s8_b1", "tx32_ty4_s8_b2", "tx16_ty8_s8_b2"};
 static const char *MHD_BF16_NAMES[] = {"tx32_ty8_s8_b1", "tx32_ty8_s8_b2", "tx32_ty4_s8_b3"};
 
-// FP32 and BF16 storage: the scalar variants, then the field-pair kernel's (mhd_pairs.cu).
-int mhd_num_variants(int storage) { return storage == 1 ? 2 : 3 + mhd_pairs_num_variants(); }
+int mhd_num_variants(int storage) { return storage == 1 ? 2 : 3; }
 
 const char *mhd_variant_name(int storage, int v) {
     if (v < 0 || v >= mhd_num_variants(storage)) return "?";
-    if (storage != 1 && v >= 3) return mhd_pairs_variant_name(v - 3);
     return storage == 1 ? MHD_F64_NAMES[v] : storage == 2 ? MHD_F32_NAMES[v] : MHD_BF16_NAMES[v];
 }
 
-bool mhd_variant_uses_io(int storage, int v, int *rows) {
-    if (storage == 1 || v < 3 || !mhd_pairs_variant_uses_io(v - 3)) return false;
-    if (rows) *rows = mhd_pairs_io_box_rows(v - 3);
-    return true;
-}
-
 void mhd_box(int storage, int v, int box[3]) {
-    if (storage != 1 && v >= 3) return mhd_pairs_box(storage, v - 3, box);
     int i = 0;
     auto put = [&](int tx, int ty, int hx) {
         if (i++ == v) { box[0] = tx + 2 * hx; box[1] = ty + 2 * R6; box[2] = 1; }
@@ -382,18 +373,19 @@ void mhd_box(int storage, int v, int box[3]) {
 
 cudaError_t launch_mhd(int storage, int mode, int sub, const MhdMaps &maps, const Ptrs8 &fo, const Ptrs8 &w,
                        const Ptrs8 &kc, const Ptrs8 &rhs, const Geom &g, const MhdConst &c, bool images,
-                       unsigned *err, cudaStream_t s, int variant, const MhdIoMaps *io) {
-    if (storage != 1 && variant >= 3)
-        return launch_mhd_pairs(storage, mode, sub, maps, io, fo, w, kc, rhs, g,
-                                make_k<float>(c, RK_A[sub], RK_B[sub]), images, err, s, variant - 3);
+                       unsigned *err, cudaStream_t s, int variant) {
     int i = 0;
     cudaError_t res = cudaErrorInvalidValue;
-#define X(TX, TY, NS, MB)                                                                             \
-    if (i++ == variant) {                                                                             \
-        if (mode == 0)                                                                                \
-            res = run<S, C, KH, 0, TX, TY, NS, MB>(sub, maps, fo, w, kc, rhs, g, c, images, err, s);  \
-        else                                                                                          \
-            res = run<S, C, KH, 1, TX, TY, NS, MB>(sub, maps, fo, w, kc, rhs, g, c, images, err, s);  \
+    // the conduction term of A3 is compiled in only for launches with K != 0
+    const bool cond = c.K != 0.0;
+#define X(TX, TY, NS, MB)                                                                                  \
+    if (i++ == variant) {                                                                                  \
+        if (mode == 0)                                                                                     \
+            res = cond ? run<S, C, KH, 0, TX, TY, NS, MB, true>(sub, maps, fo, w, kc, rhs, g, c, images, err, s) \
+                       : run<S, C, KH, 0, TX, TY, NS, MB, false>(sub, maps, fo, w, kc, rhs, g, c, images, err, s); \
+        else                                                                                               \
+            res = cond ? run<S, C, KH, 1, TX, TY, NS, MB, true>(sub, maps, fo, w, kc, rhs, g, c, images, err, s) \
+                       : run<S, C, KH, 1, TX, TY, NS, MB, false>(sub, maps, fo, w, kc, rhs, g, c, images, err, s); \
     }
     if (storage == 1) {
         using S = double; using C = double; constexpr bool KH = false;
@@ -441,8 +433,14 @@ mhd_batch_kernel(const BatchHeader *hdr, const BatchMhd *items, float alpha, flo
         __syncthreads();
         const Geom g = it.g;
         Ptrs8 none{};
-        const bool ok = mhd_tile<float, float, true, 0, MB_TX, MB_TY, MB_NSLOT>(
-            it.maps, it.fout, it.w, it.kc, none, g, ks, tx, ty, tz, it.zc, first, last, 1, err, ring, full);
+        const bool ok =
+            it.k.K != 0.f
+                ? mhd_tile<float, float, true, 0, MB_TX, MB_TY, MB_NSLOT, true>(it.maps, it.fout, it.w, it.kc, none, g, ks,
+                                                                              tx, ty, tz, it.zc, first, last, 1, err,
+                                                                              ring, full)
+                : mhd_tile<float, float, true, 0, MB_TX, MB_TY, MB_NSLOT, false>(it.maps, it.fout, it.w, it.kc, none, g,
+                                                                               ks, tx, ty, tz, it.zc, first, last, 1,
+                                                                               err, ring, full);
         __syncthreads();
         if (!ok) return;
     }

@@ -1,7 +1,6 @@
 // mhd_rhs.cuh -- the pointwise part of the MHD step: the right-hand side of Eqs. A1-A4
-// (phi of Eq. 9) from the derivative quantities of one cell.  Shared by the scalar kernel
-// (mhd.cu) and the field-pair kernel (mhd_pairs.cu), so both evaluate the same expression in
-// the same order.
+// (phi of Eq. 9) from the derivative quantities of one cell, shared by the per-grid MHD kernels
+// and the batched serving kernel (mhd.cu).
 #pragma once
 
 #include "internal.h"
@@ -27,8 +26,9 @@ template <typename C> struct MhdDerivs {
 
 // The right-hand side of Eqs. A1-A4 (H = C = 0).  The conduction term of A3 with constant K
 // uses T = T0 exp(phi), phi = gamma s/cp + (gamma-1)(lnrho - lnrho0):
-// div(K grad T)/(rho T) = (K/rho)(lap phi + |grad phi|^2).
-template <typename C>
+// div(K grad T)/(rho T) = (K/rho)(lap phi + |grad phi|^2).  It is compiled in only for
+// CONDUCT (launches with K != 0), so the K = 0 kernels carry none of its registers.
+template <bool CONDUCT, typename C>
 __device__ __forceinline__ void mhd_rhs_assemble(const MhdDerivs<C> &d, const MK<C> &k, C *rhs) {
     const C jx = (d.gdiva[0] - d.lapa[0]) * k.inv_mu0;
     const C jy = (d.gdiva[1] - d.lapa[1]) * k.inv_mu0;
@@ -69,7 +69,7 @@ __device__ __forceinline__ void mhd_rhs_assemble(const MhdDerivs<C> &d, const MK
     const C j2 = jx * jx + jy * jy + jz * jz;
     rhs[F_SS] = -(ux * d.gs[0] + uy * d.gs[1] + uz * d.gs[2]) +
                 (k.eta * k.mu0 * j2 + C(2) * rho * k.nu * s2 + k.zeta * rho * divu * divu) * inv_rhoT;
-    if (k.K != C(0)) {
+    if constexpr (CONDUCT) {
         const C gp = k.gamma * k.inv_cp, gm1 = k.gamma - C(1);
         C gphi2 = C(0);
 #pragma unroll
