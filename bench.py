@@ -50,8 +50,12 @@ def _peaks():
 # DRAM traffic per launch of the dominant kernel from one ncu capture (profiles/), valid only
 # while the kernel source is unchanged (first 16 hex digits of sha256 of each file).
 NCU_TRAFFIC = {
-    "heat_f64": {"variant": "tx32_by8_ry1_s7_zc64", "bytes": 155.361792e6 + 105.888e6,
-                 "src": {"diffusion.cu": "eb8c2175aa4dfaa2", "common.cuh": "aebf8526fb672ab0"}},
+    # dram__bytes_read.sum + dram__bytes_write.sum per launch (mean of 3 launches, 1-pass capture)
+    "heat_f64": {"variant": "vx2_by8_ry1_zb2_s8", "bytes": 145022208 + 102321920,
+                 "src": {"diffusion.cu": "2744d5010604daf8", "common.cuh": "ce4816ab9ebe500d"}},
+    # one launch of the --set full capture at 256^3
+    "heat_f32": {"variant": "f32_by4_ry2_zb2_s8_m3", "bytes": 82109696 + 28893952,
+                 "src": {"diffusion_f32.cu": "89234518939e8c73", "common.cuh": "ce4816ab9ebe500d"}},
 }
 
 
@@ -611,7 +615,8 @@ def run_extras(L, synth, stream, hbm_peak, args):
         "ms_per_job": round(res["ms_job"], 4), "kernel_ms_avg": round(res["ms_kernel"], 5),
         "mcell_updates_per_s": round(cells * HEAT_STEPS / (res["ms_job"] / 1e3) / 1e6, 1),
         "variant": res["variant"],
-        "roofline": _roof("hbm", gbs, hbm_peak, "GB/s", note="8 B/cell-update algorithmic")}
+        "roofline": _roof("hbm", gbs, hbm_peak, "GB/s", traffic=_traffic("heat_f32", res["variant"]),
+                          note="8 B/cell-update algorithmic; traffic = ncu dram bytes/launch")}
     res["plan"].close()
     # config 2 FP32 at 512^3: the two 540 MB fields far exceed the 126 MB L2
     n5 = 2 * HEAT_N
