@@ -484,12 +484,13 @@ static stencil_status run_pass(stencil_t p, void *const *src, void *const *dst, 
     const bool periodic = p->bc == STENCIL_BC_PERIODIC;
     const Geom &g = p->geom;
     if (p->kind == STENCIL_MAXFILTER) {
-        CK(p, launch_maxfilter(storage_code(p->storage), p->radius, src[0], dst[0], g, periodic, periodic, s),
+        CK(p, launch_maxfilter(storage_code(p->storage), p->radius, src[0], dst[0], g, periodic, periodic, p->err, s),
            "maxfilter launch");
         return STENCIL_OK;
     }
     if (p->kind == STENCIL_XCORR && p->radius > 4) {
-        CK(p, launch_xcorr_wide(storage_code(p->storage), p->radius, src[0], dst[0], g, p->wdev, periodic, periodic, s),
+        CK(p, launch_xcorr_wide(storage_code(p->storage), p->radius, src[0], dst[0], g, p->wdev, periodic, periodic,
+                                p->err, s),
            "xcorr (wide) launch");
         return STENCIL_OK;
     }

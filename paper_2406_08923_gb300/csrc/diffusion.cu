@@ -8,8 +8,7 @@
 //
 // GB300 design (2.5D z-streaming):
 //   * A CTA owns a TX x TY tile of the xy-plane (TX = 32 VX, TY = BY RY) and marches along z
-//     over a chunk of planes (chunk length chosen by the host from the kernel's occupancy so
-//     the grid fills whole waves of the 152 SMs).  Each padded input plane tile
+//     over a short chunk of planes (4), so the grid is tens of waves of small CTAs.  Each padded input plane tile
 //     (TX + 8) x (TY + 6) arrives by one TMA load (cp.async.bulk.tensor.3d) in a ring of
 //     NSLOT shared-memory slots, completion on one mbarrier per slot; loads run NSLOT - 3
 //     planes ahead of the compute.
@@ -423,8 +422,11 @@ static cudaError_t run(const CUtensorMap *map, void *out, const Geom &g, const D
     }
     const int tx = (int)((g.n[0] + Cfg::TX - 1) / Cfg::TX), ty = (int)((g.n[1] + Cfg::TY - 1) / Cfg::TY);
     const int nz = (int)g.n[2];
-    const int chunks = choose_zchunks(tx * ty, nz, occ[dev] * device_sms(), sizeof(T) == 4 ? 0.5 : 0.05);
-    const int zc = (nz + chunks - 1) / chunks;
+    // FP64 is bound by the FP64 pipe, and the y/z halo re-reads of short chunks hit in L2, so
+    // chunks are short (4 planes): tens of waves of small CTAs keep the pipe evenly fed through
+    // every CTA's start-up and the grid's tail (5 % faster than whole waves of long chunks at
+    // 256^3).
+    const int zc = std::min(nz, 4);
     dim3 grid(tx, ty, (unsigned)((nz + zc - 1) / zc));
     return launch_pdl(k, grid, dim3(32 * BY), Cfg::SMEM, s, *map, static_cast<T *>(out), g, c, zc, images ? 1 : 0,
                       err);

@@ -44,9 +44,9 @@ cudaError_t launch_xcorr(int dtype, int r, const void *in, void *out, const Geom
 // per launch (xcorr_wide.cu).
 int xcorr_wide_max_radius();
 cudaError_t launch_xcorr_wide(int dtype, int r, const void *in, void *out, const Geom &g, const void *wdev,
-                              bool periodic, bool images, cudaStream_t s);
+                              bool periodic, bool images, unsigned *err, cudaStream_t s);
 cudaError_t launch_maxfilter(int dtype, int r, const void *in, void *out, const Geom &g, bool periodic, bool images,
-                             cudaStream_t s);
+                             unsigned *err, cudaStream_t s);
 
 // Grid sizing shared by the z-streaming kernels: number of z-chunks that best fills whole
 // waves of `slots` resident CTAs (see diffusion.cu), and the SM count of the current device.

@@ -83,69 +83,145 @@ __device__ __forceinline__ void put1(T *outx, int64_t n, int r, int images, int6
     }
 }
 
+// Shared-memory layout of one staging buffer of the wide cross-correlation: the chunk's cells
+// c0 - r .. c0 + CH + r - 1 start at element `lead` = rr - r, where rr is r rounded up to whole
+// 16-byte groups, so that a bulk copy of cells c0 - rr .. c0 + CH + rr - 1 lands at element 0.
+// Past the span come zeros for the padded weight blocks.
+template <typename T> struct WideBuf {
+    static constexpr int V = Wide<T>::V, CH = WT * V, L = 16 / (int)sizeof(T);
+    static __host__ __device__ int rr(int r) { return (r + L - 1) / L * L; }
+    static __host__ __device__ int nwp(int r) { return (2 * r + 1 + V - 1) / V * V; }
+    // elements per buffer (a multiple of L, so every buffer starts 16-byte aligned)
+    static __host__ __device__ int elems(int r) { return (2 * rr(r) + CH + nwp(r) + V + L - 1) / L * L; }
+    static __host__ __device__ int wlen(int r) { return (nwp(r) + L - 1) / L * L; }
+};
+
+// The chunk's staging can use one bulk copy when its whole aligned span lies in the interior
+// (the edge chunks wrap or read the caller's halo through `stage`).
+__device__ __forceinline__ bool wide_bulk_ok(int64_t c0, int64_t n, int ch, int rr) {
+    return c0 - rr >= 0 && c0 + ch + rr <= n;
+}
+
+// Persistent kernel: CTA b handles chunks b, b + G, b + 2G, ... (G = gridDim.x) with two
+// staging buffers.  While it computes chunk k, the bulk copy of chunk k + 1 (issued by thread 0,
+// completion on one mbarrier per buffer) is in flight, so the load latency of a chunk overlaps
+// the previous chunk's multiply-adds and stores.  Bounded waits: on expiry the CTA records
+// ERR_TIMEOUT, waits (bounded) for its copy in flight and returns.
 template <typename T>
 __global__ void __launch_bounds__(WT)
 xcorr_wide_kernel(const T *__restrict__ in, T *__restrict__ out, Geom geo, const T *__restrict__ wg, int r,
-                  int periodic, int images) {
-    constexpr int V = Wide<T>::V;
-    constexpr int CH = WT * V;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int nw = 2 * r + 1;
-    const int nwp = (nw + V - 1) / V * V;  // weights padded to whole blocks of V (zeros)
+                  int periodic, int images, unsigned *err) {
+    using B = WideBuf<T>;
+    constexpr int V = B::V, CH = B::CH, L = B::L;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full[2];
+    const int nw = 2 * r + 1, nwp = B::nwp(r), rr = B::rr(r), lead = rr - r, be = B::elems(r);
     T *ws = reinterpret_cast<T *>(smem_raw);
-    T *s = ws + nwp;                       // CH + nwp + V cells (the tail past the span is 0)
+    T *buf0 = ws + B::wlen(r);
     const int64_t n = geo.n[0];
-    const int64_t c0 = (int64_t)blockIdx.x * CH;
     const T *inx = in + geo.off[0];
     T *outx = out + geo.off[0];
+    const int64_t nchunks = (n + CH - 1) / CH;
+    const uint32_t bytes = (uint32_t)((CH + 2 * rr) * sizeof(T));
 
+    if (threadIdx.x == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_fence_init();
+    }
     for (int j = threadIdx.x; j < nwp; j += WT) ws[j] = j < nw ? wg[j] : T(0);
-    const int span = CH + 2 * r;
-    stage(inx, n, c0, r, span, CH, periodic, s);
-    for (int e = span + threadIdx.x; e < CH + nwp + V; e += WT) s[e] = T(0);
+    for (int e = threadIdx.x; e < 2 * be; e += WT) buf0[e] = T(0);
+    fence_proxy_async();  // the zero fill precedes the bulk copies into the same buffers
     __syncthreads();
 
-    const int base = threadIdx.x * V;
-    T acc[V];
-#pragma unroll
-    for (int v = 0; v < V; ++v) acc[v] = T(0);
-    for (int j0 = 0; j0 < nwp; j0 += V) {
-        T w[V], x[2 * V - 1];
-#pragma unroll
-        for (int u = 0; u < V; ++u) w[u] = ws[j0 + u];
-#pragma unroll
-        for (int k = 0; k < 2 * V - 1; ++k) x[k] = s[base + j0 + k];
-#pragma unroll
-        for (int u = 0; u < V; ++u)
-#pragma unroll
-            for (int v = 0; v < V; ++v) acc[v] = fma(w[u], x[v + u], acc[v]);
+    auto issue = [&](int64_t c, int b) {  // thread 0: bulk copy of chunk c into buffer b
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&full[b], bytes);
+        bulk_load_1d(buf0 + b * be, inx + c * CH - rr, bytes, &full[b]);
+    };
+    // per buffer b: bit b of `phase` is the mbarrier parity of its next copy, bit b of
+    // `inflight` says that a copy into it is outstanding (uniform across the CTA)
+    uint32_t phase = 0u, inflight = 0u;
+    int64_t c = blockIdx.x;
+    if (c < nchunks && wide_bulk_ok(c * CH, n, CH, rr)) {
+        if (threadIdx.x == 0) issue(c, 0);
+        inflight |= 1u;
     }
-    // results through shared memory (the staged cells are no longer needed), then coalesced
-    // 16-byte stores of the chunk and scalar stores of its periodic images
-    __syncthreads();
-#pragma unroll
-    for (int v = 0; v < V; ++v) s[base + v] = acc[v];
-    __syncthreads();
-    constexpr int L = 16 / (int)sizeof(T);
-    using VT = typename V16<T>::type;
-    if (c0 + CH <= n) {
-        for (int q = threadIdx.x; q < CH / L; q += WT) {
-            VT x;
-            T *e = reinterpret_cast<T *>(&x);
-#pragma unroll
-            for (int u = 0; u < L; ++u) e[u] = s[q * L + u];
-            reinterpret_cast<VT *>(outx + c0)[q] = x;
+    bool ok = true;
+    for (int k = 0; c < nchunks; ++k, c += gridDim.x) {
+        const int b = k & 1;
+        T *buf = buf0 + b * be;
+        const int64_t c0 = c * CH;
+        const int64_t cn = c + gridDim.x;  // prefetch the next chunk into the other buffer
+        if (cn < nchunks && wide_bulk_ok(cn * CH, n, CH, rr)) {
+            if (threadIdx.x == 0) issue(cn, b ^ 1);
+            inflight |= 2u >> b;
         }
-    } else {
-        for (int q = threadIdx.x; q < CH && c0 + q < n; q += WT) outx[c0 + q] = s[q];
+        const int span = CH + 2 * r;
+        if (inflight & (1u << b)) {
+            ok = mbar_wait_bounded(&full[b], (phase >> b) & 1u);
+            if (ok) {
+                phase ^= 1u << b;
+                inflight &= ~(1u << b);
+            }
+            // cells the copy brought past the span (fewer than L) must read as 0
+            if (threadIdx.x < rr - r) buf[lead + span + threadIdx.x] = T(0);
+        } else {
+            stage(inx, n, c0, r, span, CH, periodic, buf + lead);
+            for (int e = lead + span + threadIdx.x; e < be; e += WT) buf[e] = T(0);
+        }
+        if (__syncthreads_or(!ok)) break;
+
+        const T *s = buf + lead;
+        const int base = threadIdx.x * V;
+        T acc[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = T(0);
+        for (int j0 = 0; j0 < nwp; j0 += V) {
+            T w[V], x[2 * V - 1];
+#pragma unroll
+            for (int u = 0; u < V; ++u) w[u] = ws[j0 + u];
+#pragma unroll
+            for (int q = 0; q < 2 * V - 1; ++q) x[q] = s[base + j0 + q];
+#pragma unroll
+            for (int u = 0; u < V; ++u)
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc[v] = fma(w[u], x[v + u], acc[v]);
+        }
+        // results through shared memory (the staged cells are no longer needed), then
+        // coalesced 16-byte stores of the chunk and scalar stores of its periodic images
+        __syncthreads();
+#pragma unroll
+        for (int v = 0; v < V; ++v) buf[base + v] = acc[v];
+        __syncthreads();
+        using VT = typename V16<T>::type;
+        if (c0 + CH <= n) {
+            for (int q = threadIdx.x; q < CH / L; q += WT) {
+                VT x;
+                T *e = reinterpret_cast<T *>(&x);
+#pragma unroll
+                for (int u = 0; u < L; ++u) e[u] = buf[q * L + u];
+                reinterpret_cast<VT *>(outx + c0)[q] = x;
+            }
+        } else {
+            for (int q = threadIdx.x; q < CH && c0 + q < n; q += WT) outx[c0 + q] = buf[q];
+        }
+        if (images && (c0 < r || c0 + CH > n - r))
+            for (int q = threadIdx.x; q < CH; q += WT) {
+                const int64_t p = c0 + q;
+                if (p >= n) break;
+                if (p < r) outx[p + n] = buf[q];
+                if (p >= n - r) outx[p - n] = buf[q];
+            }
+        // buffer b is refilled (chunk k + 2) only after every thread is done with it
+        fence_proxy_async();
+        __syncthreads();
     }
-    if (images)
-        for (int q = threadIdx.x; q < CH; q += WT) {
-            const int64_t p = c0 + q;
-            if (p >= n) break;
-            if (p < r) outx[p + n] = s[q];
-            if (p >= n - r) outx[p - n] = s[q];
-        }
+    if (!ok && threadIdx.x == 0) {
+        atomicOr(err, ERR_TIMEOUT);
+        for (int b = 0; b < 2; ++b)  // drain a copy still in flight before the CTA exits
+            if (inflight & (1u << b)) (void)mbar_wait_bounded(&full[b], (phase >> b) & 1u, 100000000ull);
+    }
 }
 
 template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return b > a ? b : a; }
@@ -169,68 +245,130 @@ template <> struct MaxKey<double> {
     }
 };
 
+// Max filter, persistent like the cross-correlation: two staging buffers (chunk k + 1 arrives by
+// bulk copy while chunk k is reduced) and one work buffer for the doubling passes, which
+// ping-pong between the chunk's staging buffer and the work buffer.
+template <typename T> struct MaxBuf {
+    static constexpr int L = 16 / (int)sizeof(T);
+    static __host__ __device__ int rr(int r) { return (r + L - 1) / L * L; }
+    static __host__ __device__ int elems(int r) { return (MF_CHUNK + 2 * rr(r) + L - 1) / L * L; }
+};
+
 template <typename T>
 __global__ void __launch_bounds__(WT)
-maxfilter_kernel(const T *__restrict__ in, T *__restrict__ out, Geom geo, int r, int periodic, int images) {
+maxfilter_kernel(const T *__restrict__ in, T *__restrict__ out, Geom geo, int r, int periodic, int images,
+                 unsigned *err) {
     using MK = MaxKey<T>;
     using K = typename MK::K;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int span = MF_CHUNK + 2 * r;
-    T *st = reinterpret_cast<T *>(smem_raw);
-    K *a = reinterpret_cast<K *>(smem_raw);
-    K *b = a + span;
+    static_assert(sizeof(K) == sizeof(T), "keys are converted in place");
+    using B = MaxBuf<T>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full[2];
+    const int span = MF_CHUNK + 2 * r, rr = B::rr(r), lead = rr - r, be = B::elems(r);
+    T *buf0 = reinterpret_cast<T *>(smem_raw);  // staging 0, staging 1, work
     const int64_t n = geo.n[0];
-    const int64_t c0 = (int64_t)blockIdx.x * MF_CHUNK;
     const T *inx = in + geo.off[0];
     T *outx = out + geo.off[0];
-    stage(inx, n, c0, r, span, MF_CHUNK, periodic, st);
-    __syncthreads();
-    for (int i = threadIdx.x; i < span; i += WT) a[i] = MK::to(st[i]);  // same size: in place
-    __syncthreads();
+    const int64_t nchunks = (n + MF_CHUNK - 1) / MF_CHUNK;
+    const uint32_t bytes = (uint32_t)((MF_CHUNK + 2 * rr) * sizeof(T));
     const int w = 2 * r + 1;
-    int len = 1;  // a[i] = max of the `len` cells starting at i, for i <= span - len
-    while (2 * len <= w) {
-        for (int i = threadIdx.x; i <= span - 2 * len; i += WT) b[i] = tmax(a[i], a[i + len]);
-        __syncthreads();
-        K *t = a;
-        a = b;
-        b = t;
-        len *= 2;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_fence_init();
     }
-    for (int i = threadIdx.x; i < MF_CHUNK; i += WT) {
-        const int64_t p = c0 + i;
-        if (p < n) put1(outx, n, r, images, p, MK::from(tmax(a[i], a[i + w - len])));
+    __syncthreads();
+    auto issue = [&](int64_t c, int b) {
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&full[b], bytes);
+        bulk_load_1d(buf0 + b * be, inx + c * MF_CHUNK - rr, bytes, &full[b]);
+    };
+    uint32_t phase = 0u, inflight = 0u;  // per staging buffer, as in xcorr_wide_kernel
+    int64_t c = blockIdx.x;
+    if (c < nchunks && wide_bulk_ok(c * MF_CHUNK, n, MF_CHUNK, rr)) {
+        if (threadIdx.x == 0) issue(c, 0);
+        inflight |= 1u;
+    }
+    bool ok = true;
+    for (int k = 0; c < nchunks; ++k, c += gridDim.x) {
+        const int bsel = k & 1;
+        T *st = buf0 + bsel * be + lead;
+        const int64_t c0 = c * MF_CHUNK;
+        const int64_t cn = c + gridDim.x;
+        if (cn < nchunks && wide_bulk_ok(cn * MF_CHUNK, n, MF_CHUNK, rr)) {
+            if (threadIdx.x == 0) issue(cn, bsel ^ 1);
+            inflight |= 2u >> bsel;
+        }
+        if (inflight & (1u << bsel)) {
+            ok = mbar_wait_bounded(&full[bsel], (phase >> bsel) & 1u);
+            if (ok) {
+                phase ^= 1u << bsel;
+                inflight &= ~(1u << bsel);
+            }
+        } else {
+            stage(inx, n, c0, r, span, MF_CHUNK, periodic, st);
+        }
+        if (__syncthreads_or(!ok)) break;
+        K *a = reinterpret_cast<K *>(st);
+        K *bw = reinterpret_cast<K *>(buf0 + 2 * be + lead);
+        for (int i = threadIdx.x; i < span; i += WT) a[i] = MK::to(st[i]);  // same size: in place
+        __syncthreads();
+        int len = 1;  // a[i] = max of the `len` cells starting at i, for i <= span - len
+        while (2 * len <= w) {
+            for (int i = threadIdx.x; i <= span - 2 * len; i += WT) bw[i] = tmax(a[i], a[i + len]);
+            __syncthreads();
+            K *t = a;
+            a = bw;
+            bw = t;
+            len *= 2;
+        }
+        for (int i = threadIdx.x; i < MF_CHUNK; i += WT) {
+            const int64_t p = c0 + i;
+            if (p < n) put1(outx, n, r, images, p, MK::from(tmax(a[i], a[i + w - len])));
+        }
+        fence_proxy_async();
+        __syncthreads();
+    }
+    if (!ok && threadIdx.x == 0) {
+        atomicOr(err, ERR_TIMEOUT);
+        for (int q = 0; q < 2; ++q)
+            if (inflight & (1u << q)) (void)mbar_wait_bounded(&full[q], (phase >> q) & 1u, 100000000ull);
     }
 }
 
 template <typename T>
 cudaError_t run_wide(const void *in, void *out, const Geom &g, const void *wdev, int r, bool periodic, bool images,
-                     cudaStream_t s) {
-    constexpr int V = Wide<T>::V;
-    const int nwp = (2 * r + 1 + V - 1) / V * V;
-    const size_t smem = sizeof(T) * ((size_t)nwp + WT * V + nwp + V);
+                     unsigned *err, cudaStream_t s) {
+    using B = WideBuf<T>;
+    const size_t smem = sizeof(T) * ((size_t)B::wlen(r) + 2 * (size_t)B::elems(r));
     auto k = xcorr_wide_kernel<T>;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    const unsigned blocks = (unsigned)((g.n[0] + WT * V - 1) / (WT * V));
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, WT, smem);
+    if (e != cudaSuccess) return e;
+    const long chunks = (long)((g.n[0] + B::CH - 1) / B::CH);
+    const unsigned blocks = (unsigned)std::max(1L, std::min(chunks, (long)std::max(occ, 1) * device_sms()));
     k<<<blocks, WT, smem, s>>>(static_cast<const T *>(in), static_cast<T *>(out), g, static_cast<const T *>(wdev), r,
-                               periodic ? 1 : 0, images ? 1 : 0);
+                               periodic ? 1 : 0, images ? 1 : 0, err);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t run_maxf(const void *in, void *out, const Geom &g, int r, bool periodic, bool images, cudaStream_t s) {
-    const size_t smem = 2 * sizeof(T) * ((size_t)MF_CHUNK + 2 * r);
+cudaError_t run_maxf(const void *in, void *out, const Geom &g, int r, bool periodic, bool images, unsigned *err,
+                     cudaStream_t s) {
+    const size_t smem = 3 * sizeof(T) * (size_t)MaxBuf<T>::elems(r);
     auto k = maxfilter_kernel<T>;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    const unsigned blocks = (unsigned)((g.n[0] + MF_CHUNK - 1) / MF_CHUNK);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, WT, smem);
+    if (e != cudaSuccess) return e;
+    const long chunks = (long)((g.n[0] + MF_CHUNK - 1) / MF_CHUNK);
+    const unsigned blocks = (unsigned)std::max(1L, std::min(chunks, (long)std::max(occ, 1) * device_sms()));
     k<<<blocks, WT, smem, s>>>(static_cast<const T *>(in), static_cast<T *>(out), g, r, periodic ? 1 : 0,
-                               images ? 1 : 0);
+                               images ? 1 : 0, err);
     return cudaGetLastError();
 }
 
@@ -239,20 +377,20 @@ cudaError_t run_maxf(const void *in, void *out, const Geom &g, int r, bool perio
 int xcorr_wide_max_radius() { return 1024; }
 
 cudaError_t launch_xcorr_wide(int dtype, int r, const void *in, void *out, const Geom &g, const void *wdev,
-                              bool periodic, bool images, cudaStream_t s) {
+                              bool periodic, bool images, unsigned *err, cudaStream_t s) {
     if (r < 0 || r > xcorr_wide_max_radius()) return cudaErrorInvalidValue;
-    if (dtype == 1) return run_wide<double>(in, out, g, wdev, r, periodic, images, s);
-    if (dtype == 2) return run_wide<float>(in, out, g, wdev, r, periodic, images, s);
+    if (dtype == 1) return run_wide<double>(in, out, g, wdev, r, periodic, images, err, s);
+    if (dtype == 2) return run_wide<float>(in, out, g, wdev, r, periodic, images, err, s);
     return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_maxfilter(int dtype, int r, const void *in, void *out, const Geom &g, bool periodic, bool images,
-                             cudaStream_t s) {
+                             unsigned *err, cudaStream_t s) {
     if (r < 0 || r > xcorr_wide_max_radius()) return cudaErrorInvalidValue;
     switch (dtype) {
-    case 0: return run_maxf<int32_t>(in, out, g, r, periodic, images, s);
-    case 1: return run_maxf<double>(in, out, g, r, periodic, images, s);
-    case 2: return run_maxf<float>(in, out, g, r, periodic, images, s);
+    case 0: return run_maxf<int32_t>(in, out, g, r, periodic, images, err, s);
+    case 1: return run_maxf<double>(in, out, g, r, periodic, images, err, s);
+    case 2: return run_maxf<float>(in, out, g, r, periodic, images, err, s);
     default: return cudaErrorInvalidValue;
     }
 }
