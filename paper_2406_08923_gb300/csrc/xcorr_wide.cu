@@ -102,6 +102,50 @@ __device__ __forceinline__ bool wide_bulk_ok(int64_t c0, int64_t n, int ch, int 
     return c0 - rr >= 0 && c0 + ch + rr <= n;
 }
 
+constexpr int MAX_NBUF = 3;
+
+// Bulk-copy pipeline over the chunks of a persistent CTA.  The CTA's k-th chunk (global chunk
+// blockIdx.x + k gridDim.x) is staged in buffer k % nbuf, and copies run nbuf - 1 chunks ahead:
+// thread 0 issues one cp.async.bulk per chunk, completion on the buffer's mbarrier.  The state
+// (bit b of `phase`: parity of buffer b's next completion; bit b of `inflight`: a copy into
+// buffer b is outstanding) is kept identically by every thread.
+template <typename T> struct ChunkPipe {
+    uint64_t *full;
+    T *buf0;
+    int be, ch, rr, nbuf;
+    const T *inx;
+    int64_t n, nchunks;
+    uint32_t bytes, phase, inflight;
+
+    __device__ bool bulk_ok(int64_t c) const { return c < nchunks && wide_bulk_ok(c * ch, n, ch, rr); }
+    __device__ T *buf(int b) const { return buf0 + (size_t)b * be; }
+    // chunk c into buffer b (a no-op for chunks that are staged by `stage` instead)
+    __device__ void issue(int64_t c, int b) {
+        if (!bulk_ok(c)) return;
+        if (threadIdx.x == 0) {
+            fence_proxy_async();
+            mbar_arrive_expect_tx(&full[b], bytes);
+            bulk_load_1d(buf(b), inx + c * ch - rr, bytes, &full[b]);
+        }
+        inflight |= 1u << b;
+    }
+    // Wait for buffer b's copy if one is outstanding; `*bulk` says whether there was one.
+    // Returns false if the bounded wait expired.
+    __device__ bool wait(int b, bool *bulk) {
+        *bulk = (inflight >> b) & 1u;
+        if (!*bulk) return true;
+        if (!mbar_wait_bounded(&full[b], (phase >> b) & 1u)) return false;
+        phase ^= 1u << b;
+        inflight &= ~(1u << b);
+        return true;
+    }
+    // thread 0, after a timeout: wait (bounded) for copies still in flight before the CTA exits
+    __device__ void drain() {
+        for (int b = 0; b < nbuf; ++b)
+            if ((inflight >> b) & 1u) (void)mbar_wait_bounded(&full[b], (phase >> b) & 1u, 100000000ull);
+    }
+};
+
 // Persistent kernel: CTA b handles chunks b, b + G, b + 2G, ... (G = gridDim.x) with two
 // staging buffers.  While it computes chunk k, the bulk copy of chunk k + 1 (issued by thread 0,
 // completion on one mbarrier per buffer) is in flight, so the load latency of a chunk overlaps
@@ -110,64 +154,45 @@ __device__ __forceinline__ bool wide_bulk_ok(int64_t c0, int64_t n, int ch, int 
 template <typename T>
 __global__ void __launch_bounds__(WT)
 xcorr_wide_kernel(const T *__restrict__ in, T *__restrict__ out, Geom geo, const T *__restrict__ wg, int r,
-                  int periodic, int images, unsigned *err) {
+                  int periodic, int images, int nbuf, unsigned *err) {
     using B = WideBuf<T>;
     constexpr int V = B::V, CH = B::CH, L = B::L;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t full[2];
+    __shared__ __align__(8) uint64_t full[MAX_NBUF];
     const int nw = 2 * r + 1, nwp = B::nwp(r), rr = B::rr(r), lead = rr - r, be = B::elems(r);
     T *ws = reinterpret_cast<T *>(smem_raw);
-    T *buf0 = ws + B::wlen(r);
     const int64_t n = geo.n[0];
-    const T *inx = in + geo.off[0];
     T *outx = out + geo.off[0];
-    const int64_t nchunks = (n + CH - 1) / CH;
-    const uint32_t bytes = (uint32_t)((CH + 2 * rr) * sizeof(T));
+    ChunkPipe<T> pp{full, ws + B::wlen(r), be, CH, rr, nbuf, in + geo.off[0], n, (n + CH - 1) / CH,
+                    (uint32_t)((CH + 2 * rr) * sizeof(T)), 0u, 0u};
 
     if (threadIdx.x == 0) {
-        mbar_init(&full[0], 1);
-        mbar_init(&full[1], 1);
+        for (int b = 0; b < nbuf; ++b) mbar_init(&full[b], 1);
         mbar_fence_init();
     }
     for (int j = threadIdx.x; j < nwp; j += WT) ws[j] = j < nw ? wg[j] : T(0);
-    for (int e = threadIdx.x; e < 2 * be; e += WT) buf0[e] = T(0);
+    for (int e = threadIdx.x; e < nbuf * be; e += WT) pp.buf0[e] = T(0);
     fence_proxy_async();  // the zero fill precedes the bulk copies into the same buffers
     __syncthreads();
 
-    auto issue = [&](int64_t c, int b) {  // thread 0: bulk copy of chunk c into buffer b
-        fence_proxy_async();
-        mbar_arrive_expect_tx(&full[b], bytes);
-        bulk_load_1d(buf0 + b * be, inx + c * CH - rr, bytes, &full[b]);
-    };
-    // per buffer b: bit b of `phase` is the mbarrier parity of its next copy, bit b of
-    // `inflight` says that a copy into it is outstanding (uniform across the CTA)
-    uint32_t phase = 0u, inflight = 0u;
+    const int64_t G = gridDim.x;
     int64_t c = blockIdx.x;
-    if (c < nchunks && wide_bulk_ok(c * CH, n, CH, rr)) {
-        if (threadIdx.x == 0) issue(c, 0);
-        inflight |= 1u;
-    }
+    for (int j = 0; j < nbuf - 1; ++j) pp.issue(c + j * G, j);
     bool ok = true;
-    for (int k = 0; c < nchunks; ++k, c += gridDim.x) {
-        const int b = k & 1;
-        T *buf = buf0 + b * be;
+    for (int k = 0; c < pp.nchunks; ++k, c += G) {
+        const int b = k % nbuf;
+        T *buf = pp.buf(b);
         const int64_t c0 = c * CH;
-        const int64_t cn = c + gridDim.x;  // prefetch the next chunk into the other buffer
-        if (cn < nchunks && wide_bulk_ok(cn * CH, n, CH, rr)) {
-            if (threadIdx.x == 0) issue(cn, b ^ 1);
-            inflight |= 2u >> b;
-        }
+        // the buffer of chunk k + nbuf - 1 last held chunk k - 1, finished at the loop's barrier
+        pp.issue(c + (nbuf - 1) * G, (k + nbuf - 1) % nbuf);
         const int span = CH + 2 * r;
-        if (inflight & (1u << b)) {
-            ok = mbar_wait_bounded(&full[b], (phase >> b) & 1u);
-            if (ok) {
-                phase ^= 1u << b;
-                inflight &= ~(1u << b);
-            }
+        bool bulk;
+        ok = pp.wait(b, &bulk);
+        if (ok && bulk) {
             // cells the copy brought past the span (fewer than L) must read as 0
             if (threadIdx.x < rr - r) buf[lead + span + threadIdx.x] = T(0);
-        } else {
-            stage(inx, n, c0, r, span, CH, periodic, buf + lead);
+        } else if (ok) {
+            stage(pp.inx, n, c0, r, span, CH, periodic, buf + lead);
             for (int e = lead + span + threadIdx.x; e < be; e += WT) buf[e] = T(0);
         }
         if (__syncthreads_or(!ok)) break;
@@ -213,14 +238,13 @@ xcorr_wide_kernel(const T *__restrict__ in, T *__restrict__ out, Geom geo, const
                 if (p < r) outx[p + n] = buf[q];
                 if (p >= n - r) outx[p - n] = buf[q];
             }
-        // buffer b is refilled (chunk k + 2) only after every thread is done with it
+        // buffer b is refilled (chunk k + nbuf) only after every thread is done with it
         fence_proxy_async();
         __syncthreads();
     }
     if (!ok && threadIdx.x == 0) {
         atomicOr(err, ERR_TIMEOUT);
-        for (int b = 0; b < 2; ++b)  // drain a copy still in flight before the CTA exits
-            if (inflight & (1u << b)) (void)mbar_wait_bounded(&full[b], (phase >> b) & 1u, 100000000ull);
+        pp.drain();
     }
 }
 
@@ -257,61 +281,41 @@ template <typename T> struct MaxBuf {
 template <typename T>
 __global__ void __launch_bounds__(WT)
 maxfilter_kernel(const T *__restrict__ in, T *__restrict__ out, Geom geo, int r, int periodic, int images,
-                 unsigned *err) {
+                 int nbuf, unsigned *err) {
     using MK = MaxKey<T>;
     using K = typename MK::K;
     static_assert(sizeof(K) == sizeof(T), "keys are converted in place");
     using B = MaxBuf<T>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t full[2];
+    __shared__ __align__(8) uint64_t full[MAX_NBUF];
     const int span = MF_CHUNK + 2 * r, rr = B::rr(r), lead = rr - r, be = B::elems(r);
-    T *buf0 = reinterpret_cast<T *>(smem_raw);  // staging 0, staging 1, work
     const int64_t n = geo.n[0];
-    const T *inx = in + geo.off[0];
     T *outx = out + geo.off[0];
-    const int64_t nchunks = (n + MF_CHUNK - 1) / MF_CHUNK;
-    const uint32_t bytes = (uint32_t)((MF_CHUNK + 2 * rr) * sizeof(T));
+    // buffers 0 .. nbuf-1 stage chunks; buffer nbuf is the work buffer of the doubling passes
+    ChunkPipe<T> pp{full, reinterpret_cast<T *>(smem_raw), be, MF_CHUNK, rr, nbuf, in + geo.off[0], n,
+                    (n + MF_CHUNK - 1) / MF_CHUNK, (uint32_t)((MF_CHUNK + 2 * rr) * sizeof(T)), 0u, 0u};
     const int w = 2 * r + 1;
 
     if (threadIdx.x == 0) {
-        mbar_init(&full[0], 1);
-        mbar_init(&full[1], 1);
+        for (int b = 0; b < nbuf; ++b) mbar_init(&full[b], 1);
         mbar_fence_init();
     }
     __syncthreads();
-    auto issue = [&](int64_t c, int b) {
-        fence_proxy_async();
-        mbar_arrive_expect_tx(&full[b], bytes);
-        bulk_load_1d(buf0 + b * be, inx + c * MF_CHUNK - rr, bytes, &full[b]);
-    };
-    uint32_t phase = 0u, inflight = 0u;  // per staging buffer, as in xcorr_wide_kernel
+    const int64_t G = gridDim.x;
     int64_t c = blockIdx.x;
-    if (c < nchunks && wide_bulk_ok(c * MF_CHUNK, n, MF_CHUNK, rr)) {
-        if (threadIdx.x == 0) issue(c, 0);
-        inflight |= 1u;
-    }
+    for (int j = 0; j < nbuf - 1; ++j) pp.issue(c + j * G, j);
     bool ok = true;
-    for (int k = 0; c < nchunks; ++k, c += gridDim.x) {
-        const int bsel = k & 1;
-        T *st = buf0 + bsel * be + lead;
+    for (int k = 0; c < pp.nchunks; ++k, c += G) {
+        const int b = k % nbuf;
+        T *st = pp.buf(b) + lead;
         const int64_t c0 = c * MF_CHUNK;
-        const int64_t cn = c + gridDim.x;
-        if (cn < nchunks && wide_bulk_ok(cn * MF_CHUNK, n, MF_CHUNK, rr)) {
-            if (threadIdx.x == 0) issue(cn, bsel ^ 1);
-            inflight |= 2u >> bsel;
-        }
-        if (inflight & (1u << bsel)) {
-            ok = mbar_wait_bounded(&full[bsel], (phase >> bsel) & 1u);
-            if (ok) {
-                phase ^= 1u << bsel;
-                inflight &= ~(1u << bsel);
-            }
-        } else {
-            stage(inx, n, c0, r, span, MF_CHUNK, periodic, st);
-        }
+        pp.issue(c + (nbuf - 1) * G, (k + nbuf - 1) % nbuf);
+        bool bulk;
+        ok = pp.wait(b, &bulk);
+        if (ok && !bulk) stage(pp.inx, n, c0, r, span, MF_CHUNK, periodic, st);
         if (__syncthreads_or(!ok)) break;
         K *a = reinterpret_cast<K *>(st);
-        K *bw = reinterpret_cast<K *>(buf0 + 2 * be + lead);
+        K *bw = reinterpret_cast<K *>(pp.buf(nbuf) + lead);
         for (int i = threadIdx.x; i < span; i += WT) a[i] = MK::to(st[i]);  // same size: in place
         __syncthreads();
         int len = 1;  // a[i] = max of the `len` cells starting at i, for i <= span - len
@@ -332,33 +336,57 @@ maxfilter_kernel(const T *__restrict__ in, T *__restrict__ out, Geom geo, int r,
     }
     if (!ok && threadIdx.x == 0) {
         atomicOr(err, ERR_TIMEOUT);
-        for (int q = 0; q < 2; ++q)
-            if (inflight & (1u << q)) (void)mbar_wait_bounded(&full[q], (phase >> q) & 1u, 100000000ull);
+        pp.drain();
     }
 }
+
+// Pipeline depth of the max filter.  Its doubling passes are bound by shared memory, and
+// measured depths 1-3 at radius 8..1024 (FP32 and FP64) favour occupancy over prefetch: one
+// staging buffer (the chunk's own copy, then its passes), except at radius 0, a plain copy,
+// where prefetching the next chunk wins.
+inline int maxf_nbuf(int r) { return r == 0 ? 2 : 1; }
 
 template <typename T>
 cudaError_t run_wide(const void *in, void *out, const Geom &g, const void *wdev, int r, bool periodic, bool images,
                      unsigned *err, cudaStream_t s) {
     using B = WideBuf<T>;
-    const size_t smem = sizeof(T) * ((size_t)B::wlen(r) + 2 * (size_t)B::elems(r));
     auto k = xcorr_wide_kernel<T>;
+    // two staging buffers (prefetch) unless the second one costs resident CTAs; the choice
+    // and the occupancy are computed once per radius
+    static int choice[1025][2];  // {nbuf, resident CTAs per SM}, 0 = not yet computed
+    if (!choice[r][0]) {
+        int nbuf = 0, occ = 0;
+        for (int nb = 2; nb >= 1; --nb) {
+            const size_t sm = sizeof(T) * ((size_t)B::wlen(r) + (size_t)nb * B::elems(r));
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
+            int o = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, WT, sm);
+            if (e != cudaSuccess) return e;
+            if (nbuf == 0 || o > occ) {
+                nbuf = nb;
+                occ = o;
+            }
+        }
+        choice[r][1] = occ;
+        choice[r][0] = nbuf;
+    }
+    const int nbuf = choice[r][0], occ = choice[r][1];
+    const size_t smem = sizeof(T) * ((size_t)B::wlen(r) + (size_t)nbuf * B::elems(r));
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, WT, smem);
     if (e != cudaSuccess) return e;
     const long chunks = (long)((g.n[0] + B::CH - 1) / B::CH);
     const unsigned blocks = (unsigned)std::max(1L, std::min(chunks, (long)std::max(occ, 1) * device_sms()));
     k<<<blocks, WT, smem, s>>>(static_cast<const T *>(in), static_cast<T *>(out), g, static_cast<const T *>(wdev), r,
-                               periodic ? 1 : 0, images ? 1 : 0, err);
+                               periodic ? 1 : 0, images ? 1 : 0, nbuf, err);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t run_maxf(const void *in, void *out, const Geom &g, int r, bool periodic, bool images, unsigned *err,
                      cudaStream_t s) {
-    const size_t smem = 3 * sizeof(T) * (size_t)MaxBuf<T>::elems(r);
+    const int nbuf = maxf_nbuf(r);
+    const size_t smem = (size_t)(nbuf + 1) * sizeof(T) * (size_t)MaxBuf<T>::elems(r);
     auto k = maxfilter_kernel<T>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -368,7 +396,7 @@ cudaError_t run_maxf(const void *in, void *out, const Geom &g, int r, bool perio
     const long chunks = (long)((g.n[0] + MF_CHUNK - 1) / MF_CHUNK);
     const unsigned blocks = (unsigned)std::max(1L, std::min(chunks, (long)std::max(occ, 1) * device_sms()));
     k<<<blocks, WT, smem, s>>>(static_cast<const T *>(in), static_cast<T *>(out), g, r, periodic ? 1 : 0,
-                               images ? 1 : 0, err);
+                               images ? 1 : 0, nbuf, err);
     return cudaGetLastError();
 }
 
