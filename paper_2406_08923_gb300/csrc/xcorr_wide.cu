@@ -26,9 +26,6 @@
 namespace stn {
 namespace {
 
-template <typename T> struct Wide;
-template <> struct Wide<float> { static constexpr int V = 15; };
-template <> struct Wide<double> { static constexpr int V = 7; };
 constexpr int WT = 256;                // threads per CTA
 constexpr int MF_CHUNK = 4096;         // max-filter outputs per CTA
 
@@ -87,8 +84,8 @@ __device__ __forceinline__ void put1(T *outx, int64_t n, int r, int images, int6
 // c0 - r .. c0 + CH + r - 1 start at element `lead` = rr - r, where rr is r rounded up to whole
 // 16-byte groups, so that a bulk copy of cells c0 - rr .. c0 + CH + rr - 1 lands at element 0.
 // Past the span come zeros for the padded weight blocks.
-template <typename T> struct WideBuf {
-    static constexpr int V = Wide<T>::V, CH = WT * V, L = 16 / (int)sizeof(T);
+template <typename T, int V_> struct WideBuf {
+    static constexpr int V = V_, CH = WT * V, L = 16 / (int)sizeof(T);
     static __host__ __device__ int rr(int r) { return (r + L - 1) / L * L; }
     static __host__ __device__ int nwp(int r) { return (2 * r + 1 + V - 1) / V * V; }
     // elements per buffer (a multiple of L, so every buffer starts 16-byte aligned)
@@ -151,11 +148,11 @@ template <typename T> struct ChunkPipe {
 // completion on one mbarrier per buffer) is in flight, so the load latency of a chunk overlaps
 // the previous chunk's multiply-adds and stores.  Bounded waits: on expiry the CTA records
 // ERR_TIMEOUT, waits (bounded) for its copy in flight and returns.
-template <typename T>
+template <typename T, int V_>
 __global__ void __launch_bounds__(WT)
 xcorr_wide_kernel(const T *__restrict__ in, T *__restrict__ out, Geom geo, const T *__restrict__ wg, int r,
                   int periodic, int images, int nbuf, unsigned *err) {
-    using B = WideBuf<T>;
+    using B = WideBuf<T, V_>;
     constexpr int V = B::V, CH = B::CH, L = B::L;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full[MAX_NBUF];
@@ -346,11 +343,11 @@ maxfilter_kernel(const T *__restrict__ in, T *__restrict__ out, Geom geo, int r,
 // where prefetching the next chunk wins.
 inline int maxf_nbuf(int r) { return r == 0 ? 2 : 1; }
 
-template <typename T>
+template <typename T, int V>
 cudaError_t run_wide(const void *in, void *out, const Geom &g, const void *wdev, int r, bool periodic, bool images,
                      unsigned *err, cudaStream_t s) {
-    using B = WideBuf<T>;
-    auto k = xcorr_wide_kernel<T>;
+    using B = WideBuf<T, V>;
+    auto k = xcorr_wide_kernel<T, V>;
     // two staging buffers (prefetch) unless the second one costs resident CTAs; the choice
     // and the occupancy are computed once per radius
     static int choice[1025][2];  // {nbuf, resident CTAs per SM}, 0 = not yet computed
@@ -382,6 +379,30 @@ cudaError_t run_wide(const void *in, void *out, const Geom &g, const void *wdev,
     return cudaGetLastError();
 }
 
+// Outputs per thread V (= weights per register block): the 2r+1 weights are padded to whole
+// blocks of V, so V is chosen per radius from a few compiled sizes (all odd: lanes V cells
+// apart fall on distinct banks).  A block costs V^2 multiply-adds, about 3V shared loads and
+// some address arithmetic for V outputs.  FP32 is issue-bound: the cost per output is blocks
+// x (V + 6), the 6 fitted to radius sweeps on GB300 (at r = 64 and 128, V = 15 beats V = 13
+// although it pads more).  FP64 is bound by the FP64 pipe, where a shared load weighs about a
+// tenth of a multiply-add: blocks x (V + 0.3), in tenths.  Ties go to the larger V.
+template <typename T> int wide_block(int r, const int *vs, int nv) {
+    const int nw = 2 * r + 1;
+    int best = vs[0];
+    long best_cost = -1;
+    for (int i = 0; i < nv; ++i) {
+        const int v = vs[i], blocks = (nw + v - 1) / v;
+        const long cost = sizeof(T) == 8 ? (long)blocks * (10 * v + 3) : (long)blocks * (v + 6);
+        if (best_cost < 0 || cost < best_cost || (cost == best_cost && v > best)) {
+            best = v;
+            best_cost = cost;
+        }
+    }
+    return best;
+}
+constexpr int WIDE_V_F32[] = {9, 11, 13, 15};
+constexpr int WIDE_V_F64[] = {5, 7, 9};
+
 template <typename T>
 cudaError_t run_maxf(const void *in, void *out, const Geom &g, int r, bool periodic, bool images, unsigned *err,
                      cudaStream_t s) {
@@ -407,8 +428,21 @@ int xcorr_wide_max_radius() { return 1024; }
 cudaError_t launch_xcorr_wide(int dtype, int r, const void *in, void *out, const Geom &g, const void *wdev,
                               bool periodic, bool images, unsigned *err, cudaStream_t s) {
     if (r < 0 || r > xcorr_wide_max_radius()) return cudaErrorInvalidValue;
-    if (dtype == 1) return run_wide<double>(in, out, g, wdev, r, periodic, images, err, s);
-    if (dtype == 2) return run_wide<float>(in, out, g, wdev, r, periodic, images, err, s);
+    if (dtype == 1) {
+        switch (wide_block<double>(r, WIDE_V_F64, 3)) {
+        case 5: return run_wide<double, 5>(in, out, g, wdev, r, periodic, images, err, s);
+        case 9: return run_wide<double, 9>(in, out, g, wdev, r, periodic, images, err, s);
+        default: return run_wide<double, 7>(in, out, g, wdev, r, periodic, images, err, s);
+        }
+    }
+    if (dtype == 2) {
+        switch (wide_block<float>(r, WIDE_V_F32, 4)) {
+        case 9: return run_wide<float, 9>(in, out, g, wdev, r, periodic, images, err, s);
+        case 11: return run_wide<float, 11>(in, out, g, wdev, r, periodic, images, err, s);
+        case 13: return run_wide<float, 13>(in, out, g, wdev, r, periodic, images, err, s);
+        default: return run_wide<float, 15>(in, out, g, wdev, r, periodic, images, err, s);
+        }
+    }
     return cudaErrorInvalidValue;
 }
 

@@ -35,8 +35,10 @@ def _weights(r, signed):
 
 
 @pytest.mark.parametrize("storage", [L.STENCIL_F64, L.STENCIL_F32])
-@pytest.mark.parametrize("r,n,sweeps", [(5, 3001, 1), (16, 70001, 3), (100, 4097, 2), (1024, 5000, 1),
-                                        (1024, (1 << 20) + 3, 2)])
+# radii cover every compiled register-block size V (FP32 9/11/13/15, FP64 5/7/9), and the
+# sizes both the bulk-copied interior chunks and the staged edge chunks
+@pytest.mark.parametrize("r,n,sweeps", [(5, 3001, 1), (8, 20001, 2), (16, 70001, 3), (32, 50003, 1), (100, 4097, 2),
+                                        (128, 300007, 1), (1024, 5000, 1), (1024, (1 << 20) + 3, 2)])
 def test_wide_xcorr_matches_oracle(cuda_lib, storage, r, n, sweeps):
     signed = storage == L.STENCIL_F64  # FP32 sums of 2r+1 terms: keep them well conditioned
     g = _weights(r, signed)
