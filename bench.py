@@ -279,7 +279,8 @@ def run_radius_sweep(L, synth, stream, hbm_peak):
     (Sec. 5.3, Figs. 10-11): 2^24 cells per problem (64 MiB FP32 / 128 MiB FP64, the paper's
     sizes): 2^24 in 1D, 4096^2 in 2D, 256^3 in 3D.  Time per Euler step and its fraction of
     HBM bandwidth at one read and one write per cell-step (1D runs up to 16 steps per launch in
-    shared memory, so its traffic is lower than that)."""
+    shared memory and 2D FP32 up to 4 when the autotuner picks temporal blocking, so their
+    traffic is lower than that)."""
     out = {}
     shapes = {1: (1 << 24,), 2: (4096, 4096), 3: (256, 256, 256)}
     steps = {1: 64, 2: 20, 3: 20}
@@ -292,7 +293,8 @@ def run_radius_sweep(L, synth, stream, hbm_peak):
                            params=L.heat_params(shape))
                 a, b = p.alloc(), p.alloc()
                 p.upload(a, [base])
-                if ndim == 3 and r == 3:
+                if (ndim == 3 and r == 3) or (ndim == 2 and st == L.STENCIL_F32):
+                    # 2D FP32: the tile kernel or temporal blocking (2 or 4 steps per pass)
                     p.autotune(a, b, nsteps=4, reps=2, stream=stream)
                 k = steps[ndim]
                 p.step(a, b, k, stream)

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libstencil.so")
-SOURCES = ["api.cu", "halo.cu", "xcorr.cu", "xcorr_wide.cu", "diffusion.cu", "diffusion_f32.cu", "diffusion2d.cu", "mhd.cu", "norms.cu", "batch.cu"]
+SOURCES = ["api.cu", "halo.cu", "xcorr.cu", "xcorr_wide.cu", "diffusion.cu", "diffusion_f32.cu", "diffusion2d.cu", "diffusion2d_tb.cu", "mhd.cu", "norms.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include")]

@@ -508,6 +508,11 @@ static stencil_status run_pass(stencil_t p, void *const *src, void *const *dst, 
            "diffusion (1D) launch");
         return STENCIL_OK;
     }
+    if (p->kind == STENCIL_DIFFUSION && p->ndim == 2 && sweeps > 1) {  // temporally blocked pass
+        CK(p, launch_diffusion2d_tb(storage_code(p->storage), sweeps, src[0], dst[0], g, p->dcoef, s),
+           "diffusion (2D, temporally blocked) launch");
+        return STENCIL_OK;
+    }
     if (p->kind == STENCIL_DIFFUSION) {
         int box[3];
         if (p->ndim == 2) diffusion2d_box(storage_code(p->storage), p->radius, box);
@@ -573,6 +578,16 @@ stencil_status stencil_step(stencil_t p, void *const *fin, void *const *fout, in
             int k = std::min(left, maxs);
             sweeps.push_back(k);
             left -= k;
+        }
+        npass = (int)sweeps.size();
+    } else if (p->kind == STENCIL_DIFFUSION && p->ndim == 2 && p->variant > 0 && periodic &&
+               diffusion2d_tb_ok(storage_code(p->storage), p->geom)) {
+        // temporal blocking: passes of K = 2 or 4 steps, the remainder one step at a time
+        const int k = p->variant == 1 ? 2 : 4;
+        for (int left = nsteps; left > 0;) {
+            const int take = left >= k ? k : 1;
+            sweeps.push_back(take);
+            left -= take;
         }
         npass = (int)sweeps.size();
     } else {
@@ -671,6 +686,7 @@ stencil_status stencil_field_norms(stencil_t p, void *const *fields, double *out
 }
 
 static int num_variants(stencil_t p) {
+    if (p->kind == STENCIL_DIFFUSION && p->ndim == 2) return p->storage == STENCIL_F32 ? 3 : 1;
     if (p->kind == STENCIL_DIFFUSION)
         return p->ndim == 3 ? diffusion_num_variants(storage_code(p->storage), p->radius) : 1;
     if (p->kind == STENCIL_MHD8) return mhd_num_variants(storage_code(p->storage));
@@ -681,7 +697,8 @@ static const char *variant_name(stencil_t p, int v) {
     if (p->kind == STENCIL_MAXFILTER) return "doubling_chunk4096";
     if (p->kind == STENCIL_XCORR && p->radius > 4) return "wide_register_blocked";
     if (p->kind == STENCIL_DIFFUSION && p->ndim == 1) return "xcorr_folded_chunk2048_temporal_blocking";
-    if (p->kind == STENCIL_DIFFUSION && p->ndim == 2) return "tile2d_32vx_by8_ry4";
+    if (p->kind == STENCIL_DIFFUSION && p->ndim == 2)
+        return v == 1 ? "stream2d_tb2" : v == 2 ? "stream2d_tb4" : "tile2d_32vx_by8_ry4";
     if (p->kind == STENCIL_DIFFUSION) return diffusion_variant_name(storage_code(p->storage), p->radius, v);
     if (p->kind == STENCIL_MHD8) return mhd_variant_name(storage_code(p->storage), v);
     return "chunk2048_temporal_blocking";

@@ -78,6 +78,11 @@ cudaError_t launch_diffusion_f32(const CUtensorMap *map_in, float *out, const Ge
 cudaError_t launch_diffusion2d(int dtype, const CUtensorMap *map_in, void *out, const Geom &g, const DiffCoef &c,
                                bool images, unsigned *err, cudaStream_t s);
 void diffusion2d_box(int dtype, int r, int box[3]);
+// 2D, temporally blocked (diffusion2d_tb.cu): `steps` = 2 or 4 Euler steps per pass, FP32,
+// periodic, nx a multiple of 4 (diffusion2d_tb_ok); reads `in` with periodic wrap (no halo).
+bool diffusion2d_tb_ok(int dtype, const Geom &g);
+cudaError_t launch_diffusion2d_tb(int dtype, int steps, const void *in, void *out, const Geom &g, const DiffCoef &c,
+                                  cudaStream_t s);
 
 // MHD8 (Eqs. A1-A4 + RK3).  Constants in the compute type are built inside mhd.cu.
 struct MhdConst {

@@ -104,3 +104,34 @@ def test_caller_filled_halo_one_step(cuda_lib, ndim, r):
     ref = oracle.diffusion_r_box(fhat, r, par.dt, par.alpha, _h(par, ndim), shape)
     assert_close(got, ref, 1e-12, f"caller halo {ndim}D r={r}")
     p.close()
+
+
+@pytest.mark.parametrize("r", [1, 2, 3, 4])
+@pytest.mark.parametrize("shape,steps", [((45, 72), 9), ((37, 12), 5), ((300, 1024), 6)])
+def test_2d_every_variant_matches_oracle(cuda_lib, r, shape, steps):
+    # FP32 2D: the one-step tile kernel and the temporally blocked streaming kernels (2 and 4
+    # steps per pass, the remainder one step at a time).  nx is a multiple of 4 so the blocked
+    # variants run; the shapes overhang a strip (72, 12 < 104 cells), wrap rows more than once
+    # (ny = 37 < 2 K r + chunk) and span several strips and row chunks (1024 x 300).
+    storage = L.STENCIL_F32
+    p = _plan(shape, r, storage)
+    nv = p.variant()[1]
+    assert nv == 3
+    f = _field(shape, storage)
+    par = p.params
+    ref = oracle.diffusion_r(f, r, par.dt, par.alpha, _h(par, 2), steps)
+    ox, oy, _ = p.origin
+    nx, ny, _ = p.dims
+    for v in range(nv):
+        p.set_variant(v)
+        a, b = p.alloc(), p.alloc()
+        p.upload(a, [f])
+        p.step(a, b, steps)
+        p.sync()
+        assert_close(p.download(b)[0], ref, TOL[storage], f"2D r={r} {shape} variant {p.variant()[2]}")
+        full = p.view3(b[0])[0].double().cpu().numpy()
+        box = full[oy - r:oy + ny + r, ox - r:ox + nx + r]
+        want = np.pad(box[r:r + ny, r:r + nx], ((r, r), (r, r)), mode="wrap")
+        np.testing.assert_array_equal(box, want)
+        np.testing.assert_array_equal(p.download(a)[0], f)
+    p.close()
