@@ -74,6 +74,8 @@ def _traffic(case, variant_name):
 # FP64 vector FMA rate of GB300 (nominal 1.25 TFLOP/s dense, recipe table); FP32 from the
 # unit count: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz boost.
 FP64_PEAK_TFLOPS = 1.25
+FP64_PIPE_TINSTR = 2 * 152 * 2.07e9 / 1e12  # FP64 instructions (DFMA, DADD, DMUL alike) per s
+MHD_F64_INSTR, MHD_F64_FLOP = 600, 836      # per cell-substep, ncu sass counts of the MHD kernel
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
@@ -635,10 +637,17 @@ def run_extras(L, synth, stream, hbm_peak, args):
     # config 3: fused 8-field MHD, 256^3 FP64, 20 RK3 steps
     cells = MHD_N ** 3
     res = mhd_job(L, synth, L.STENCIL_F64, MHD_N, MHD_STEPS, w, 1, stream)
+    # FP64 instructions per cell-substep, counted by ncu (sass dadd + dfma + dmul, substep 0 at
+    # 128^3: 600 per cell, 836 flop); the FP64 pipe retires 2 per clock per SM
+    ips = cells * MHD_F64_INSTR / (res["ms_substep"] / 1e3)
     out["mhd8_256_fp64_20steps"] = {
         "ms_per_job": round(res["ms_job"], 3), "ms_per_substep": round(res["ms_substep"], 4),
         "mcell_substep_updates_per_s": round(cells / (res["ms_substep"] / 1e3) / 1e6, 1),
         "variant": res["variant"], "finite": res["finite"], "mass": res["mass"],
+        "roofline": _roof("alu", ips / 1e12, FP64_PIPE_TINSTR, "T FP64 instr/s",
+                          note="600 FP64 instructions (836 flop) per cell-substep, ncu; FP64 pipe peak "
+                               "2 instr/clk/SM x 152 SMs x 2.07 GHz"),
+        "fp64_tflops": round(cells * MHD_F64_FLOP / (res["ms_substep"] / 1e3) / 1e12, 4),
         "paper_ideal_hbm_frac": round(cells * 128.0 / (res["ms_substep"] / 1e3) / 1e9 / hbm_peak, 4)}
     res["plan"].close()
     # config 4: 384^3 FP32 / BF16 storage, Kahan-compensated RK
