@@ -17,8 +17,18 @@
 namespace stn {
 
 constexpr int XC_THREADS = 256;
-constexpr int XC_CHUNK = 2048;   // outputs per CTA
+// Consecutive outputs per thread and sweep (register blocking).  Odd, so that lanes XC_V cells
+// apart read and write distinct shared-memory banks.
+constexpr int XC_V = 9;
 constexpr int XC_MAX_SWEEPS = 16;
+// Outputs per CTA: with its halo (up to 15 sweeps x 4 cells per side) every sweep's span fits
+// in the 256 x 9 outputs one pass of the threads computes.
+constexpr int XC_CHUNK = XC_THREADS * XC_V - 2 * (XC_MAX_SWEEPS - 1) * 4;  // 2184
+constexpr int XC_PAD = 4;  // buffer elements before logical cell 0
+// elements per shared-memory buffer: a sweep starting at cell s r <= 64 reads up to
+// 256 x 9 + 4 cells past its start
+constexpr int XC_BUF = XC_PAD + 64 + XC_THREADS * XC_V + 16;
+static_assert(XC_CHUNK % 4 == 0, "the chunk body is moved as 16-byte vectors");
 
 int xcorr_max_sweeps_per_launch() { return XC_MAX_SWEEPS; }
 
@@ -46,7 +56,7 @@ __device__ __forceinline__ void xcorr_chunk(const T *__restrict__ in, T *__restr
     const int H = sweeps * R;
     const int W = XC_CHUNK + 2 * H;
     A *buf0 = reinterpret_cast<A *>(smem_raw);
-    A *buf1 = buf0 + W;
+    A *buf1 = buf0 + XC_BUF;
     const int64_t n = geo.n[0];
     const int64_t c0 = (int64_t)chunk * XC_CHUNK;
     const T *inx = in + geo.off[0];  // interior element 0
@@ -62,7 +72,7 @@ __device__ __forceinline__ void xcorr_chunk(const T *__restrict__ in, T *__restr
             VT x = src[v];
             const T *e = reinterpret_cast<const T *>(&x);
 #pragma unroll
-            for (int u = 0; u < V; ++u) buf0[H + v * V + u] = (A)e[u];
+            for (int u = 0; u < V; ++u) buf0[XC_PAD + H + v * V + u] = (A)e[u];
         }
     }
     for (int e = threadIdx.x; e < W; e += XC_THREADS) {
@@ -77,18 +87,28 @@ __device__ __forceinline__ void xcorr_chunk(const T *__restrict__ in, T *__restr
         } else {
             v = (gi >= -R && gi < n + R) ? inx[gi] : T(0);
         }
-        buf0[e] = (A)v;
+        buf0[XC_PAD + e] = (A)v;
     }
     __syncthreads();
 
+    // Sweeps.  Thread t computes the XC_V outputs starting at s r + XC_V t from one window of
+    // XC_V + 2r cells in registers, so a cell is read from shared memory (XC_V + 2r) / XC_V
+    // times per sweep instead of 2r + 1 times.  Outputs past the valid span [s r, W - s r) are
+    // computed from stale cells and never read by a valid output.
     A *src = buf0, *dst = buf1;
     for (int s = 1; s <= sweeps; ++s) {
-        const int lo = s * R, hi = W - s * R;
-        for (int p = lo + threadIdx.x; p < hi; p += XC_THREADS) {
+        const int q0 = s * R + XC_V * threadIdx.x;
+        const A *wp = src + XC_PAD + q0 - R;
+        A win[XC_V + 2 * R];  // cells q0 - R .. q0 + XC_V - 1 + R
+#pragma unroll
+        for (int k = 0; k < XC_V + 2 * R; ++k) win[k] = wp[k];
+        A *dp = dst + XC_PAD + q0;
+#pragma unroll
+        for (int v = 0; v < XC_V; ++v) {
             A acc = A(0);
 #pragma unroll
-            for (int j = -R; j <= R; ++j) acc = mac<A>(acc, (A)cf.g[j + R], src[p + j]);
-            dst[p] = acc;
+            for (int j = -R; j <= R; ++j) acc = mac<A>(acc, (A)cf.g[j + R], win[R + v + j]);
+            dp[v] = acc;
         }
         __syncthreads();
         A *t = src;
@@ -97,7 +117,7 @@ __device__ __forceinline__ void xcorr_chunk(const T *__restrict__ in, T *__restr
     }
 
     // write the chunk (+ periodic images of the array ends)
-    const A *res = src + H;
+    const A *res = src + XC_PAD + H;
     if (full) {
         VT *d = reinterpret_cast<VT *>(outx + c0);
         for (int v = threadIdx.x; v < XC_CHUNK / V; v += XC_THREADS) {
@@ -135,7 +155,7 @@ static cudaError_t run(const void *in, void *out, const Geom &g, const void *coe
     using A = typename XAcc<T>::type;
     XCoef<T> cf{};
     for (int j = 0; j < 2 * R + 1; ++j) cf.g[j] = static_cast<const T *>(coeffs)[j];
-    const size_t smem = 2 * sizeof(A) * (XC_CHUNK + 2 * sweeps * R);
+    const size_t smem = 2 * sizeof(A) * XC_BUF;
     const unsigned blocks = (unsigned)((g.n[0] + XC_CHUNK - 1) / XC_CHUNK);
     auto k = xcorr_kernel<T, R>;
     if (smem > 48 * 1024) {
@@ -194,7 +214,7 @@ xcorr_batch_kernel(const BatchHeader *hdr, const BatchXcorr *items) {
     }
 }
 
-static size_t xcorr_batch_smem() { return 2 * sizeof(float) * (XC_CHUNK + 2 * 3); }
+static size_t xcorr_batch_smem() { return 2 * sizeof(float) * XC_BUF; }
 
 int xcorr_batch_grid() {
     static int grid[64] = {};
