@@ -11,8 +11,11 @@
 //     spans exactly 32 groups, one per lane, and stage K is the strip itself.  The widening
 //     (K - 1) R cells per side is the only redundant work: about 10 % at r = 3, K = 4.
 //   * Rows stream in y.  A new row of f_0 enters per iteration, and stage s then computes its
-//     row lagging s R rows behind, from the 2R+1 rows of stage s - 1 held in a small
-//     shared-memory ring.  Stage K's row goes to global memory with its periodic images (Eq. 2).
+//     row lagging s R rows behind.  Each lane keeps, per stage, a register queue of the 2R+1
+//     input rows at its own group (y neighbours come from registers); x neighbours come from
+//     the stage's input row in a small per-warp shared-memory ring.  A cell therefore costs one
+//     16-byte store and three 16-byte loads of shared memory per stage, the bound being shared
+//     memory bandwidth.  Stage K's row goes to global memory with its periodic images (Eq. 2).
 //   * f_0 rows are fetched with 16-byte cp.async copies, P rows ahead, from periodically wrapped
 //     coordinates: the widened strip at a face reads the far side of the domain directly, so
 //     the kernel needs no halo in its input at all (nx a multiple of 4, so no float4 group
@@ -35,26 +38,30 @@ constexpr int TB_WARPS = 4;  // warps (independent strips) per CTA
 // reads R cells beyond its own width).
 __host__ __device__ constexpr int tb_g(int K, int s, int R) { return s == 0 ? tb_g(K, 1, R) + 1 : ((K - s) * R + 3) / 4; }
 
+// Slot of row index v in a ring of n rows (for any integer v).
+__host__ __device__ constexpr int tb_slot(int v, int n) { return ((v % n) + n) % n; }
+
 template <int R, int K> struct Tb {
     static constexpr int G0 = tb_g(K, 0, R);
     static constexpr int G1 = tb_g(K, 1, R);
     static constexpr int TXG = 32 - 2 * G1;  // output groups per strip
     static constexpr int TX = 4 * TXG;       // output cells per strip
     static constexpr int W = TXG + 2 * G0;   // groups per ring row (stage 0 width)
-    static constexpr int P = 3;              // f_0 rows in flight ahead of stage 1
-    // Every ring (f_0 and the K - 1 intermediate stages) has N rows, and the row loop is
-    // unrolled over N iterations, so every ring slot is a compile-time constant.
-    static constexpr int N = 2 * R + 1 + P;
-    static constexpr int RING = N * W * 4;  // floats per ring
-    static constexpr int WARP_FLOATS = K * RING;
+    static constexpr int NQ = 2 * R + 1;     // register queue rows per stage
+    // The row loop is unrolled over NL = 2 NQ iterations, so every queue entry and ring slot is a
+    // compile-time constant.  The f_0 ring has NL rows and runs P rows ahead (its oldest row in
+    // use lags R behind the newest); the rings of stages 1 .. K-1 have NQ rows.
+    static constexpr int NL = 2 * NQ;
+    static constexpr int P = (3 * R + 1) < 7 ? (3 * R + 1) : 7;
+    static constexpr int RING0 = NL * W * 4;  // floats
+    static constexpr int RINGI = NQ * W * 4;
+    static constexpr int WARP_FLOATS = RING0 + (K - 1) * RINGI;
     static constexpr size_t SMEM = (size_t)TB_WARPS * WARP_FLOATS * sizeof(float);
     static_assert(R >= 1 && R <= 4, "radius 1..4: one float4 group per side covers the x neighbours");
     static_assert(TXG >= 8, "strip too narrow");
     static_assert(W <= 64, "two groups per lane at most");
+    static_assert(P + R < NL, "the f_0 ring holds the prefetched rows and the R rows in use");
 };
-
-// Ring slot of row index v (mod N, for any integer v).
-__host__ __device__ constexpr int tb_slot(int v, int n) { return ((v % n) + n) % n; }
 
 struct W2f {  // folded weights
     float g0, gx[4], gy[4];
@@ -70,34 +77,39 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
 
 __device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 
-// One row of stage S (1..K) for this lane's group at loop iteration j (j = U mod N): output row
-// o = j - S R from rows o-R .. o+R of stage S-1 (ring S-1; ring 0 holds f_0), into ring S
-// (S < K) or to global memory (S == K).
-template <int R, int K, int S, int U>
-__device__ __forceinline__ void tb_stage(int lane, int j, int rows_in, float *rings, float *__restrict__ out,
-                                         const Geom &g, const W2f &w, int x0, int ys) {
+// Ring row (float offset) of row index v in the input ring of stage S (ring 0 = f_0).
+template <int R, int K, int S> __device__ __forceinline__ constexpr int tb_in_row(int v) {
     using C = Tb<R, K>;
-    const int o = j - S * R;
-    if (o < S * R || o >= rows_in - S * R) return;  // row outside stage S's valid range (warp-uniform)
+    if constexpr (S == 1) return tb_slot(v, C::NL) * C::W * 4;
+    else return C::RING0 + (S - 2) * C::RINGI + tb_slot(v, C::NQ) * C::W * 4;
+}
+
+// Stage S (1..K) at loop iteration j (j = U mod NL) for this lane's group:
+//  1. the leading input row L = j - (S-1) R (just produced by stage S-1, or fetched for S = 1)
+//     enters the lane's queue;
+//  2. output row o = j - S R is computed from the queue (y neighbours, centre) and the x
+//     neighbours of input row o in the ring, into ring S (S < K) or global memory (S == K).
+template <int R, int K, int S, int U>
+__device__ __forceinline__ void tb_stage(int lane, int j, int rows_in, float *rings, float4 (&Q)[2 * R + 1],
+                                         float *__restrict__ out, const Geom &g, const W2f &w, int x0, int ys) {
+    using C = Tb<R, K>;
     constexpr int GS = tb_g(K, S, R);
     if (lane >= C::TXG + 2 * GS) return;
     const int q = lane - GS + C::G0;  // ring slot of this lane's group
-    const float *in_ring = rings + (S - 1) * C::RING + 4 * q;
-    constexpr int OC = U - S * R;  // ring row of o, before the mod
-    const float *rc = in_ring + tb_slot(OC, C::N) * C::W * 4;
-    float E[12];
-    {
-        const float4 a = ld4(rc - 4), b = ld4(rc), c = ld4(rc + 4);
-        E[0] = a.x, E[1] = a.y, E[2] = a.z, E[3] = a.w;
-        E[4] = b.x, E[5] = b.y, E[6] = b.z, E[7] = b.w;
-        E[8] = c.x, E[9] = c.y, E[10] = c.z, E[11] = c.w;
-    }
+    const int L = j - (S - 1) * R;
+    if (L >= (S - 1) * R && L < rows_in - (S - 1) * R)  // valid row of stage S-1 (warp-uniform)
+        Q[tb_slot(U - (S - 1) * R, C::NQ)] = ld4(rings + tb_in_row<R, K, S>(U - (S - 1) * R) + 4 * q);
+    const int o = j - S * R;
+    if (o < S * R || o >= rows_in - S * R) return;  // row outside stage S's valid range
+    constexpr int OC = U - S * R;  // o, before the mod
+    const float *rc = rings + tb_in_row<R, K, S>(OC) + 4 * q;
+    const float4 cl = ld4(rc - 4), cc = Q[tb_slot(OC, C::NQ)], cr = ld4(rc + 4);
+    const float E[12] = {cl.x, cl.y, cl.z, cl.w, cc.x, cc.y, cc.z, cc.w, cr.x, cr.y, cr.z, cr.w};
     const float2 G0v = make_float2(w.g0, w.g0);
     float2 acc[2] = {__fmul2_rn(G0v, make_float2(E[4], E[5])), __fmul2_rn(G0v, make_float2(E[6], E[7]))};
 #pragma unroll
     for (int a = 1; a <= R; ++a) {
-        const float4 yp = ld4(in_ring + tb_slot(OC + a, C::N) * C::W * 4);
-        const float4 ym = ld4(in_ring + tb_slot(OC - a, C::N) * C::W * 4);
+        const float4 yp = Q[tb_slot(OC + a, C::NQ)], ym = Q[tb_slot(OC - a, C::NQ)];
         const float2 GX = make_float2(w.gx[a - 1], w.gx[a - 1]), GY = make_float2(w.gy[a - 1], w.gy[a - 1]);
         const float2 ys2[2] = {__fadd2_rn(make_float2(yp.x, yp.y), make_float2(ym.x, ym.y)),
                                __fadd2_rn(make_float2(yp.z, yp.w), make_float2(ym.z, ym.w))};
@@ -113,7 +125,8 @@ __device__ __forceinline__ void tb_stage(int lane, int j, int rows_in, float *ri
     }
     const float4 res = make_float4(acc[0].x, acc[0].y, acc[1].x, acc[1].y);
     if constexpr (S < K) {
-        *reinterpret_cast<float4 *>(rings + S * C::RING + tb_slot(OC, C::N) * C::W * 4 + 4 * q) = res;
+        *reinterpret_cast<float4 *>(rings + C::RING0 + (S - 1) * C::RINGI + tb_slot(OC, C::NQ) * C::W * 4 + 4 * q) =
+            res;
     } else {
         const int nx = (int)g.n[0], ny = (int)g.n[1];
         const int x = x0 + 4 * (q - C::G0), y = ys - K * R + o;
@@ -128,12 +141,16 @@ __device__ __forceinline__ void tb_stage(int lane, int j, int rows_in, float *ri
     }
 }
 
+template <int R, int K> struct TbQueues {
+    float4 q[K][2 * R + 1];
+};
+
 template <int R, int K, int S, int U>
-__device__ __forceinline__ void tb_stages(int lane, int j, int rows_in, float *rings, float *out, const Geom &g,
-                                          const W2f &w, int x0, int ys) {
-    tb_stage<R, K, S, U>(lane, j, rows_in, rings, out, g, w, x0, ys);
+__device__ __forceinline__ void tb_stages(int lane, int j, int rows_in, float *rings, TbQueues<R, K> &qs, float *out,
+                                          const Geom &g, const W2f &w, int x0, int ys) {
+    tb_stage<R, K, S, U>(lane, j, rows_in, rings, qs.q[S - 1], out, g, w, x0, ys);
     __syncwarp();
-    if constexpr (S < K) tb_stages<R, K, S + 1, U>(lane, j, rows_in, rings, out, g, w, x0, ys);
+    if constexpr (S < K) tb_stages<R, K, S + 1, U>(lane, j, rows_in, rings, qs, out, g, w, x0, ys);
 }
 
 // Per-lane state of the f_0 stream: the wrapped x offsets of the lane's (up to two) groups and
@@ -151,31 +168,31 @@ template <int R, int K>
 __device__ __forceinline__ void tb_issue(TbStream &st, float *ring0, int slot, int lane, int ny) {
     using C = Tb<R, K>;
     const float *src = st.in + st.base + (int64_t)st.yl * st.pitch;
-    float *dst = ring0 + slot * C::W * 4 + 4 * lane;
+    float *dst = ring0 + slot * C::W * 4 + 4 * lane;  // ring 0 (f_0) starts the warp's rings
     cp_async16(dst, src + st.xoff[0]);
     if (st.ngroups > 1) cp_async16(dst + 4 * 32, src + st.xoff[1]);
     st.yl = st.yl + 1 == ny ? 0 : st.yl + 1;
 }
 
-// One loop iteration j (j = U mod N): fetch f_0 row j + P, wait for row j, run the K stages.
+// One loop iteration j (j = U mod NL): fetch f_0 row j + P, wait for row j, run the K stages.
 template <int R, int K, int U>
-__device__ __forceinline__ void tb_iter(int lane, int j, int rows_in, float *rings, float *out, const Geom &g,
-                                        const W2f &w, int x0, int ys, TbStream &st) {
+__device__ __forceinline__ void tb_iter(int lane, int j, int rows_in, float *rings, TbQueues<R, K> &qs, float *out,
+                                        const Geom &g, const W2f &w, int x0, int ys, TbStream &st) {
     using C = Tb<R, K>;
     if (j >= rows_in) return;
-    // the slot of row j + P held row j + P - N = j - 2R - 1, which stage 1 no longer reads
-    if (j + C::P < rows_in) tb_issue<R, K>(st, rings, tb_slot(U + C::P, C::N), lane, (int)g.n[1]);
+    // the slot of row j + P held row j + P - NL < j - R, which stage 1 no longer reads
+    if (j + C::P < rows_in) tb_issue<R, K>(st, rings, tb_slot(U + C::P, C::NL), lane, (int)g.n[1]);
     cp_async_commit();
     cp_async_wait<C::P>();  // row j has landed (this lane's copies) ...
     __syncwarp();           // ... and every lane's
-    tb_stages<R, K, 1, U>(lane, j, rows_in, rings, out, g, w, x0, ys);
+    tb_stages<R, K, 1, U>(lane, j, rows_in, rings, qs, out, g, w, x0, ys);
 }
 
 template <int R, int K, int... Us>
-__device__ __forceinline__ void tb_period(int lane, int j0, int rows_in, float *rings, float *out, const Geom &g,
-                                          const W2f &w, int x0, int ys, TbStream &st,
+__device__ __forceinline__ void tb_period(int lane, int j0, int rows_in, float *rings, TbQueues<R, K> &qs, float *out,
+                                          const Geom &g, const W2f &w, int x0, int ys, TbStream &st,
                                           std::integer_sequence<int, Us...>) {
-    (tb_iter<R, K, Us>(lane, j0 + Us, rows_in, rings, out, g, w, x0, ys, st), ...);
+    (tb_iter<R, K, Us>(lane, j0 + Us, rows_in, rings, qs, out, g, w, x0, ys, st), ...);
 }
 
 template <int R, int K>
@@ -194,6 +211,7 @@ heat2d_tb_kernel(const float *__restrict__ in, float *__restrict__ out, Geom g, 
     const int rows_in = count + 2 * K * R;
     const int x0 = strip * C::TX;
     float *rings = tb_smem + wid * C::WARP_FLOATS;  // ring 0: f_0; ring s: stage s
+    TbQueues<R, K> qs;
 
     TbStream st;
     st.in = in;
@@ -214,8 +232,8 @@ heat2d_tb_kernel(const float *__restrict__ in, float *__restrict__ out, Geom g, 
         if (j < rows_in) tb_issue<R, K>(st, rings, j, lane, ny);
         cp_async_commit();
     }
-    for (int j0 = 0; j0 < rows_in; j0 += C::N)
-        tb_period<R, K>(lane, j0, rows_in, rings, out, g, w, x0, ys, st, std::make_integer_sequence<int, C::N>{});
+    for (int j0 = 0; j0 < rows_in; j0 += C::NL)
+        tb_period<R, K>(lane, j0, rows_in, rings, qs, out, g, w, x0, ys, st, std::make_integer_sequence<int, C::NL>{});
 }
 
 template <int R, int K>
