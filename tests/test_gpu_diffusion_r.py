@@ -135,3 +135,40 @@ def test_2d_every_variant_matches_oracle(cuda_lib, r, shape, steps):
         np.testing.assert_array_equal(box, want)
         np.testing.assert_array_equal(p.download(a)[0], f)
     p.close()
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_2d_blocked_variants_fall_back(cuda_lib, variant):
+    # the temporally blocked variants need periodic boundaries and nx a multiple of 4; otherwise
+    # they run the one-step kernel, with the same results
+    r = 3
+    shape = (45, 70)  # nx = 70
+    p = _plan(shape, r, L.STENCIL_F32)
+    p.set_variant(variant)
+    f = _field(shape, L.STENCIL_F32)
+    a, b = p.alloc(), p.alloc()
+    p.upload(a, [f])
+    p.step(a, b, 5)
+    p.sync()
+    par = p.params
+    assert_close(p.download(b)[0], oracle.diffusion_r(f, r, par.dt, par.alpha, _h(par, 2), 5), TOL[L.STENCIL_F32],
+                 f"variant {variant}, nx = 70")
+    p.close()
+    # caller-filled halo, nx a multiple of 4: one step, read as given
+    shape = (47, 72)
+    p = _plan(shape, r, L.STENCIL_F32, bc=L.STENCIL_BC_CALLER)
+    p.set_variant(variant)
+    a, b = p.alloc(), p.alloc()
+    ox, oy, _ = p.origin
+    nx, ny, _ = p.dims
+    boxv = synth.uniform(SEED, 11, (ny + 2 * r) * (nx + 2 * r), -1.0, 1.0).reshape(ny + 2 * r, nx + 2 * r)
+    boxv = boxv.astype(np.float32).astype(np.float64)
+    import torch
+    v = p.view3(a[0])
+    v[0, oy - r:oy + ny + r, ox - r:ox + nx + r] = torch.from_numpy(boxv).to(v.device, torch.float32)
+    p.step(a, b, 1)
+    p.sync()
+    par = p.params
+    ref = oracle.diffusion_r_box(boxv, r, par.dt, par.alpha, _h(par, 2), shape)
+    assert_close(p.download(b)[0], ref, TOL[L.STENCIL_F32], f"variant {variant}, caller halo")
+    p.close()
