@@ -245,7 +245,10 @@ stencil_status stencil_sync(stencil_t plan, void *stream);
 
 /*
  * Kernel variants and runtime autotuning.  Each kind has a small table of kernel variants
- * (tile shape, pipeline depth, z-chunk length).  As in the paper's automated tuning of the
+ * (tile shape, pipeline depth, z-chunk length).  2D FP32 DIFFUSION also has temporally
+ * blocked variants (1: two, 2: four Euler steps per pass over the field, the remainder one
+ * step at a time); they apply with periodic boundaries and nx a multiple of 4 and otherwise
+ * run the one-step kernel, with the same results.  As in the paper's automated tuning of the
  * thread-block decomposition (Sec. 5.1), stencil_autotune times every variant on the
  * caller's buffers (one warm-up call, then `reps` timed calls of stencil_step(nsteps) with
  * CUDA events on `stream`), discards variants that fail to launch, and keeps the fastest.
