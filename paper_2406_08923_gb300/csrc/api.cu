@@ -71,8 +71,8 @@ struct stencil_plan {
     int64_t bytes_per_field = 0;
     // coefficients
     int32_t gi[9] = {};
-    double gd[9] = {};
-    float gf[9] = {};
+    double gd[33] = {};  // FP64 radius <= 4; FP32 radius <= 16 (the temporally blocked kernel)
+    float gf[33] = {};
     DiffCoef dcoef{};
     MhdConst mconst{};
     // library-owned scratch
@@ -329,6 +329,8 @@ stencil_status stencil_create(int ndim, const int64_t dims[3], int radius, const
     std::vector<double> wide_w;  // XCORR radius > 4: weights copied to the device below
     if (kind == STENCIL_XCORR && radius > 4) {
         wide_w.assign(static_cast<const double *>(coeffs), static_cast<const double *>(coeffs) + ncoeffs);
+        if (radius <= 16)  // FP32 radius 5..16 also runs the temporally blocked kernel
+            for (int j = 0; j < ncoeffs; ++j) p->gf[j] = (float)wide_w[j];
     } else if (kind == STENCIL_MAXFILTER) {
     } else if (kind == STENCIL_XCORR) {
         for (int j = 0; j < ncoeffs; ++j) {
@@ -478,6 +480,12 @@ stencil_status stencil_halo_fill(stencil_t p, void *const *fields, void *stream)
     return STENCIL_OK;
 }
 
+// XCORR plans that run the temporally blocked, register-window kernel (csrc/xcorr.cu): radius
+// <= 4, and FP32 up to radius 16 (it beats the wide kernel there); the rest run the wide kernel.
+static bool xcorr_blocked(stencil_t p) {
+    return p->kind == STENCIL_XCORR && (p->radius <= 4 || (p->storage == STENCIL_F32 && p->radius <= 16));
+}
+
 // One pass of the plan's kernel from src to dst (sub = RK substep for MHD8).
 static stencil_status run_pass(stencil_t p, void *const *src, void *const *dst, int sweeps, int sub,
                                cudaStream_t s) {
@@ -488,7 +496,7 @@ static stencil_status run_pass(stencil_t p, void *const *src, void *const *dst, 
            "maxfilter launch");
         return STENCIL_OK;
     }
-    if (p->kind == STENCIL_XCORR && p->radius > 4) {
+    if (p->kind == STENCIL_XCORR && !xcorr_blocked(p)) {
         CK(p, launch_xcorr_wide(storage_code(p->storage), p->radius, src[0], dst[0], g, p->wdev, periodic, periodic,
                                 p->err, s),
            "xcorr (wide) launch");
@@ -572,8 +580,8 @@ stencil_status stencil_step(stencil_t p, void *const *fin, void *const *fout, in
                             (p->kind == STENCIL_DIFFUSION && p->ndim == 1);
     if (xcorr_like) {
         // temporal blocking for the radius <= 4 kernel; one sweep per launch otherwise
-        const bool single = !periodic || p->kind == STENCIL_MAXFILTER || p->radius > 4;
-        const int maxs = single ? 1 : xcorr_max_sweeps_per_launch();
+        const bool single = !periodic || p->kind == STENCIL_MAXFILTER || (p->kind == STENCIL_XCORR && !xcorr_blocked(p));
+        const int maxs = single ? 1 : xcorr_max_sweeps_per_launch(p->radius);
         for (int left = nsteps; left > 0;) {
             int k = std::min(left, maxs);
             sweeps.push_back(k);
@@ -695,7 +703,7 @@ static int num_variants(stencil_t p) {
 
 static const char *variant_name(stencil_t p, int v) {
     if (p->kind == STENCIL_MAXFILTER) return "doubling_chunk4096";
-    if (p->kind == STENCIL_XCORR && p->radius > 4) return "wide_register_blocked";
+    if (p->kind == STENCIL_XCORR && !xcorr_blocked(p)) return "wide_register_blocked";
     if (p->kind == STENCIL_DIFFUSION && p->ndim == 1) return "xcorr_folded_chunk2184_v9_temporal_blocking";
     if (p->kind == STENCIL_DIFFUSION && p->ndim == 2)
         return v == 1 ? "stream2d_tb2" : v == 2 ? "stream2d_tb4" : "tile2d_32vx_by8_ry4";

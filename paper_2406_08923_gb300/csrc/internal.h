@@ -34,7 +34,7 @@ cudaError_t launch_halo_fill(const Geom &g, int r, int esize, const Ptrs8 &f, in
 // 2 = f32.  periodic: halo read by wrapping interior indices (any sweeps <= max);
 // otherwise a single sweep reading the caller's halo.  images: write periodic images of
 // the output into its halo.
-int xcorr_max_sweeps_per_launch();
+int xcorr_max_sweeps_per_launch(int r);
 cudaError_t launch_xcorr(int dtype, int r, const void *in, void *out, const Geom &g,
                          const void *coeffs, int sweeps, bool periodic, bool images,
                          cudaStream_t s);

@@ -11,6 +11,7 @@
 // is bit-identical to sweeping once per launch.  int32 arithmetic is done in uint32
 // (modulo 2^32); floating point uses fused multiply-add in order j = -r..r.
 #include <algorithm>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -27,12 +28,14 @@ constexpr int XC_CHUNK = XC_THREADS * XC_V - 2 * (XC_MAX_SWEEPS - 1) * 4;  // 21
 // FP64 sweeps one output per thread and iteration (below), so its chunk is a round 2048.
 template <typename T> constexpr int xc_chunk() { return sizeof(T) == 8 ? 2048 : XC_CHUNK; }
 constexpr int XC_PAD = 4;  // buffer elements before logical cell 0
-// elements per shared-memory buffer: a sweep starting at cell s r <= 64 reads up to
-// 256 x 9 + 4 cells past its start
-constexpr int XC_BUF = XC_PAD + 64 + XC_THREADS * XC_V + 16;
+// elements per shared-memory buffer: a sweep starting at cell s r <= 80 (the halo of the
+// sweeps one launch runs, at most 15 x 5 cells) reads up to 256 x 9 + 16 cells past its start
+constexpr int XC_BUF = XC_PAD + 80 + XC_THREADS * XC_V + 24;
 static_assert(XC_CHUNK % 4 == 0, "the chunk body is moved as 16-byte vectors");
 
-int xcorr_max_sweeps_per_launch() { return XC_MAX_SWEEPS; }
+// Sweeps per launch at radius r: the halo of S sweeps must leave every sweep's span within the
+// 256 x 9 outputs of one pass, i.e. 2 r (S - 1) <= 120.
+int xcorr_max_sweeps_per_launch(int r) { return r <= 4 ? XC_MAX_SWEEPS : std::min(XC_MAX_SWEEPS, 1 + 60 / r); }
 
 template <typename T> struct XAcc { using type = T; };
 template <> struct XAcc<int32_t> { using type = uint32_t; };
@@ -47,7 +50,8 @@ template <> __device__ __forceinline__ uint32_t mac<uint32_t>(uint32_t acc, uint
     return acc + g * f;
 }
 
-template <typename T> struct XCoef { T g[9]; };
+constexpr int XC_MAX_R = 16;  // FP32 radius 5..16 also runs here (int32 and FP64: 0..4)
+template <typename T> struct XCoef { T g[2 * XC_MAX_R + 1]; };
 
 // One chunk of xc_chunk<T>() outputs: stage, sweep in shared memory, write (+ images).
 template <typename T, int R>
@@ -195,14 +199,32 @@ static cudaError_t run_r(int r, const void *in, void *out, const Geom &g, const 
     case 2: return run<T, 2>(in, out, g, coeffs, sweeps, periodic, images, s);
     case 3: return run<T, 3>(in, out, g, coeffs, sweeps, periodic, images, s);
     case 4: return run<T, 4>(in, out, g, coeffs, sweeps, periodic, images, s);
-    default: return cudaErrorInvalidValue;
+    default: break;
     }
+    if constexpr (std::is_same<T, float>::value) {
+        switch (r) {
+        case 5: return run<T, 5>(in, out, g, coeffs, sweeps, periodic, images, s);
+        case 6: return run<T, 6>(in, out, g, coeffs, sweeps, periodic, images, s);
+        case 7: return run<T, 7>(in, out, g, coeffs, sweeps, periodic, images, s);
+        case 8: return run<T, 8>(in, out, g, coeffs, sweeps, periodic, images, s);
+        case 9: return run<T, 9>(in, out, g, coeffs, sweeps, periodic, images, s);
+        case 10: return run<T, 10>(in, out, g, coeffs, sweeps, periodic, images, s);
+        case 11: return run<T, 11>(in, out, g, coeffs, sweeps, periodic, images, s);
+        case 12: return run<T, 12>(in, out, g, coeffs, sweeps, periodic, images, s);
+        case 13: return run<T, 13>(in, out, g, coeffs, sweeps, periodic, images, s);
+        case 14: return run<T, 14>(in, out, g, coeffs, sweeps, periodic, images, s);
+        case 15: return run<T, 15>(in, out, g, coeffs, sweeps, periodic, images, s);
+        case 16: return run<T, 16>(in, out, g, coeffs, sweeps, periodic, images, s);
+        default: break;
+        }
+    }
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_xcorr(int dtype, int r, const void *in, void *out, const Geom &g,
                          const void *coeffs, int sweeps, bool periodic, bool images,
                          cudaStream_t s) {
-    if (sweeps < 1 || sweeps > XC_MAX_SWEEPS) return cudaErrorInvalidValue;
+    if (sweeps < 1 || sweeps > xcorr_max_sweeps_per_launch(r)) return cudaErrorInvalidValue;
     switch (dtype) {
     case 0: return run_r<int32_t>(r, in, out, g, coeffs, sweeps, periodic, images, s);
     case 1: return run_r<double>(r, in, out, g, coeffs, sweeps, periodic, images, s);

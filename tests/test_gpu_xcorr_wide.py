@@ -47,7 +47,9 @@ def test_wide_xcorr_matches_oracle(cuda_lib, storage, r, n, sweeps):
         data = data.astype(np.float32).astype(np.float64)
         g = g.astype(np.float32).astype(np.float64)
     p, a, b = _run(L.STENCIL_XCORR, storage, n, r, data, coeffs=g, sweeps=sweeps)
-    assert p.variant()[2] == "wide_register_blocked"
+    # FP32 up to radius 16 runs the temporally blocked kernel, the rest the wide one
+    blocked = storage == L.STENCIL_F32 and r <= 16
+    assert (p.variant()[2] == "wide_register_blocked") != blocked, p.variant()[2]
     got = p.download(b)[0]
     ref = oracle.xcorr1d(data, g, sweeps)
     assert_close(got, ref, TOL[storage], f"xcorr r={r} n={n}")
@@ -108,4 +110,32 @@ def test_maxfilter_caller_halo(cuda_lib):
     p.step(a, b, 1)
     p.sync()
     assert np.array_equal(p.download(b)[0], oracle.maxfilter1d_box(fhat.astype(np.float64), r))
+    p.close()
+
+
+@pytest.mark.parametrize("r,n,sweeps", [(5, 9001, 14), (9, 4099, 8), (12, 70001, 13), (16, 2187, 5)])
+def test_blocked_fp32_mid_radius(cuda_lib, r, n, sweeps):
+    # FP32 radius 5..16 through the temporally blocked kernel: up to 1 + 60 / r sweeps per
+    # launch, so these sweep counts need several launches; ragged chunks and short arrays
+    g = _weights(r, False)
+    data = synth.uniform(SEED, 400 + r, n, 0.0, 1.0).astype(np.float32).astype(np.float64)
+    g = g.astype(np.float32).astype(np.float64)
+    p, a, b = _run(L.STENCIL_XCORR, L.STENCIL_F32, n, r, data, coeffs=g, sweeps=sweeps)
+    assert p.variant()[2] != "wide_register_blocked"
+    assert_close(p.download(b)[0], oracle.xcorr1d(data, g, sweeps), 1e-5, f"r={r} sweeps={sweeps}")
+    full = p.view3(b[0])[0, 0].double().cpu().numpy()
+    o = p.origin[0]
+    np.testing.assert_array_equal(full[o - r:o], full[o + n - r:o + n])
+    np.testing.assert_array_equal(full[o + n:o + n + r], full[o:o + r])
+    p.close()
+    # caller-filled halo, one sweep
+    p = L.Plan(1, (n,), r, 1, L.STENCIL_BC_CALLER, L.STENCIL_XCORR, L.STENCIL_F32, L.STENCIL_F32, coeffs=g)
+    a, b = p.alloc(), p.alloc()
+    fhat = synth.uniform(SEED, 500 + r, n + 2 * r, 0.0, 1.0).astype(np.float32)
+    import torch
+    o = p.origin[0]
+    p.view3(a[0])[0, 0, o - r:o + n + r] = torch.from_numpy(fhat).to(a[0].device)
+    p.step(a, b, 1)
+    p.sync()
+    assert_close(p.download(b)[0], oracle.xcorr1d_box(fhat.astype(np.float64), g), 1e-5, "caller halo")
     p.close()
