@@ -71,8 +71,8 @@ struct stencil_plan {
     int64_t bytes_per_field = 0;
     // coefficients
     int32_t gi[9] = {};
-    double gd[33] = {};  // FP64 radius <= 4; FP32 radius <= 16 (the temporally blocked kernel)
-    float gf[33] = {};
+    double gd[65] = {};  // FP64 radius <= 4; FP32 radius <= 32 (the temporally blocked kernel)
+    float gf[65] = {};
     DiffCoef dcoef{};
     MhdConst mconst{};
     // library-owned scratch
@@ -329,7 +329,7 @@ stencil_status stencil_create(int ndim, const int64_t dims[3], int radius, const
     std::vector<double> wide_w;  // XCORR radius > 4: weights copied to the device below
     if (kind == STENCIL_XCORR && radius > 4) {
         wide_w.assign(static_cast<const double *>(coeffs), static_cast<const double *>(coeffs) + ncoeffs);
-        if (radius <= 16)  // FP32 radius 5..16 also runs the temporally blocked kernel
+        if (radius <= 32)  // FP32 radius 5..32 also runs the temporally blocked kernel
             for (int j = 0; j < ncoeffs; ++j) p->gf[j] = (float)wide_w[j];
     } else if (kind == STENCIL_MAXFILTER) {
     } else if (kind == STENCIL_XCORR) {
@@ -481,9 +481,9 @@ stencil_status stencil_halo_fill(stencil_t p, void *const *fields, void *stream)
 }
 
 // XCORR plans that run the temporally blocked, register-window kernel (csrc/xcorr.cu): radius
-// <= 4, and FP32 up to radius 16 (it beats the wide kernel there); the rest run the wide kernel.
+// <= 4, and FP32 up to radius 32 (it beats the wide kernel there); the rest run the wide kernel.
 static bool xcorr_blocked(stencil_t p) {
-    return p->kind == STENCIL_XCORR && (p->radius <= 4 || (p->storage == STENCIL_F32 && p->radius <= 16));
+    return p->kind == STENCIL_XCORR && (p->radius <= 4 || (p->storage == STENCIL_F32 && p->radius <= 32));
 }
 
 // One pass of the plan's kernel from src to dst (sub = RK substep for MHD8).

@@ -28,9 +28,9 @@ constexpr int XC_CHUNK = XC_THREADS * XC_V - 2 * (XC_MAX_SWEEPS - 1) * 4;  // 21
 // FP64 sweeps one output per thread and iteration (below), so its chunk is a round 2048.
 template <typename T> constexpr int xc_chunk() { return sizeof(T) == 8 ? 2048 : XC_CHUNK; }
 constexpr int XC_PAD = 4;  // buffer elements before logical cell 0
-// elements per shared-memory buffer: a sweep starting at cell s r <= 80 (the halo of the
-// sweeps one launch runs, at most 15 x 5 cells) reads up to 256 x 9 + 16 cells past its start
-constexpr int XC_BUF = XC_PAD + 80 + XC_THREADS * XC_V + 24;
+// elements per shared-memory buffer: a sweep starting at cell s r <= 96 (the halo of the
+// sweeps one launch runs, at most 3 x 30 cells) reads up to 256 x 9 + 40 cells past its start
+constexpr int XC_BUF = XC_PAD + 96 + XC_THREADS * XC_V + 40;
 static_assert(XC_CHUNK % 4 == 0, "the chunk body is moved as 16-byte vectors");
 
 // Sweeps per launch at radius r: the halo of S sweeps must leave every sweep's span within the
@@ -50,7 +50,7 @@ template <> __device__ __forceinline__ uint32_t mac<uint32_t>(uint32_t acc, uint
     return acc + g * f;
 }
 
-constexpr int XC_MAX_R = 16;  // FP32 radius 5..16 also runs here (int32 and FP64: 0..4)
+constexpr int XC_MAX_R = 32;  // FP32 radius 5..32 also runs here (int32 and FP64: 0..4)
 template <typename T> struct XCoef { T g[2 * XC_MAX_R + 1]; };
 
 // One chunk of xc_chunk<T>() outputs: stage, sweep in shared memory, write (+ images).
@@ -215,6 +215,22 @@ static cudaError_t run_r(int r, const void *in, void *out, const Geom &g, const 
         case 14: return run<T, 14>(in, out, g, coeffs, sweeps, periodic, images, s);
         case 15: return run<T, 15>(in, out, g, coeffs, sweeps, periodic, images, s);
         case 16: return run<T, 16>(in, out, g, coeffs, sweeps, periodic, images, s);
+        case 17: return run<T, 17>(in, out, g, coeffs, sweeps, periodic, images, s);
+        case 18: return run<T, 18>(in, out, g, coeffs, sweeps, periodic, images, s);
+        case 19: return run<T, 19>(in, out, g, coeffs, sweeps, periodic, images, s);
+        case 20: return run<T, 20>(in, out, g, coeffs, sweeps, periodic, images, s);
+        case 21: return run<T, 21>(in, out, g, coeffs, sweeps, periodic, images, s);
+        case 22: return run<T, 22>(in, out, g, coeffs, sweeps, periodic, images, s);
+        case 23: return run<T, 23>(in, out, g, coeffs, sweeps, periodic, images, s);
+        case 24: return run<T, 24>(in, out, g, coeffs, sweeps, periodic, images, s);
+        case 25: return run<T, 25>(in, out, g, coeffs, sweeps, periodic, images, s);
+        case 26: return run<T, 26>(in, out, g, coeffs, sweeps, periodic, images, s);
+        case 27: return run<T, 27>(in, out, g, coeffs, sweeps, periodic, images, s);
+        case 28: return run<T, 28>(in, out, g, coeffs, sweeps, periodic, images, s);
+        case 29: return run<T, 29>(in, out, g, coeffs, sweeps, periodic, images, s);
+        case 30: return run<T, 30>(in, out, g, coeffs, sweeps, periodic, images, s);
+        case 31: return run<T, 31>(in, out, g, coeffs, sweeps, periodic, images, s);
+        case 32: return run<T, 32>(in, out, g, coeffs, sweeps, periodic, images, s);
         default: break;
         }
     }

@@ -47,8 +47,8 @@ def test_wide_xcorr_matches_oracle(cuda_lib, storage, r, n, sweeps):
         data = data.astype(np.float32).astype(np.float64)
         g = g.astype(np.float32).astype(np.float64)
     p, a, b = _run(L.STENCIL_XCORR, storage, n, r, data, coeffs=g, sweeps=sweeps)
-    # FP32 up to radius 16 runs the temporally blocked kernel, the rest the wide one
-    blocked = storage == L.STENCIL_F32 and r <= 16
+    # FP32 up to radius 32 runs the temporally blocked kernel, the rest the wide one
+    blocked = storage == L.STENCIL_F32 and r <= 32
     assert (p.variant()[2] == "wide_register_blocked") != blocked, p.variant()[2]
     got = p.download(b)[0]
     ref = oracle.xcorr1d(data, g, sweeps)
@@ -113,9 +113,10 @@ def test_maxfilter_caller_halo(cuda_lib):
     p.close()
 
 
-@pytest.mark.parametrize("r,n,sweeps", [(5, 9001, 14), (9, 4099, 8), (12, 70001, 13), (16, 2187, 5)])
+@pytest.mark.parametrize("r,n,sweeps", [(5, 9001, 14), (9, 4099, 8), (12, 70001, 13), (16, 2187, 5),
+                                        (20, 5003, 7), (30, 4405, 4), (32, 50003, 3)])
 def test_blocked_fp32_mid_radius(cuda_lib, r, n, sweeps):
-    # FP32 radius 5..16 through the temporally blocked kernel: up to 1 + 60 / r sweeps per
+    # FP32 radius 5..32 through the temporally blocked kernel: up to 1 + 60 / r sweeps per
     # launch, so these sweep counts need several launches; ragged chunks and short arrays
     g = _weights(r, False)
     data = synth.uniform(SEED, 400 + r, n, 0.0, 1.0).astype(np.float32).astype(np.float64)
