@@ -343,11 +343,12 @@ cudaError_t run(const CUtensorMap *map, float *out, const Geom &g, const Coef32 
     X(4, 2, 2, 8, 3)          \
     X(4, 1, 2, 8, 4)          \
     X(8, 1, 2, 8, 2)          \
-    X(4, 1, 2, 8, 3)
+    X(4, 1, 2, 8, 3)          \
+    X(8, 2, 2, 8, 2)
 #define HEAT32_VARIANTS_OTHER(X) X(4, 2, 2, 8, 3)
 
 const char *const NAMES_R3[] = {"f32_by4_ry2_zb2_s8_m3", "f32_by4_ry1_zb2_s8_m4", "f32_by8_ry1_zb2_s8_m2",
-                                "f32_by4_ry1_zb2_s8_m3"};
+                                "f32_by4_ry1_zb2_s8_m3", "f32_by8_ry2_zb2_s8_m2"};
 const char *const NAMES_OTHER[] = {"?", "f32_r1_by4_ry2_zb2_s8_m3", "f32_r2_by4_ry2_zb2_s8_m3", "?",
                                    "f32_r4_by4_ry2_zb2_s8_m3"};
 
@@ -372,7 +373,7 @@ cudaError_t dispatch(int variant, const CUtensorMap *map, float *out, const Geom
 
 }  // namespace
 
-int diffusion_f32_num_variants(int r) { return r == 3 ? 4 : (r >= 1 && r <= 4 ? 1 : 0); }
+int diffusion_f32_num_variants(int r) { return r == 3 ? 5 : (r >= 1 && r <= 4 ? 1 : 0); }
 
 const char *diffusion_f32_variant_name(int r, int v) {
     if (v < 0 || v >= diffusion_f32_num_variants(r)) return "?";
