@@ -54,11 +54,11 @@ NCU_TRAFFIC = {
     "heat_f64": {"variant": "vx2_by4_ry1_zb2_s8", "bytes": 145016576 + 107296427,
                  "src": {"diffusion.cu": "ab9ca43e704d3e8a", "common.cuh": "3f7458d1c75ca5f9"}},
     # 256^3, mean of 3 launches (1-pass capture)
-    "heat_f32": {"variant": "f32_by4_ry2_zb2_s8_m3", "bytes": 82112853 + 25682347,
-                 "src": {"diffusion_f32.cu": "89234518939e8c73", "common.cuh": "3f7458d1c75ca5f9"}},
+    "heat_f32": {"variant": "f32_by4_ry2_zb2_s8_m3", "bytes": 81985963 + 25849515,
+                 "src": {"diffusion_f32.cu": "790dce206050e090", "common.cuh": "3f7458d1c75ca5f9"}},
     # 512^3, mean of 3 launches (1-pass capture)
-    "heat_f32_512": {"variant": "f32_by4_ry2_zb2_s8_m3", "bytes": 580587776 + 526500608,
-                     "src": {"diffusion_f32.cu": "89234518939e8c73", "common.cuh": "3f7458d1c75ca5f9"}},
+    "heat_f32_512": {"variant": "f32_by8_ry2_zb2_s8_m2", "bytes": 586108416 + 523425109,
+                     "src": {"diffusion_f32.cu": "790dce206050e090", "common.cuh": "3f7458d1c75ca5f9"}},
 }
 
 
