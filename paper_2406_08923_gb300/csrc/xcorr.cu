@@ -1,10 +1,13 @@
 // xcorr.cu -- 1D cross-correlation f'_i = sum_{j=-r..r} g_j f^_{i+j} (Sec. 3.1, Eq. 3).
 //
+// Radius 0..4 (int32, FP32, FP64) and, for FP32, 5..32.
+//
 // GB300 design: the input (2^20 int32 = 4 MiB in the benchmark) is L2-resident and a single
 // sweep moves ~8 MB, far less than what a launch costs in latency.  So one launch performs
 // several sweeps (temporal blocking): each CTA stages its chunk plus a halo of
 // sweeps * r cells per side in shared memory (coalesced 128-bit loads for the body,
-// periodic wrap for the halo), runs the sweeps in shared memory on a shrinking valid region,
+// periodic wrap for the halo), runs the sweeps in shared memory on a shrinking valid region
+// (each thread 9 consecutive outputs from a register window; FP64 one output per thread),
 // and writes its chunk once, together with the periodic images of the array ends so the
 // output is a complete augmented array (Eq. 2).  Every output value is produced by the same
 // multiply-add sequence j = -r..r as a one-sweep-per-launch kernel would use, so the result

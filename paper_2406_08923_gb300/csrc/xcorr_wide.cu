@@ -1,14 +1,15 @@
 // xcorr_wide.cu -- 1D stencils of large radius: the cross-correlation of Eq. 3 for radius
-// 5..1024 (the radius sweep of Sec. 5.2, Fig. 8) and the max filter f'_i = max_{j=-r..r} f^_{i+j}
-// (the nonlinear stencil of Sec. 2.1) for radius 0..1024.
+// 5..1024 in FP64 and 33..1024 in FP32 (the radius sweep of Sec. 5.2, Fig. 8; FP32 up to radius
+// 32 runs the temporally blocked kernel of xcorr.cu) and the max filter
+// f'_i = max_{j=-r..r} f^_{i+j} (the nonlinear stencil of Sec. 2.1) for radius 0..1024.
 //
 // Cross-correlation.  At large radius the work is 2r+1 multiply-adds per output, so the kernel
 // is built for FMA throughput: a CTA stages its chunk of outputs plus a halo of r cells per side
 // and the 2r+1 weights in shared memory; each thread computes V consecutive outputs, and for
 // every block of V weights loads the 2V-1 cells those outputs need into registers once and
 // performs V x V multiply-adds from registers (one shared load per ~5 FMAs at V = 15).  V is
-// odd so that lanes, V cells apart, fall on distinct shared-memory banks.  Each output adds its
-// terms in the order j = -r .. r.
+// odd so that lanes, V cells apart, fall on distinct shared-memory banks, and chosen per radius
+// (wide_block).  Each output adds its terms in the order j = -r .. r.
 //
 // Max filter.  A direct window maximum costs 2r+1 comparisons per output.  Instead the chunk
 // (+ halo) is reduced by doubling in shared memory: after step k every cell holds the maximum
