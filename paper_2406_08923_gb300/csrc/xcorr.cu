@@ -28,7 +28,9 @@ constexpr int XC_MAX_SWEEPS = 16;
 // Outputs per CTA: with its halo (up to 15 sweeps x 4 cells per side) every sweep's span fits
 // in the 256 x 9 outputs one pass of the threads computes.
 constexpr int XC_CHUNK = XC_THREADS * XC_V - 2 * (XC_MAX_SWEEPS - 1) * 4;  // 2184
-// FP64 sweeps one output per thread and iteration (below), so its chunk is a round 2048.
+// FP64 sweeps one output per thread and iteration (below), so its chunk is a round 2048, or
+// 1024 when 2048 would leave fewer than 4 CTAs per SM (the 2^20-cell benchmark: the FP64
+// pipe then waits on the SMs that got one CTA more than the others).
 template <typename T> constexpr int xc_chunk() { return sizeof(T) == 8 ? 2048 : XC_CHUNK; }
 constexpr int XC_PAD = 4;  // buffer elements before logical cell 0
 // elements per shared-memory buffer: a sweep starting at cell s r <= 96 (the halo of the
@@ -56,13 +58,14 @@ template <> __device__ __forceinline__ uint32_t mac<uint32_t>(uint32_t acc, uint
 constexpr int XC_MAX_R = 32;  // FP32 radius 5..32 also runs here (int32 and FP64: 0..4)
 template <typename T> struct XCoef { T g[2 * XC_MAX_R + 1]; };
 
-// One chunk of xc_chunk<T>() outputs: stage, sweep in shared memory, write (+ images).
+// One chunk of outputs (xc_chunk<T>(); FP64: chunk_len) : stage, sweep in shared memory, write
+// (+ images).
 template <typename T, int R>
 __device__ __forceinline__ void xcorr_chunk(const T *__restrict__ in, T *__restrict__ out, const Geom &geo,
                                             const XCoef<T> &cf, int sweeps, int periodic, int images, int chunk,
-                                            unsigned char *smem_raw) {
+                                            unsigned char *smem_raw, int chunk_len = 0) {
     using A = typename XAcc<T>::type;
-    constexpr int CHUNK = xc_chunk<T>();
+    const int CHUNK = sizeof(A) == 8 ? chunk_len : xc_chunk<T>();
     const int H = sweeps * R;
     const int W = CHUNK + 2 * H;
     A *buf0 = reinterpret_cast<A *>(smem_raw);
@@ -170,9 +173,9 @@ __device__ __forceinline__ void xcorr_chunk(const T *__restrict__ in, T *__restr
 template <typename T, int R>
 __global__ void __launch_bounds__(XC_THREADS)
 xcorr_kernel(const T *__restrict__ in, T *__restrict__ out, Geom geo, XCoef<T> cf, int sweeps, int periodic,
-             int images) {
+             int images, int chunk_len) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    xcorr_chunk<T, R>(in, out, geo, cf, sweeps, periodic, images, blockIdx.x, smem_raw);
+    xcorr_chunk<T, R>(in, out, geo, cf, sweeps, periodic, images, blockIdx.x, smem_raw, chunk_len);
 }
 
 template <typename T, int R>
@@ -182,14 +185,16 @@ static cudaError_t run(const void *in, void *out, const Geom &g, const void *coe
     XCoef<T> cf{};
     for (int j = 0; j < 2 * R + 1; ++j) cf.g[j] = static_cast<const T *>(coeffs)[j];
     const size_t smem = 2 * sizeof(A) * XC_BUF;
-    const unsigned blocks = (unsigned)((g.n[0] + xc_chunk<T>() - 1) / xc_chunk<T>());
+    int chunk_len = xc_chunk<T>();
+    if (sizeof(T) == 8 && (g.n[0] + chunk_len - 1) / chunk_len < 4 * device_sms()) chunk_len /= 2;
+    const unsigned blocks = (unsigned)((g.n[0] + chunk_len - 1) / chunk_len);
     auto k = xcorr_kernel<T, R>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     k<<<blocks, XC_THREADS, smem, s>>>(static_cast<const T *>(in), static_cast<T *>(out), g, cf,
-                                       sweeps, periodic ? 1 : 0, images ? 1 : 0);
+                                       sweeps, periodic ? 1 : 0, images ? 1 : 0, chunk_len);
     return cudaGetLastError();
 }
 
