@@ -284,7 +284,8 @@ typedef struct stencil_request {
     stencil_params params; /* DIFFUSION and MHD8 constants (as for stencil_create) */
 } stencil_request;
 
-enum { STENCIL_REQ_PENDING = 0, STENCIL_REQ_ACTIVE = 1, STENCIL_REQ_COMPLETING = 2, STENCIL_REQ_DONE = 3 };
+enum { STENCIL_REQ_PENDING = 0, STENCIL_REQ_ACTIVE = 1, STENCIL_REQ_COMPLETING = 2, STENCIL_REQ_DONE = 3,
+       STENCIL_REQ_CANCELLED = 4 };
 
 /* Create a server with an HBM budget (bytes of problem data resident at once) and at most
  * max_active problems in flight.  Allocates only small tables; problem memory comes from
@@ -310,6 +311,15 @@ stencil_status stencil_server_progress(stencil_server_t server, int *n_pending, 
                                        int *n_done);
 /* State of a ticket (STENCIL_REQ_*). */
 stencil_status stencil_server_poll(stencil_server_t server, int64_t ticket, int *state);
+/*
+ * Cancel a problem that has not started its copy-back.  A pending problem leaves the queue;
+ * an active one leaves the batch before the next iteration, and its device memory returns to
+ * the pool in stream order (after the iteration already launched).  Its host_out arrays are
+ * never written, and host_in / host_out may be released once this returns.  The ticket then
+ * reports STENCIL_REQ_CANCELLED.  EINVAL for an unknown ticket or one already COMPLETING, DONE
+ * or CANCELLED.
+ */
+stencil_status stencil_server_cancel(stencil_server_t server, int64_t ticket);
 /* Bytes resident now, the peak, and cells x steps of all finished problems. */
 stencil_status stencil_server_stats(stencil_server_t server, int64_t *bytes_in_use,
                                     int64_t *peak_bytes, int64_t *cell_updates_done);

@@ -31,9 +31,10 @@ EXPORTED = (
     "stencil_set_variant", "stencil_autotune", "stencil_field_norms_noalloc", "stencil_selftest_wait",
     "stencil_server_create", "stencil_server_destroy", "stencil_server_submit", "stencil_server_progress",
     "stencil_server_poll", "stencil_server_stats", "stencil_server_sync", "stencil_server_last_error_detail",
+    "stencil_server_cancel",
 )
 
-STENCIL_REQ_PENDING, STENCIL_REQ_ACTIVE, STENCIL_REQ_COMPLETING, STENCIL_REQ_DONE = range(4)
+STENCIL_REQ_PENDING, STENCIL_REQ_ACTIVE, STENCIL_REQ_COMPLETING, STENCIL_REQ_DONE, STENCIL_REQ_CANCELLED = range(5)
 
 
 class stencil_params(ctypes.Structure):
@@ -92,6 +93,7 @@ def load():
             "stencil_server_submit": (I, [P, ctypes.POINTER(stencil_request), PP, PP, ctypes.POINTER(I64)]),
             "stencil_server_progress": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
             "stencil_server_poll": (I, [P, I64, ctypes.POINTER(I)]),
+            "stencil_server_cancel": (I, [P, I64]),
             "stencil_server_stats": (I, [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)]),
             "stencil_server_sync": (I, [P]),
             "stencil_server_last_error_detail": (ctypes.c_char_p, [P]),
@@ -256,6 +258,10 @@ def stencil_server_poll(h, ticket):
     st = ctypes.c_int()
     _scheck(load().stencil_server_poll(h, int(ticket), ctypes.byref(st)), "stencil_server_poll", h)
     return st.value
+
+
+def stencil_server_cancel(h, ticket):
+    _scheck(load().stencil_server_cancel(h, int(ticket)), "stencil_server_cancel", h)
 
 
 def stencil_server_stats(h):

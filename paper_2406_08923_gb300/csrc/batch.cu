@@ -87,7 +87,7 @@ bool encode_f32(CUtensorMap *m, const float *ptr, const Geom &g, const int box[3
 
 size_t up256(size_t b) { return (b + 255) & ~size_t(255); }
 
-enum { ST_PENDING = 0, ST_ACTIVE = 1, ST_COMPLETING = 2, ST_DONE = 3 };
+enum { ST_PENDING = 0, ST_ACTIVE = 1, ST_COMPLETING = 2, ST_DONE = 3, ST_CANCELLED = 4 };
 
 struct Req {
     int64_t ticket = 0;
@@ -600,6 +600,39 @@ stencil_status stencil_server_poll(stencil_server_t s, int64_t ticket, int *stat
     auto it = s->table.find(ticket);
     if (it == s->table.end()) return sfail(s, STENCIL_EINVAL, "unknown ticket");
     if (state) *state = it->second->state;
+    return STENCIL_OK;
+}
+
+stencil_status stencil_server_cancel(stencil_server_t s, int64_t ticket) {
+    if (!s) return sfail(nullptr, STENCIL_EINVAL, "server is NULL");
+    auto it = s->table.find(ticket);
+    if (it == s->table.end()) return sfail(s, STENCIL_EINVAL, "unknown ticket");
+    Req *r = it->second;
+    if (r->state == ST_PENDING) {
+        for (auto p = s->pending.begin(); p != s->pending.end(); ++p)
+            if (*p == r) {
+                s->pending.erase(p);
+                break;
+            }
+    } else if (r->state == ST_ACTIVE) {
+        for (size_t a = 0; a < s->active.size(); ++a)
+            if (s->active[a] == r) {
+                s->active[a] = s->active.back();
+                s->active.pop_back();
+                break;
+            }
+        // the iteration already launched may still read the block: free it in stream order
+        SCK(s, cudaFreeAsync(r->base, s->stream), "pool free");
+        r->base = nullptr;
+        s->used -= (int64_t)r->bytes;
+    } else {
+        return sfail(s, STENCIL_EINVAL, "ticket is already completing, done or cancelled");
+    }
+    r->state = ST_CANCELLED;
+    for (int q = 0; q < 8; ++q) {
+        r->host_in[q] = nullptr;
+        r->host_out[q] = nullptr;
+    }
     return STENCIL_OK;
 }
 

@@ -102,3 +102,46 @@ def test_malformed_requests_rejected(cuda_lib):
             L.stencil_server_submit(server, big, [x.data_ptr()] * 8, [x.data_ptr()] * 8)
     finally:
         L.stencil_server_destroy(server)
+
+
+def test_cancel_pending_and_active(cuda_lib):
+    # a cancelled problem leaves the queue (pending) or the batch (active), its memory returns to
+    # the pool, its host output is never written, and the other problems still finish correctly
+    n, steps = 16, 6
+    templates = serving.Templates(pinned=True)
+    src = templates.get(L.STENCIL_DIFFUSION, n)[0]
+    outs = [torch.full((n ** 3,), -7.0, dtype=torch.float32).pin_memory() for _ in range(4)]
+    server = L.stencil_server_create(10 ** 9, 2)  # two slots: requests 2 and 3 wait
+    try:
+        q = serving.request_params(L.STENCIL_DIFFUSION, n, steps)
+        tickets = [L.stencil_server_submit(server, q, [src.data_ptr()], [o.data_ptr()]) for o in outs]
+        L.stencil_server_cancel(server, tickets[3])  # pending
+        assert L.stencil_server_poll(server, tickets[3]) == L.STENCIL_REQ_CANCELLED
+        L.stencil_server_progress(server)  # admits 0 and 1, one step each
+        assert L.stencil_server_poll(server, tickets[0]) == L.STENCIL_REQ_ACTIVE
+        L.stencil_server_cancel(server, tickets[0])  # active
+        assert L.stencil_server_poll(server, tickets[0]) == L.STENCIL_REQ_CANCELLED
+        with pytest.raises(L.StencilError) as e:
+            L.stencil_server_cancel(server, tickets[0])
+        assert e.value.status == L.STENCIL_EINVAL
+        for _ in range(200):
+            L.stencil_server_progress(server)
+            if all(L.stencil_server_poll(server, t) == L.STENCIL_REQ_DONE for t in (tickets[1], tickets[2])):
+                break
+        L.stencil_server_sync(server)
+        assert L.stencil_server_poll(server, tickets[1]) == L.STENCIL_REQ_DONE
+        assert L.stencil_server_poll(server, tickets[2]) == L.STENCIL_REQ_DONE
+        used, _, done = L.stencil_server_stats(server)
+        assert used == 0
+        assert done == 2 * n ** 3 * steps
+        for i in (0, 3):
+            assert torch.all(outs[i] == -7.0)
+        par = L.heat_params(n)
+        ref = oracle.diffusion(src.numpy().astype(np.float64).reshape(n, n, n), par.dt, par.alpha,
+                               (par.dx[0], par.dx[1], par.dx[2]), steps)
+        for i in (1, 2):
+            assert_close(outs[i].numpy(), ref.ravel(), 1e-5, f"request {i}")
+        with pytest.raises(L.StencilError):
+            L.stencil_server_cancel(server, tickets[1])  # done
+    finally:
+        L.stencil_server_destroy(server)
