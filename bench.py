@@ -691,6 +691,11 @@ CASES = {
     "mhd_f32": ("mhd", 2, MHD_N_LOWP, 1),
     "mhd_bf16": ("mhd", 3, MHD_N_LOWP, 1),
     "xcorr_i32": ("xcorr", 0, XC_N, XC_SWEEPS),
+    # radius sweep workloads (2^24 cells; --radius picks r)
+    "xcorr1d_f32": ("xcorr_r", 2, 1 << 24, 1),
+    "xcorr1d_f64": ("xcorr_r", 1, 1 << 24, 1),
+    "maxfilter_f32": ("maxfilter", 2, 1 << 24, 1),
+    "heat2d_f32": ("heat2d", 2, 4096, 4),
 }
 
 
@@ -715,6 +720,23 @@ def run_case(args):
         p = L.Plan(3, (n, n, n), 3, 8, L.STENCIL_BC_PERIODIC, L.STENCIL_MHD8, storage, compute, params=par)
         a, b = p.alloc(), p.alloc()
         p.upload(a, synth.mhd_fields(n))
+    elif kind == "heat2d":
+        r = args.radius or 3
+        shape = (n, n)
+        p = L.Plan(2, shape, r, 1, L.STENCIL_BC_PERIODIC, L.STENCIL_DIFFUSION, storage, storage,
+                   params=L.heat_params(shape))
+        a, b = p.alloc(), p.alloc()
+        p.upload(a, [synth.uniform(2406089237, 2, n * n, -1.0, 1.0).reshape(shape)])
+    elif kind in ("xcorr_r", "maxfilter"):
+        r = args.radius if args.radius is not None else 64
+        g = None
+        if kind == "xcorr_r":
+            g = synth.uniform(2406089239, 10 + r, 2 * r + 1, 0.0, 1.0)
+            g = g / g.sum()
+        p = L.Plan(1, (n,), r, 1, L.STENCIL_BC_PERIODIC,
+                   L.STENCIL_XCORR if kind == "xcorr_r" else L.STENCIL_MAXFILTER, storage, storage, coeffs=g)
+        a, b = p.alloc(), p.alloc()
+        p.upload(a, [synth.uniform(2406089239, 1, n, 0.0, 1.0)])
     else:
         data, g = synth.xcorr_int32(n)
         p = L.Plan(1, (n,), 3, 1, L.STENCIL_BC_PERIODIC, L.STENCIL_XCORR, storage, storage, coeffs=g)
@@ -725,8 +747,8 @@ def run_case(args):
         p.step(a, b, steps, stream)
     ms = _timed(lambda: p.step(a, b, steps, stream), args.steps, stream)
     p.sync()
-    print(json.dumps({"case": args.case, "n": n, "steps_per_job": steps, "variant": p.variant()[2],
-                      "ms_per_job": round(ms, 4)}), flush=True)
+    print(json.dumps({"case": args.case, "n": n, "radius": args.radius, "steps_per_job": steps,
+                      "variant": p.variant()[2], "ms_per_job": round(ms, 4)}), flush=True)
     return 0
 
 
@@ -743,6 +765,7 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="grid size for --case")
     ap.add_argument("--variant", type=int, default=0, help="kernel variant for --case")
     ap.add_argument("--job-steps", type=int, default=None, help="steps per job for --case")
+    ap.add_argument("--radius", type=int, default=None, help="stencil radius for the 1D / 2D --case workloads")
     ap.add_argument("--serving", action="store_true", help="serving configuration only (one JSON line)")
     ap.add_argument("--radius-sweep", action="store_true", help="diffusion radius sweep only (one JSON line)")
     args = ap.parse_args()
