@@ -92,3 +92,28 @@ def test_minimum_extent_wraps_several_times(cuda_lib):
     data, g = synth.xcorr_int32(7, seed=9)
     out, *_ = _run(data, g, 16, L.STENCIL_I32)
     assert np.array_equal(out, oracle.xcorr1d(data, g, 16))
+
+
+@pytest.mark.parametrize("dtype", [L.STENCIL_I32, L.STENCIL_F32, L.STENCIL_F64])
+def test_large_grid_full_blocks(cuda_lib, dtype):
+    # 2^21 + 5 cells: enough chunks for 256-thread blocks (FP64: 2048-cell chunks); smaller
+    # grids run 128-thread blocks (FP64: 1024-cell chunks).  16 + 3 sweeps: two launches.
+    n = (1 << 21) + 5
+    if dtype == L.STENCIL_I32:
+        data, g = synth.xcorr_int32(n)
+    else:
+        data = synth.uniform(2406089231, 9, n, -1.0, 1.0)
+        g = D2
+        if dtype == L.STENCIL_F32:
+            data = data.astype(np.float32).astype(np.float64)
+            g = D2.astype(np.float32).astype(np.float64)
+    out, whole, p, _ = _run(data, g, 19, dtype)
+    ref = oracle.xcorr1d(data, g, 19)
+    if dtype == L.STENCIL_I32:
+        assert np.array_equal(out, ref)
+    else:
+        assert_close(out, ref, 1e-12 if dtype == L.STENCIL_F64 else 1e-5, "2^21 + 5")
+    ox = p.origin[0]
+    np.testing.assert_array_equal(whole[ox - 3:ox], whole[ox + n - 3:ox + n])
+    np.testing.assert_array_equal(whole[ox + n:ox + n + 3], whole[ox:ox + 3])
+    p.close()
