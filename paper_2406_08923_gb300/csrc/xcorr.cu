@@ -58,15 +58,14 @@ template <> __device__ __forceinline__ uint32_t mac<uint32_t>(uint32_t acc, uint
 constexpr int XC_MAX_R = 32;  // FP32 radius 5..32 also runs here (int32 and FP64: 0..4)
 template <typename T> struct XCoef { T g[2 * XC_MAX_R + 1]; };
 
-// One chunk of outputs: stage, sweep in shared memory, write (+ images).  The block has 128 or
-// 256 threads; the chunk is 9 x threads - 120 cells (FP64: chunk_len).
+// One chunk of outputs (xc_chunk<T>(); FP64: chunk_len) : stage, sweep in shared memory, write
+// (+ images).
 template <typename T, int R>
 __device__ __forceinline__ void xcorr_chunk(const T *__restrict__ in, T *__restrict__ out, const Geom &geo,
                                             const XCoef<T> &cf, int sweeps, int periodic, int images, int chunk,
                                             unsigned char *smem_raw, int chunk_len = 0) {
     using A = typename XAcc<T>::type;
-    const int NT = (int)blockDim.x;
-    const int CHUNK = sizeof(A) == 8 ? chunk_len : NT * XC_V - 2 * (XC_MAX_SWEEPS - 1) * 4;
+    const int CHUNK = sizeof(A) == 8 ? chunk_len : xc_chunk<T>();
     const int H = sweeps * R;
     const int W = CHUNK + 2 * H;
     A *buf0 = reinterpret_cast<A *>(smem_raw);
@@ -82,14 +81,14 @@ __device__ __forceinline__ void xcorr_chunk(const T *__restrict__ in, T *__restr
     const bool full = c0 + CHUNK <= n;
     if (full) {
         const VT *src = reinterpret_cast<const VT *>(inx + c0);
-        for (int v = threadIdx.x; v < CHUNK / V; v += NT) {
+        for (int v = threadIdx.x; v < CHUNK / V; v += XC_THREADS) {
             VT x = src[v];
             const T *e = reinterpret_cast<const T *>(&x);
 #pragma unroll
             for (int u = 0; u < V; ++u) buf0[XC_PAD + H + v * V + u] = (A)e[u];
         }
     }
-    for (int e = threadIdx.x; e < W; e += NT) {
+    for (int e = threadIdx.x; e < W; e += XC_THREADS) {
         const bool body = e >= H && e < H + CHUNK;
         if (full && body) continue;
         int64_t gi = c0 - H + e;
@@ -115,7 +114,7 @@ __device__ __forceinline__ void xcorr_chunk(const T *__restrict__ in, T *__restr
     for (int s = 1; s <= sweeps; ++s) {
         if constexpr (sizeof(A) == 8) {
             const int lo = s * R, hi = W - s * R;
-            for (int p = lo + threadIdx.x; p < hi; p += NT) {
+            for (int p = lo + threadIdx.x; p < hi; p += XC_THREADS) {
                 A acc = A(0);
 #pragma unroll
                 for (int j = -R; j <= R; ++j) acc = mac<A>(acc, (A)cf.g[j + R], src[XC_PAD + p + j]);
@@ -150,7 +149,7 @@ __device__ __forceinline__ void xcorr_chunk(const T *__restrict__ in, T *__restr
     const A *res = src + XC_PAD + H;
     if (full) {
         VT *d = reinterpret_cast<VT *>(outx + c0);
-        for (int v = threadIdx.x; v < CHUNK / V; v += NT) {
+        for (int v = threadIdx.x; v < CHUNK / V; v += XC_THREADS) {
             VT x;
             T *e = reinterpret_cast<T *>(&x);
 #pragma unroll
@@ -158,11 +157,11 @@ __device__ __forceinline__ void xcorr_chunk(const T *__restrict__ in, T *__restr
             d[v] = x;
         }
     } else {
-        for (int p = threadIdx.x; p < CHUNK && c0 + p < n; p += NT)
+        for (int p = threadIdx.x; p < CHUNK && c0 + p < n; p += XC_THREADS)
             outx[c0 + p] = (T)res[p];
     }
     if (images) {
-        for (int p = threadIdx.x; p < CHUNK; p += NT) {
+        for (int p = threadIdx.x; p < CHUNK; p += XC_THREADS) {
             const int64_t gi = c0 + p;
             if (gi >= n) break;
             if (gi < R) outx[gi + n] = (T)res[p];
@@ -186,25 +185,16 @@ static cudaError_t run(const void *in, void *out, const Geom &g, const void *coe
     XCoef<T> cf{};
     for (int j = 0; j < 2 * R + 1; ++j) cf.g[j] = static_cast<const T *>(coeffs)[j];
     const size_t smem = 2 * sizeof(A) * XC_BUF;
-    // Fewer than 4 CTAs per SM leaves the SMs unevenly loaded (the 2^20-cell benchmark): halve
-    // the chunk (FP64) or the block (the others: 128 threads, 1032-cell chunks).
-    int chunk_len = xc_chunk<T>(), threads = XC_THREADS;
-    if ((g.n[0] + chunk_len - 1) / chunk_len < 4 * device_sms()) {
-        if (sizeof(T) == 8) {
-            chunk_len /= 2;
-        } else {
-            threads = XC_THREADS / 2;
-            chunk_len = threads * XC_V - 2 * (XC_MAX_SWEEPS - 1) * 4;
-        }
-    }
+    int chunk_len = xc_chunk<T>();
+    if (sizeof(T) == 8 && (g.n[0] + chunk_len - 1) / chunk_len < 4 * device_sms()) chunk_len /= 2;
     const unsigned blocks = (unsigned)((g.n[0] + chunk_len - 1) / chunk_len);
     auto k = xcorr_kernel<T, R>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k<<<blocks, threads, smem, s>>>(static_cast<const T *>(in), static_cast<T *>(out), g, cf, sweeps,
-                                    periodic ? 1 : 0, images ? 1 : 0, chunk_len);
+    k<<<blocks, XC_THREADS, smem, s>>>(static_cast<const T *>(in), static_cast<T *>(out), g, cf,
+                                       sweeps, periodic ? 1 : 0, images ? 1 : 0, chunk_len);
     return cudaGetLastError();
 }
 

@@ -96,8 +96,8 @@ def test_minimum_extent_wraps_several_times(cuda_lib):
 
 @pytest.mark.parametrize("dtype", [L.STENCIL_I32, L.STENCIL_F32, L.STENCIL_F64])
 def test_large_grid_full_blocks(cuda_lib, dtype):
-    # 2^21 + 5 cells: enough chunks for 256-thread blocks (FP64: 2048-cell chunks); smaller
-    # grids run 128-thread blocks (FP64: 1024-cell chunks).  16 + 3 sweeps: two launches.
+    # 2^21 + 5 cells: enough chunks for FP64's 2048-cell chunks (smaller grids run 1024-cell
+    # chunks), many chunks and a ragged tail.  16 + 3 sweeps: two launches.
     n = (1 << 21) + 5
     if dtype == L.STENCIL_I32:
         data, g = synth.xcorr_int32(n)
