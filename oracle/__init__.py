@@ -29,15 +29,20 @@ _lib = None
 R = 3  # radius of the 6th-order central differences (Sec. 3.3)
 
 
-def build(force: bool = False) -> str:
-    """Compile oracle.c into liboracle.so (gcc, -O2, no FMA contraction, OpenMP)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".{os.getpid()}.tmp"
+def build(force: bool = False, src: str | None = None, lib: str | None = None) -> str:
+    """Compile oracle.c into liboracle.so (gcc, -O2, no FMA contraction, OpenMP).
+
+    `src` / `lib` default to this package's source and library; the planted-mistake tests pass
+    a mutated copy of the source and a library path in a temporary directory."""
+    src = src or _SRC
+    lib = lib or _LIB
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
+        tmp = lib + f".{os.getpid()}.tmp"
         cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
-               "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB)
-    return _LIB
+               "-fPIC", "-shared", src, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True, capture_output=True)
+        os.replace(tmp, lib)
+    return lib
 
 
 def _load():

@@ -7,6 +7,15 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+# Planted-mistake runs (test_oracle_mistakes.py) point the oracle package at a mutated copy of
+# its C source, compiled beforehand into a temporary directory.  Unset in every other run.
+_MUTANT_SRC = os.environ.get("STENCIL_ORACLE_MUTANT_SRC")
+if _MUTANT_SRC:
+    import oracle as _oracle
+
+    _oracle._SRC = _MUTANT_SRC
+    _oracle._LIB = os.path.splitext(_MUTANT_SRC)[0] + ".so"
+
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built library")

@@ -169,6 +169,55 @@ def test_grad_div_A_in_current():
     _check(oracle.mhd_rhs(f, p), exp)
 
 
+def test_entropy_advection_by_a_uniform_flow():
+    # u uniform, lnrho uniform, s = eps sin(k x): A3 reduces to ds/dt = -u . grad s (no shear, no
+    # current), A2 to the entropy part of the pressure term, A1 and A4 to zero.
+    p = _par()
+    (Z, Y, X), h = grid(N)
+    k, eps, U, l0 = 2, 2e-2, (0.4, -0.3, 0.25), 0.1
+    f = np.zeros((8, N, N, N))
+    f[LNRHO] = l0
+    f[UX], f[UY], f[UZ] = U
+    f[SS] = eps * np.sin(k * X)
+    dsdx = lam1(k, h) * eps * np.cos(k * X)
+    cs2, _ = _temp(p, l0, f[SS])
+    exp = np.zeros_like(f)
+    exp[UX] = -cs2 * dsdx / p.cp
+    exp[SS] = -U[0] * dsdx
+    _check(oracle.mhd_rhs(f, p), exp)
+
+
+def test_lorentz_force_and_induction_every_component():
+    # A = (a sin(q z), c sin(m x), b sin(k x)) is divergence-free, so j = -lap A / mu0 and
+    # B = curl A = (0, dAx/dz - dAz/dx, dAy/dx); with a uniform u every component of u x B and
+    # j x B is nonzero somewhere, so each is checked with its own sign.
+    p = _par()
+    (Z, Y, X), h = grid(N)
+    (q, a), (m, c), (k, b) = (2, 1e-2), (3, -2e-2), (1, 1.5e-2)
+    U, l0 = (0.3, -0.45, 0.2), -0.15
+    f = np.zeros((8, N, N, N))
+    f[LNRHO] = l0
+    f[UX], f[UY], f[UZ] = U
+    f[AX] = a * np.sin(q * Z)
+    f[AY] = c * np.sin(m * X)
+    f[AZ] = b * np.sin(k * X)
+    lapA = (lam2(q, h) * f[AX], lam2(m, h) * f[AY], lam2(k, h) * f[AZ])
+    j = [-v / p.mu0 for v in lapA]
+    B = (np.zeros_like(X),
+         lam1(q, h) * a * np.cos(q * Z) - lam1(k, h) * b * np.cos(k * X),
+         lam1(m, h) * c * np.cos(m * X))
+    uxB = (U[1] * B[2] - U[2] * B[1], U[2] * B[0] - U[0] * B[2], U[0] * B[1] - U[1] * B[0])
+    jxB = (j[1] * B[2] - j[2] * B[1], j[2] * B[0] - j[0] * B[2], j[0] * B[1] - j[1] * B[0])
+    rho = np.exp(l0)
+    _, T = _temp(p, l0, 0.0)
+    exp = np.zeros_like(f)
+    for cidx in range(3):
+        exp[UX + cidx] = jxB[cidx] / rho
+        exp[AX + cidx] = uxB[cidx] + p.eta * lapA[cidx]
+    exp[SS] = p.eta * p.mu0 * (j[0] ** 2 + j[1] ** 2 + j[2] ** 2) / (rho * T)
+    _check(oracle.mhd_rhs(f, p), exp)
+
+
 @pytest.mark.parametrize("dt", [0.1, 0.3])
 def test_rk3_stability_polynomial_on_beltrami_field(dt):
     p = _par(eta=0.5)
