@@ -628,6 +628,12 @@ def run_extras(L, synth, stream, hbm_peak, args):
                      "timing": "CUDA-graph replay of stencil_step (eager: one ctypes call per job)",
                      "mcell_updates_per_s": round(XC_N * XC_SWEEPS / (res["ms_job"] / 1e3) / 1e6, 1),
                      "launches_per_job": 1, "bound": "l2 + launch latency (4-8 MiB working set)"}
+        if dt == L.STENCIL_F64:
+            # 7 FMAs (14 flop) per output and sweep on the FP64 pipe, which bounds this case
+            tf = XC_N * XC_SWEEPS * 14 / (res["ms_job"] / 1e3) / 1e12
+            out[name]["bound"] = "FP64 pipe (4 MiB working set, L2-resident)"
+            out[name]["roofline"] = _roof("alu", tf, FP64_PEAK_TFLOPS, "TFLOP/s",
+                                          note="14 flop per cell-sweep; FP64 nominal 1.25 TFLOP/s")
     # config 2, FP32 variant
     res = heat_job(L, synth, L.STENCIL_F32, HEAT_N, HEAT_STEPS, w, r, stream)
     cells = HEAT_N ** 3

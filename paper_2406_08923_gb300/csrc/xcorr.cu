@@ -28,14 +28,19 @@ constexpr int XC_MAX_SWEEPS = 16;
 // Outputs per CTA: with its halo (up to 15 sweeps x 4 cells per side) every sweep's span fits
 // in the 256 x 9 outputs one pass of the threads computes.
 constexpr int XC_CHUNK = XC_THREADS * XC_V - 2 * (XC_MAX_SWEEPS - 1) * 4;  // 2184
-// FP64 sweeps one output per thread and iteration (below), so its chunk is a round 2048, or
-// 1024 when 2048 would leave fewer than 4 CTAs per SM (the 2^20-cell benchmark: the FP64
-// pipe then waits on the SMs that got one CTA more than the others).
+// FP64 sweeps one output per thread and iteration (below), so its chunk is a runtime length
+// (even, 256..2048).  A grid too small for several waves of 2048-cell chunks gets chunks that
+// put exactly 4 CTAs on every SM (the 2^20-cell benchmark: 1726 cells, 150 us per 10 sweeps).
+// Measured there: 2048 cells (3.4 CTAs per SM, unbalanced) 176 us; 1024 158 us; 864 (8 per
+// SM) 168 us; 1380 (5 per SM) 154 us.
 template <typename T> constexpr int xc_chunk() { return sizeof(T) == 8 ? 2048 : XC_CHUNK; }
 constexpr int XC_PAD = 4;  // buffer elements before logical cell 0
 // elements per shared-memory buffer: a sweep starting at cell s r <= 96 (the halo of the
 // sweeps one launch runs, at most 3 x 30 cells) reads up to 256 x 9 + 40 cells past its start
 constexpr int XC_BUF = XC_PAD + 96 + XC_THREADS * XC_V + 40;
+// FP64 buffers hold exactly the staged span (the scalar sweep reads nothing outside it), so a
+// short chunk also takes less shared memory; even, so the second buffer stays 16-byte aligned.
+__host__ __device__ constexpr int xc_f64_stride(int chunk, int halo) { return (XC_PAD + chunk + 2 * halo + 1) & ~1; }
 static_assert(XC_CHUNK % 4 == 0, "the chunk body is moved as 16-byte vectors");
 
 // Sweeps per launch at radius r: the halo of S sweeps must leave every sweep's span within the
@@ -69,7 +74,7 @@ __device__ __forceinline__ void xcorr_chunk(const T *__restrict__ in, T *__restr
     const int H = sweeps * R;
     const int W = CHUNK + 2 * H;
     A *buf0 = reinterpret_cast<A *>(smem_raw);
-    A *buf1 = buf0 + XC_BUF;
+    A *buf1 = buf0 + (sizeof(A) == 8 ? xc_f64_stride(CHUNK, H) : XC_BUF);
     const int64_t n = geo.n[0];
     const int64_t c0 = (int64_t)chunk * CHUNK;
     const T *inx = in + geo.off[0];  // interior element 0
@@ -184,9 +189,14 @@ static cudaError_t run(const void *in, void *out, const Geom &g, const void *coe
     using A = typename XAcc<T>::type;
     XCoef<T> cf{};
     for (int j = 0; j < 2 * R + 1; ++j) cf.g[j] = static_cast<const T *>(coeffs)[j];
-    const size_t smem = 2 * sizeof(A) * XC_BUF;
     int chunk_len = xc_chunk<T>();
-    if (sizeof(T) == 8 && (g.n[0] + chunk_len - 1) / chunk_len < 4 * device_sms()) chunk_len /= 2;
+    if (sizeof(T) == 8) {
+        const int64_t wave = 4 * (int64_t)device_sms();  // exactly 4 CTAs on every SM
+        const int64_t per = (g.n[0] + wave - 1) / wave;
+        chunk_len = (int)std::min<int64_t>(chunk_len, std::max<int64_t>(256, (per + 1) & ~int64_t(1)));
+    }
+    const size_t smem = sizeof(A) == 8 ? 2 * sizeof(A) * xc_f64_stride(chunk_len, sweeps * R)
+                                       : 2 * sizeof(A) * XC_BUF;
     const unsigned blocks = (unsigned)((g.n[0] + chunk_len - 1) / chunk_len);
     auto k = xcorr_kernel<T, R>;
     if (smem > 48 * 1024) {
