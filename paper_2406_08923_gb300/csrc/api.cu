@@ -704,12 +704,16 @@ static int num_variants(stencil_t p) {
 static const char *variant_name(stencil_t p, int v) {
     if (p->kind == STENCIL_MAXFILTER) return "doubling_chunk4096";
     if (p->kind == STENCIL_XCORR && !xcorr_blocked(p)) return "wide_register_blocked";
-    if (p->kind == STENCIL_DIFFUSION && p->ndim == 1) return "xcorr_folded_chunk2184_v9_temporal_blocking";
+    // FP64 sweeps one output per thread over a runtime chunk length; the other types use
+    // 2184-cell chunks and 9-output register windows
+    const bool f64 = p->storage == STENCIL_F64;
+    if (p->kind == STENCIL_DIFFUSION && p->ndim == 1)
+        return f64 ? "xcorr_folded_runtime_chunk_scalar_temporal_blocking" : "xcorr_folded_chunk2184_v9_temporal_blocking";
     if (p->kind == STENCIL_DIFFUSION && p->ndim == 2)
         return v == 1 ? "stream2d_tb2" : v == 2 ? "stream2d_tb4" : "tile2d_32vx_by8_ry4";
     if (p->kind == STENCIL_DIFFUSION) return diffusion_variant_name(storage_code(p->storage), p->radius, v);
     if (p->kind == STENCIL_MHD8) return mhd_variant_name(storage_code(p->storage), v);
-    return "chunk2184_v9_temporal_blocking";
+    return f64 ? "runtime_chunk_scalar_temporal_blocking" : "chunk2184_v9_temporal_blocking";
 }
 
 stencil_status stencil_get_variant(stencil_t p, int *variant, int *count, const char **name) {
