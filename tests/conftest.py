@@ -7,14 +7,18 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-# Planted-mistake runs (test_oracle_mistakes.py) point the oracle package at a mutated copy of
-# its C source, compiled beforehand into a temporary directory.  Unset in every other run.
-_MUTANT_SRC = os.environ.get("STENCIL_ORACLE_MUTANT_SRC")
-if _MUTANT_SRC:
-    import oracle as _oracle
+# Planted-mistake runs (test_oracle_mistakes.py) replace the oracle package by a copy in a
+# temporary directory (its wrapper or its C source mutated, the library compiled beforehand).
+# Unset in every other run.
+_MUTANT_PKG = os.environ.get("STENCIL_ORACLE_MUTANT_PKG")
+if _MUTANT_PKG:
+    import importlib.util
 
-    _oracle._SRC = _MUTANT_SRC
-    _oracle._LIB = os.path.splitext(_MUTANT_SRC)[0] + ".so"
+    _spec = importlib.util.spec_from_file_location("oracle", os.path.join(_MUTANT_PKG, "__init__.py"),
+                                                   submodule_search_locations=[_MUTANT_PKG])
+    _mod = importlib.util.module_from_spec(_spec)
+    sys.modules["oracle"] = _mod
+    _spec.loader.exec_module(_mod)
 
 
 def pytest_configure(config):

@@ -116,6 +116,22 @@ def test_anisotropic_spacing_scaling():
     np.testing.assert_allclose(d[6:9], np.broadcast_to(np.array([-1.0, 0.0, 3.0])[:, None, None, None], d[6:9].shape), atol=1e-9)
 
 
+def test_non_cubic_box_keeps_axis_order():
+    # interior (nz, ny, nx) = (5, 7, 9): every derivative plane comes back as (nz, ny, nx)
+    hs = (0.3, 0.5, 0.7)
+    ext = (9, 7, 5)  # nx, ny, nz
+    c = [np.arange(m + 6) * hh for m, hh in zip(ext, hs)]
+    Z, Y, X = np.meshgrid(c[2], c[1], c[0], indexing="ij")
+    f = X ** 3 - 2 * X * Y + Y * Z ** 2
+    d = oracle.derivs_box(f, hs)
+    assert d.shape == (9, 5, 7, 9)
+    sl = (slice(3, -3),) * 3
+    X, Y, Z = X[sl], Y[sl], Z[sl]
+    exp = (3 * X ** 2 - 2 * Y, -2 * X + Z ** 2, 2 * Y * Z, 6 * X, 0 * X, 2 * Y, -2 + 0 * X, 0 * X, 2 * Z)
+    for q, e in enumerate(exp):
+        np.testing.assert_allclose(d[q], e, atol=1e-9, err_msg=NAMES[q])
+
+
 def test_convergence_order_six():
     errs = []
     ns = (16, 32, 64)

@@ -169,6 +169,23 @@ def test_grad_div_A_in_current():
     _check(oracle.mhd_rhs(f, p), exp)
 
 
+def test_grid_spacing_per_axis_on_a_non_cubic_grid():
+    # (nz, ny, nx) = (12, 16, 20): every axis has its own spacing 2 pi / n_axis, so a density
+    # mode along x and one along z each give the pressure force with their own symbol.
+    nz, ny, nx = 12, 16, 20
+    base = dict(cs0=1.3, gamma=5.0 / 3.0, cp=1.7, lnrho0=0.3, nu=0.02, eta=0.03, zeta=0.05, mu0=1.5)
+    p = MhdParams.for_grid((nz, ny, nx), **base)
+    Z, Y, X = np.meshgrid(*(2 * np.pi * np.arange(m) / m for m in (nz, ny, nx)), indexing="ij")
+    kx, kz, eps = 3, 2, 1e-2
+    f = np.zeros((8, nz, ny, nx))
+    f[LNRHO] = eps * np.sin(kx * X) + eps * np.sin(kz * Z)
+    cs2, _ = _temp(p, f[LNRHO], 0.0)
+    exp = np.zeros_like(f)
+    exp[UX] = -cs2 * lam1(kx, 2 * np.pi / nx) * eps * np.cos(kx * X)
+    exp[UZ] = -cs2 * lam1(kz, 2 * np.pi / nz) * eps * np.cos(kz * Z)
+    _check(oracle.mhd_rhs(f, p), exp)
+
+
 def test_entropy_advection_by_a_uniform_flow():
     # u uniform, lnrho uniform, s = eps sin(k x): A3 reduces to ds/dt = -u . grad s (no shear, no
     # current), A2 to the entropy part of the pressure term, A1 and A4 to zero.

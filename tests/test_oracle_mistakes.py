@@ -1,12 +1,14 @@
 """Planted mistakes in the oracle: each one must fail at least one of the oracle's pins.
 
-Every case is a plausible slip in oracle/oracle.c: a dropped term, a wrong sign, a transposed
-operand or index, a wrong constant, an off-by-one window.  The test writes the mutated source
-into a temporary directory, compiles it there, and runs the oracle's pin tests
-(tests/test_oracle_*.py, this file excluded) in a subprocess with STENCIL_ORACLE_MUTANT_SRC
-pointing the oracle package at it (conftest.py reads the variable).  A mutant that passes every
-pin would be a mistake the pins cannot tell from the paper's arithmetic.  The committed source
-is only read.  Everything runs on the host.
+Every case is a plausible slip in the oracle: in its C arithmetic (oracle/oracle.c: a dropped
+term, a wrong sign, a transposed operand or index, a wrong constant, an off-by-one window) or
+in its Python wrapper (oracle/__init__.py: axis order, array shapes, parameter order, integer
+masking).  The test copies the package into a temporary directory with the one mistake in
+it, compiles the copy's library there, and runs the oracle's pin tests
+(tests/test_oracle_*.py, this file excluded) in a subprocess with STENCIL_ORACLE_MUTANT_PKG
+naming the copy (conftest.py loads it in place of the package).  A mistake that passes every
+pin would be one the pins cannot tell from the paper's arithmetic.  The committed oracle is
+only read.  Everything runs on the host.
 """
 import glob
 import os
@@ -21,6 +23,7 @@ import oracle
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = os.path.join(ROOT, "oracle", "oracle.c")
+PY = os.path.join(ROOT, "oracle", "__init__.py")
 PIN_FILES = sorted(f for f in glob.glob(os.path.join(HERE, "test_oracle_*.py"))
                    if os.path.basename(f) != os.path.basename(__file__))
 
@@ -133,24 +136,53 @@ MUTANTS = [
 ]
 
 
+# The same for the Python wrapper.  None of these makes the C code read or write outside the
+# arrays the wrapper allocates: a changed shape keeps the element count, or enlarges the array.
+PY_MUTANTS = [
+    ("py_dims_reversed", "return s[2], s[1], s[0]", "return s[0], s[1], s[2]"),
+    ("py_pad_halo_on_unit_axes", "h = lambda n: n + 2 * r if n > 1 else 1", "h = lambda n: n + 2 * r"),
+    ("py_xcorr_box_mask_31_bits", "fh = _c(np.asarray(fhat).astype(np.int64) & 0xFFFFFFFF, np.uint32)",
+     "fh = _c(np.asarray(fhat).astype(np.int64) & 0x7FFFFFFF, np.uint32)"),
+    ("py_xcorr_mask_31_bits", "d = _c(np.asarray(data).astype(np.int64) & 0xFFFFFFFF, np.uint32)",
+     "d = _c(np.asarray(data).astype(np.int64) & 0x7FFFFFFF, np.uint32)"),
+    ("py_xcorr_box_radius", "r = (len(g) - 1) // 2\n    n = len(fhat) - 2 * r", "r = (len(g) - 1) // 2 - 1\n    n = len(fhat) - 2 * r"),
+    ("py_params_nu_eta_swapped", "self.nu, self.eta, self.zeta", "self.eta, self.nu, self.zeta"),
+    ("py_for_grid_axis_order", "nz, ny, nx = (n, n, n) if np.isscalar(n) else tuple(n)",
+     "nx, ny, nz = (n, n, n) if np.isscalar(n) else tuple(n)"),
+    ("py_mhd_rhs_shape_transposed", "out = np.empty((8, nz, ny, nx), dtype=np.float64)",
+     "out = np.empty((8, nx, ny, nz), dtype=np.float64)"),
+    ("py_derivs_shape_transposed", "out = np.empty((9, nz, ny, nx), dtype=np.float64)",
+     "out = np.empty((9, nx, ny, nz), dtype=np.float64)"),
+    ("py_rk3_in_place", "f = _c(f8, np.float64).copy()\n    nz, ny, nx = f.shape[1:]",
+     "f = _c(f8, np.float64)\n    nz, ny, nx = f.shape[1:]"),
+    ("py_diffusion_spacing_reversed", "rc = _load().oracle_diffusion(_p(f), nx, ny, nz, dt, alpha, _p(_c(h, np.float64)), steps,",
+     "rc = _load().oracle_diffusion(_p(f), nx, ny, nz, dt, alpha, _p(_c(h[::-1], np.float64)), steps,"),
+]
+
+CASES = [("c",) + m for m in MUTANTS] + [("py",) + m for m in PY_MUTANTS]
+
+
 def test_every_mutant_applies_exactly_once():
-    src = open(SRC).read()
-    names = [m[0] for m in MUTANTS]
+    text = {"c": open(SRC).read(), "py": open(PY).read()}
+    names = [m[1] for m in CASES]
     assert len(names) == len(set(names))
-    for name, old, new in MUTANTS:
-        assert src.count(old) == 1, f"{name}: text occurs {src.count(old)} times"
+    for where, name, old, new in CASES:
+        assert text[where].count(old) == 1, f"{name}: text occurs {text[where].count(old)} times"
         assert old != new, name
 
 
-def _run_mutant(tmp, name, old, new):
-    src = open(SRC).read().replace(old, new, 1)
-    d = os.path.join(tmp, name)
+def _run_mutant(tmp, where, name, old, new):
+    """Copy the package with one mistake into tmp/name/oracle, compile it, run the pins."""
+    d = os.path.join(tmp, name, "oracle")
     os.makedirs(d)
-    path = os.path.join(d, "oracle.c")
-    with open(path, "w") as fh:
-        fh.write(src)
-    oracle.build(force=True, src=path, lib=os.path.join(d, "oracle.so"))  # must compile
-    env = dict(os.environ, STENCIL_ORACLE_MUTANT_SRC=path, OMP_NUM_THREADS="1")
+    for path, kind in ((SRC, "c"), (PY, "py")):
+        text = open(path).read()
+        if kind == where:
+            text = text.replace(old, new, 1)
+        with open(os.path.join(d, os.path.basename(path)), "w") as fh:
+            fh.write(text)
+    oracle.build(force=True, src=os.path.join(d, "oracle.c"), lib=os.path.join(d, "liboracle.so"))  # must compile
+    env = dict(os.environ, STENCIL_ORACLE_MUTANT_PKG=d, OMP_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu",
                         *PIN_FILES], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     return name, r.returncode, r.stdout[-1500:]
@@ -159,7 +191,7 @@ def _run_mutant(tmp, name, old, new):
 def test_every_planted_mistake_fails_a_pin(tmp_path):
     workers = max(1, min(8, os.cpu_count() or 1))
     with ThreadPoolExecutor(workers) as ex:
-        results = list(ex.map(lambda m: _run_mutant(str(tmp_path), *m), MUTANTS))
+        results = list(ex.map(lambda m: _run_mutant(str(tmp_path), *m), CASES))
     survivors = [n for n, rc, _ in results if rc == 0]
     broken = [(n, rc, out) for n, rc, out in results if rc not in (0, 1)]
     assert not broken, broken
@@ -169,5 +201,6 @@ def test_every_planted_mistake_fails_a_pin(tmp_path):
 def test_unmutated_copy_passes_every_pin(tmp_path):
     """The harness itself: the same run on an unmodified copy passes, so a failing mutant
     fails because of its mistake."""
-    name, rc, out = _run_mutant(str(tmp_path), "unmodified", "", "")
+    name, rc, out = _run_mutant(str(tmp_path), "c", "unmodified", "", "")
     assert rc == 0, out
+    assert "passed" in out

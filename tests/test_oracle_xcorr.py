@@ -33,6 +33,16 @@ def test_int32_wraps_like_twos_complement():
     assert np.array_equal(oracle.xcorr1d(data, g, 4), _brute_u32(data, g, 4))
 
 
+def test_int32_box_sweep_with_caller_halo_wraps_like_twos_complement():
+    # one sweep over a caller-filled int32 box (no periodic wrap): negative and extreme values
+    fhat = np.array([-2**31, 2**31 - 1, -1, 5, -77777777, 2**30 + 3, -6, 99, -2**29, 12], dtype=np.int32)
+    g = np.array([-8, 7, 5, -3, 2], dtype=np.int32)
+    r, n = 2, len(fhat) - 4
+    exp = [sum(int(g[j + r]) * int(fhat[i + r + j]) for j in range(-r, r + 1)) & 0xFFFFFFFF for i in range(n)]
+    exp = np.array(exp, dtype=np.uint64).astype(np.uint32).view(np.int32)
+    assert np.array_equal(oracle.xcorr1d_box(fhat, g), exp)
+
+
 def test_f64_matches_scipy_correlate1d_wrap():
     x = synth.xcorr_f64(257, seed=5)
     g = np.array([1 / 90, -3 / 20, 3 / 2, -49 / 18, 3 / 2, -3 / 20, 1 / 90])
@@ -73,3 +83,11 @@ def test_pad_periodic_3d_matches_numpy_wrap():
     np.testing.assert_array_equal(oracle.pad_periodic(f), np.pad(f, 3, mode="wrap"))
     f1 = synth.uniform(4, 2, 9)
     np.testing.assert_array_equal(oracle.pad_periodic(f1), np.pad(f1, 3, mode="wrap"))
+
+
+def test_pad_periodic_leaves_unit_axes_unpadded():
+    # an axis of extent 1 carries no halo (a 2D field stored as a 3D array)
+    f = synth.uniform(4, 3, 6 * 8).reshape(1, 6, 8)
+    np.testing.assert_array_equal(oracle.pad_periodic(f), np.pad(f, ((0, 0), (3, 3), (3, 3)), mode="wrap"))
+    g = synth.uniform(4, 4, 5 * 7).reshape(5, 1, 7)
+    np.testing.assert_array_equal(oracle.pad_periodic(g, 2), np.pad(g, ((2, 2), (0, 0), (2, 2)), mode="wrap"))
