@@ -1,0 +1,100 @@
+"""Shared-memory bounds of the temporally blocked cross-correlation kernel, checked on the host.
+
+The kernel (csrc/xcorr.cu) stages a chunk plus a halo of sweeps x r cells per side in a
+shared-memory buffer and runs the sweeps there.  This test reads the kernel's constants from
+its source and restates its index ranges, then checks for every radius and sweep count the
+host accepts:
+* the staged span fits the buffer;
+* every register-window read and every output write of every sweep stays in the buffer
+  (int32 / FP32: 256 threads x 9 outputs from windows of 9 + 2r cells);
+* one pass of the threads covers the whole valid span of every sweep;
+* FP64 (one output per thread, runtime chunk length): the chunk is even and 256..2048, its
+  buffers hold the staged span, and the launch fits in shared memory.
+The sweep-count rule is restated too; the test fails if its source text changes, so the
+restatement is updated with it.
+"""
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = open(os.path.join(ROOT, "paper_2406_08923_gb300", "csrc", "xcorr.cu")).read()
+
+
+def _const(name):
+    m = re.search(r"constexpr int %s = ([^;]+);" % name, SRC)
+    assert m, name
+    expr = m.group(1).split("//")[0]
+    env = {k: _const(k) for k in re.findall(r"\bXC_[A-Z_]+\b", expr)}
+    return int(eval(expr, {"__builtins__": {}}, env))
+
+
+T, V, MAXS, PAD = _const("XC_THREADS"), _const("XC_V"), _const("XC_MAX_SWEEPS"), _const("XC_PAD")
+CHUNK, BUF = _const("XC_CHUNK"), _const("XC_BUF")
+SMEM_MAX = 227 * 1024
+
+
+def max_sweeps(r):
+    # xcorr_max_sweeps_per_launch
+    return MAXS if r <= 4 else min(MAXS, 1 + 60 // r)
+
+
+def test_sweep_rule_source_is_the_restated_one():
+    assert "return r <= 4 ? XC_MAX_SWEEPS : std::min(XC_MAX_SWEEPS, 1 + 60 / r);" in SRC
+    assert (T, V, MAXS, PAD, CHUNK, BUF) == (256, 9, 16, 4, 2184, 2444)
+
+
+def test_window_kernel_stays_in_its_buffers():
+    # int32 and FP32 at r = 0..4; FP32 also at r = 5..32
+    for r in range(0, 33):
+        for sweeps in range(1, max_sweeps(r) + 1):
+            H = sweeps * r
+            W = CHUNK + 2 * H
+            assert PAD + W <= BUF, (r, sweeps)  # staging writes buf[PAD + e], e < W
+            for s in range(1, sweeps + 1):
+                q_first, q_last = s * r, s * r + V * (T - 1)
+                lo_read = PAD + q_first - r
+                hi_read = PAD + q_last - r + (V + 2 * r) - 1
+                hi_write = PAD + q_last + V - 1
+                assert 0 <= lo_read and hi_read < BUF and hi_write < BUF, (r, sweeps, s)
+                # the valid span [s r, W - s r) is covered by one pass of the threads
+                assert W - s * r <= q_last + V, (r, sweeps, s)
+            # the result read back: res[p] = src[PAD + H + p], p < CHUNK
+            assert PAD + H + CHUNK - 1 < BUF
+
+
+def f64_chunk(n, sms):
+    # run<double>: exactly 4 CTAs per SM on small grids, 2048 otherwise, even, >= 256
+    wave = 4 * sms
+    per = (n + wave - 1) // wave
+    return min(2048, max(256, (per + 1) & ~1))
+
+
+def f64_stride(chunk, halo):
+    # xc_f64_stride
+    return (PAD + chunk + 2 * halo + 1) & ~1
+
+
+def test_f64_chunks_and_buffers():
+    assert "chunk_len = (int)std::min<int64_t>(chunk_len, std::max<int64_t>(256, (per + 1) & ~int64_t(1)));" in SRC
+    assert "return (XC_PAD + chunk + 2 * halo + 1) & ~1;" in SRC
+    sizes = [1, 7, 255, 256, 4099, 5003, 65536, 2 ** 20, 2 ** 20 + 1, 2 ** 21 + 5, 2 ** 24, 2 ** 26 + 3]
+    for sms in (132, 148, 152, 160):
+        for n in sizes:
+            c = f64_chunk(n, sms)
+            assert c % 2 == 0 and 256 <= c <= 2048, (n, sms, c)
+            blocks = (n + c - 1) // c
+            assert blocks * c >= n and (blocks - 1) * c < n
+            if n <= 4 * sms * 2048 and n >= 4 * sms * 256:
+                assert blocks <= 4 * sms
+            for r in range(0, 5):
+                for sweeps in range(1, max_sweeps(r) + 1):
+                    H = sweeps * r
+                    S = f64_stride(c, H)
+                    W = c + 2 * H
+                    assert S % 2 == 0 and PAD + W <= S  # second buffer 16-byte aligned; span fits
+                    for s in range(1, sweeps + 1):
+                        # p in [s r, W - s r), reads p + j for |j| <= r
+                        assert PAD + (s - 1) * r >= 0 and PAD + W - (s - 1) * r <= S
+                    assert 2 * 8 * S <= SMEM_MAX
+    # the 2^20-cell benchmark on 152 SMs: 1726-cell chunks, 608 CTAs
+    assert f64_chunk(2 ** 20, 152) == 1726 and (2 ** 20 + 1725) // 1726 == 608
