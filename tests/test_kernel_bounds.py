@@ -1,6 +1,6 @@
-"""Shared-memory bounds of the temporally blocked cross-correlation kernel, checked on the host.
+"""Shared-memory bounds of the temporally blocked kernels, checked on the host.
 
-The kernel (csrc/xcorr.cu) stages a chunk plus a halo of sweeps x r cells per side in a
+The 1D cross-correlation kernel (csrc/xcorr.cu) stages a chunk plus a halo of sweeps x r cells per side in a
 shared-memory buffer and runs the sweeps there.  This test reads the kernel's constants from
 its source and restates its index ranges, then checks for every radius and sweep count the
 host accepts:
@@ -12,6 +12,9 @@ host accepts:
   buffers hold the staged span, and the launch fits in shared memory.
 The sweep-count rule is restated too; the test fails if its source text changes, so the
 restatement is updated with it.
+
+The 2D heat kernel (csrc/diffusion2d_tb.cu) keeps per-warp rings of rows: its x-neighbour
+reads, its prefetch slots and its ring depths are checked for K = 2, 4 and r = 1..4.
 """
 import os
 import re
@@ -98,3 +101,40 @@ def test_f64_chunks_and_buffers():
                     assert 2 * 8 * S <= SMEM_MAX
     # the 2^20-cell benchmark on 152 SMs: 1726-cell chunks, 608 CTAs
     assert f64_chunk(2 ** 20, 152) == 1726 and (2 ** 20 + 1725) // 1726 == 608
+
+
+# ---------------------------------------------------------------------------------------------
+# 2D temporally blocked heat kernel (csrc/diffusion2d_tb.cu): per-warp rings in shared memory.
+
+TB_SRC = open(os.path.join(ROOT, "paper_2406_08923_gb300", "csrc", "diffusion2d_tb.cu")).read()
+
+
+def tb_g(K, s, R):
+    return tb_g(K, 1, R) + 1 if s == 0 else ((K - s) * R + 3) // 4
+
+
+def test_blocked_2d_rings_stay_in_bounds():
+    assert "return s == 0 ? tb_g(K, 1, R) + 1 : ((K - s) * R + 3) / 4;" in TB_SRC
+    assert "constexpr int TB_WARPS = 4;" in TB_SRC
+    for K in (2, 4):  # the step counts launch_diffusion2d_tb accepts
+        for R in range(1, 5):
+            G0, G1 = tb_g(K, 0, R), tb_g(K, 1, R)
+            TXG, NQ = 32 - 2 * G1, 2 * R + 1
+            W, NL, P = TXG + 2 * G0, 2 * NQ, min(3 * R + 1, 7)
+            ring0, ringi = NL * W * 4, NQ * W * 4
+            warp_floats = ring0 + (K - 1) * ringi
+            assert TXG >= 8 and W <= 64 and P + R < NL, (K, R)
+            assert 4 * warp_floats * 4 <= SMEM_MAX, (K, R)
+            # f_0 fetch: a lane writes groups lane and (if lane + 32 < W) lane + 32 of its row
+            assert max(lane + 32 * h for lane in range(32) for h in range(2) if lane + 32 * h < W) == W - 1
+            for S in range(1, K + 1):
+                GS = tb_g(K, S, R)
+                active = TXG + 2 * GS
+                assert active <= 32, (K, R, S)
+                q = [lane - GS + G0 for lane in range(active)]
+                # x neighbours: groups q - 1 .. q + 1 of the stage's input row
+                assert min(q) - 1 >= 0 and max(q) + 1 <= W - 1, (K, R, S)
+                # the row of stage S - 1 that stage S reads R rows later is still in its ring
+                assert R < (NL if S == 1 else NQ)
+            # prefetching row j + P overwrites row j + P - NL, older than the oldest row in use
+            assert P - NL < -R
