@@ -15,6 +15,10 @@ restatement is updated with it.
 
 The 2D heat kernel (csrc/diffusion2d_tb.cu) keeps per-warp rings of rows: its x-neighbour
 reads, its prefetch slots and its ring depths are checked for K = 2, 4 and r = 1..4.
+
+TMA: every tiled load of the heat and MHD kernels starts at an x coordinate whose byte
+offset is a multiple of 16, with a box inner extent that is a multiple of 16 bytes, for every
+dtype, tile width and radius; no kernel issues a tiled store.
 """
 import os
 import re
@@ -138,3 +142,50 @@ def test_blocked_2d_rings_stay_in_bounds():
                 assert R < (NL if S == 1 else NQ)
             # prefetching row j + P overwrites row j + P - NL, older than the oldest row in use
             assert P - NL < -R
+
+
+# ---------------------------------------------------------------------------------------------
+# TMA tile loads (heat 2D/3D, MHD): the innermost coordinate of every tiled load, times the
+# element size, is a multiple of 16 bytes, and so is the box's inner extent.
+
+CSRC = os.path.join(ROOT, "paper_2406_08923_gb300", "csrc")
+
+
+def _read(name):
+    return open(os.path.join(CSRC, name)).read()
+
+
+def test_tma_loads_start_on_16_byte_boundaries():
+    api, common = _read("api.cu"), _read("common.cuh")
+    # every TMA access is a load (no tiled store or reduce, so no negative store coordinates)
+    tensor_ops = re.findall(r'"(cp\.async\.bulk\.tensor[^"]*)"', common)
+    assert tensor_ops and all(".shared::cluster.global." in op for op in tensor_ops), tensor_ops
+    # x origin of the padded layout: the radius rounded up to 16 bytes; rows padded to 32 bytes
+    assert "const int64_t xoff = ((radius + v16 - 1) / v16) * v16;" in api
+    assert "g.pad[0] = ((xoff + g.n[0] + xoff + align32 - 1) / align32) * align32;" in api
+    # each kernel's load: x = off[0] + tile_x * TX - HX
+    for f in ("diffusion.cu", "diffusion_f32.cu", "mhd.cu"):
+        assert "const int bx = (int)g.off[0] + x0 - Cfg::HX" in _read(f), f
+    assert "(int)g.off[0] + x0 - Cfg::HX" in _read("diffusion2d.cu")
+    assert "static constexpr int HX = 4;" in _read("diffusion.cu")
+    assert "TX = 128, HX = 4" in _read("diffusion_f32.cu")
+    assert "TX = 32 * VX, HX = 4" in _read("diffusion2d.cu")
+    assert "HX = 16 / (int)sizeof(S) >= 4 ? 16 / (int)sizeof(S) : 4;" in _read("mhd.cu")
+    families = []  # (esize, HX, tile widths, radii)
+    families.append((8, 4, [64, 128], range(1, 5)))            # 3D heat FP64 (TX = 64 VP)
+    families.append((4, 4, [128], range(1, 5)))                 # 3D heat FP32
+    families += [(e, 4, [32 * vx for vx in (1, 2, 4)], range(1, 5)) for e in (4, 8)]  # 2D heat
+    families += [(e, max(16 // e, 4), [16, 32], [3]) for e in (8, 4, 2)]              # MHD
+    for esize, hx, txs, radii in families:
+        for r in radii:
+            assert hx >= r  # the x halo in shared memory covers the stencil
+            v16 = 16 // esize
+            xoff = (r + v16 - 1) // v16 * v16
+            for tx in txs:
+                assert (tx + 2 * hx) * esize % 16 == 0, (esize, tx)  # box inner extent
+                for tile in range(4):
+                    x = xoff + tile * tx - hx
+                    assert x * esize % 16 == 0, (esize, hx, tx, r, tile)
+                for n in (7, 8, 100, 256, 383):
+                    pad = (2 * xoff + n + 32 // esize - 1) // (32 // esize) * (32 // esize)
+                    assert pad * esize % 32 == 0 and pad >= xoff + n + r
