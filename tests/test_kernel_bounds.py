@@ -16,6 +16,10 @@ restatement is updated with it.
 The 2D heat kernel (csrc/diffusion2d_tb.cu) keeps per-warp rings of rows: its x-neighbour
 reads, its prefetch slots and its ring depths are checked for K = 2, 4 and r = 1..4.
 
+The wide cross-correlation and the max filter (csrc/xcorr_wide.cu) stage chunks by 1D bulk
+copies: copy sizes and buffer starts are 16-byte multiples, and every read of the register
+blocks and of the doubling passes stays in its buffer, for every accepted radius.
+
 TMA: every tiled load of the heat and MHD kernels starts at an x coordinate whose byte
 offset is a multiple of 16, with a box inner extent that is a multiple of 16 bytes, for every
 dtype, tile width and radius; no kernel issues a tiled store.
@@ -189,3 +193,54 @@ def test_tma_loads_start_on_16_byte_boundaries():
                 for n in (7, 8, 100, 256, 383):
                     pad = (2 * xoff + n + 32 // esize - 1) // (32 // esize) * (32 // esize)
                     assert pad * esize % 32 == 0 and pad >= xoff + n + r
+
+
+# ---------------------------------------------------------------------------------------------
+# Wide cross-correlation and max filter (csrc/xcorr_wide.cu): bulk-copied staging buffers.
+
+WIDE_SRC = _read("xcorr_wide.cu")
+
+
+def _roundup(a, m):
+    return (a + m - 1) // m * m
+
+
+def test_wide_kernels_stay_in_their_buffers():
+    for text in ("constexpr int WT = 256;", "constexpr int MF_CHUNK = 4096;",
+                 "constexpr int WIDE_V_F32[] = {9, 11, 13, 15};", "constexpr int WIDE_V_F64[] = {5, 7, 9};",
+                 "return (2 * rr(r) + CH + nwp(r) + V + L - 1) / L * L;", "return (2 * r + 1 + V - 1) / V * V;",
+                 "return (MF_CHUNK + 2 * rr(r) + L - 1) / L * L;", "inline int maxf_nbuf(int r) { return r == 0 ? 2 : 1; }"):
+        assert text in WIDE_SRC, text
+    wt, mf = 256, 4096
+    # cross-correlation: FP32 at r = 33..1024, FP64 at r = 5..1024
+    for esize, vs, radii in ((4, (9, 11, 13, 15), range(33, 1025)), (8, (5, 7, 9), range(5, 1025))):
+        L = 16 // esize
+        for V in vs:
+            ch = wt * V
+            assert ch * esize % 16 == 0  # chunk starts c * CH stay 16-byte aligned
+            for r in radii:
+                rr, nwp = _roundup(r, L), _roundup(2 * r + 1, V)
+                be, wlen = _roundup(2 * rr + ch + nwp + V, L), _roundup(nwp, L)
+                assert be % L == 0 and wlen % L == 0  # every buffer starts 16-byte aligned
+                assert (ch + 2 * rr) * esize % 16 == 0 and ch + 2 * rr <= be  # the bulk copy
+                lead, span = rr - r, ch + 2 * r
+                assert lead + span + (rr - r) - 1 < be  # zeroed tail past the span
+                # reads s[base + j0 + q]: base <= (WT-1) V, j0 <= nwp - V, q <= 2V - 2
+                assert lead + (wt - 1) * V + (nwp - V) + (2 * V - 2) < be
+                assert esize * (wlen + be) <= SMEM_MAX  # one staging buffer always fits
+    # max filter: int32 / FP32 / FP64 at r = 0..1024, nbuf staging buffers + 1 work buffer
+    for esize in (4, 8):
+        L = 16 // esize
+        for r in range(0, 1025):
+            rr = _roundup(r, L)
+            be = _roundup(mf + 2 * rr, L)
+            lead, span, w = rr - r, mf + 2 * r, 2 * r + 1
+            assert (mf + 2 * rr) * esize % 16 == 0 and mf + 2 * rr <= be
+            assert lead + span - 1 < be
+            length = 1
+            while 2 * length <= w:
+                assert (span - 2 * length) + length < span  # a[i + len], i <= span - 2 len
+                length *= 2
+            assert (mf - 1) + (w - length) <= span - length  # the last read is a defined run
+            nbuf = 2 if r == 0 else 1
+            assert (nbuf + 1) * be * esize <= SMEM_MAX
