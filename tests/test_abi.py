@@ -1,5 +1,7 @@
 """Host-side checks of the C ABI: the library loads without a GPU, exports every symbol that
-include/stencil.h declares, and rejects invalid arguments before touching the device."""
+include/stencil.h declares, and rejects invalid arguments before touching the device.  The
+ctypes binding agrees with the header: argument counts, result kinds, enumerator values, and
+the size and field offsets of the structs (as gcc lays them out)."""
 import ctypes
 import os
 import re
@@ -142,3 +144,57 @@ def test_python_binding_raises_with_detail(lib):
         _lib.stencil_create(3, (5, 16, 16), 3, None, 1, 0, 1, 1, 1, _lib.heat_params(16))
     assert e.value.status == _lib.STENCIL_EINVAL
     assert "2*radius+1" in str(e.value)
+
+
+def _prototypes():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    out = {}
+    for m in re.finditer(r"([\w\s\*]+?)\b(stencil_\w+)\s*\(([^;{}]*?)\)\s*;", src):
+        params = m.group(3).strip()
+        out[m.group(2)] = (" ".join(m.group(1).split()), 0 if params in ("", "void") else params.count(",") + 1)
+    return src, out
+
+
+def test_binding_signatures_match_the_header(lib):
+    # every bound function takes as many arguments as its prototype, with a matching result kind
+    src, protos = _prototypes()
+    assert set(protos) == set(_declared())
+    for name, (ret, nargs) in protos.items():
+        fn = getattr(lib, name)
+        assert len(fn.argtypes) == nargs, (name, len(fn.argtypes), nargs)
+        if ret.endswith("void") and "*" not in ret:
+            assert fn.restype is None, name
+        elif "char" in ret:
+            assert fn.restype is ctypes.c_char_p, name
+        else:
+            assert fn.restype is ctypes.c_int, name
+    # enumerators the binding re-declares carry the header's values
+    for k, v in re.findall(r"\b(STENCIL_[A-Z0-9_]+)\s*=\s*(\d+)", src):
+        if hasattr(_lib, k):
+            assert getattr(_lib, k) == int(v), k
+
+
+def test_binding_structs_match_the_c_layout(tmp_path):
+    # sizes and field offsets of the two structs the ABI passes by pointer, as gcc lays them out
+    fields = {"stencil_params": [f for f, _ in _lib.stencil_params._fields_],
+              "stencil_request": [f for f, _ in _lib.stencil_request._fields_]}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "stencil.h"', "int main(void) {"]
+    for st, fs in fields.items():
+        lines.append(f'printf("%zu\\n", sizeof({st}));')
+        lines += [f'printf("%zu\\n", offsetof({st}, {f}));' for f in fs]
+    lines.append("return 0; }")
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)], check=True)
+    vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    k = 0
+    for st, fs in fields.items():
+        cls = getattr(_lib, st)
+        assert vals[k] == ctypes.sizeof(cls), st
+        k += 1
+        for f in fs:
+            assert vals[k] == getattr(cls, f).offset, (st, f)
+            k += 1
