@@ -271,6 +271,20 @@ def test_rk3_is_third_order_in_time_on_a_nonlinear_state():
     assert np.all(slopes > 2.8) and np.all(slopes < 3.3), slopes
 
 
+def test_rhs_converges_at_sixth_order_under_refinement():
+    # The same smooth fields (sums of sine modes, evaluated on each grid) at n = 24, 48, 96: the
+    # right-hand side at the coarse grid's points changes by a factor ~2^6 per refinement in
+    # every field, conduction included, as the 6th-order differences of Sec. 3.3 require.
+    res = {}
+    for n in (24, 48, 96):
+        p = MhdParams.for_grid(n, nu=0.02, eta=0.03, zeta=0.01, K=0.1)
+        res[n] = oracle.mhd_rhs(synth.mhd_fields(n, seed=5, kmax=2, amp=0.1), p)
+    e1 = np.abs(res[24] - res[48][:, ::2, ::2, ::2]).max(axis=(1, 2, 3))
+    e2 = np.abs(res[48] - res[96][:, ::2, ::2, ::2]).max(axis=(1, 2, 3))
+    slopes = np.log2(e1 / e2)
+    assert np.all(slopes > 5.5) and np.all(slopes < 6.5), slopes
+
+
 def test_box_step_matches_periodic_step():
     n = 12
     p = MhdParams.for_grid(n)
