@@ -207,8 +207,35 @@ def stencil_selftest_wait(h, limit_ns, stream=None):
     _check(load().stencil_selftest_wait(h, int(limit_ns), _stream(stream)), "stencil_selftest_wait", h)
 
 
+_ESIZE = {STENCIL_I32: 4, STENCIL_F64: 8, STENCIL_F32: 4, STENCIL_BF16: 2}
+
+
+def _einval(where, msg):
+    raise StencilError(STENCIL_EINVAL, where, msg)
+
+
 def stencil_field_norms_noalloc(fields, storage, dims, padded, origin, mass_volume, out_dev, stream=None):
-    """Allocation-free norms: results written to the device tensor out_dev (float64)."""
+    """Allocation-free norms: results written to the device tensor out_dev (float64).
+
+    The C entry point only sees addresses, so the tensors are checked here first: out_dev
+    must be a CUDA float64 tensor with room for every result, and each field a CUDA tensor
+    of the storage element size holding at least the whole padded array."""
+    where = "stencil_field_norms_noalloc"
+    need = 3 * len(fields) + (1 if mass_volume > 0 else 0)
+    if str(out_dev.dtype) != "torch.float64":
+        _einval(where, f"out_dev must be float64, not {out_dev.dtype}")
+    if out_dev.numel() < need:
+        _einval(where, f"out_dev holds {out_dev.numel()} elements, {need} needed")
+    npad = int(padded[0]) * int(padded[1]) * int(padded[2])
+    for i, t in enumerate(fields):
+        if storage in _ESIZE and t.element_size() != _ESIZE[storage]:
+            _einval(where, f"fields[{i}] element size {t.element_size()} does not match the storage "
+                           f"type ({_ESIZE[storage]} bytes)")
+        if t.numel() < npad:
+            _einval(where, f"fields[{i}] holds {t.numel()} elements, fewer than the padded array's {npad}")
+    for i, t in enumerate(list(fields) + [out_dev]):
+        if not t.is_cuda:
+            _einval(where, ("out_dev" if i == len(fields) else f"fields[{i}]") + " is not a CUDA tensor")
     p, k = _ptrs(fields)
     d = (ctypes.c_int64 * 3)(*dims)
     pd = (ctypes.c_int64 * 3)(*padded)

@@ -777,8 +777,18 @@ stencil_status stencil_field_norms_noalloc(void *const *fields, int nfields, ste
     if ((int)storage < 0 || (int)storage > 3) return fail(nullptr, STENCIL_EINVAL, "unknown dtype");
     if (!fields || !dims || !padded || !origin || !out_dev)
         return fail(nullptr, STENCIL_EINVAL, "a pointer argument is NULL");
-    for (int q = 0; q < nfields; ++q)
+    // element-aligned fields and an 8-byte aligned result: a misaligned address would fault
+    // in the kernels
+    const int es = esize_of(storage);
+    for (int q = 0; q < nfields; ++q) {
         if (!fields[q]) return fail(nullptr, STENCIL_EINVAL, "fields[" + std::to_string(q) + "] is NULL");
+        if (reinterpret_cast<uintptr_t>(fields[q]) % es != 0)
+            return fail(nullptr, STENCIL_EINVAL,
+                        "fields[" + std::to_string(q) + "] is not aligned to its " + std::to_string(es) +
+                            "-byte element size");
+    }
+    if (reinterpret_cast<uintptr_t>(out_dev) % sizeof(double) != 0)
+        return fail(nullptr, STENCIL_EINVAL, "out_dev is not 8-byte aligned");
     Geom g{};
     for (int a = 0; a < 3; ++a) {
         if (dims[a] < 1 || origin[a] < 0 || padded[a] < origin[a] + dims[a])

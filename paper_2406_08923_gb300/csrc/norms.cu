@@ -23,12 +23,16 @@ template <> __device__ __forceinline__ double to_d<__nv_bfloat16>(__nv_bfloat16 
     return (double)__bfloat162float(v);
 }
 
+// max that propagates NaN (fmax drops it): a field that has gone NaN must report a NaN
+// max |f|, not the largest finite value.
+__device__ __forceinline__ double nanmax(double a, double b) { return (a != a || b != b) ? a + b : fmax(a, b); }
+
 __device__ __forceinline__ void warp_reduce(double &s, double &s2, double &mx, double &ms) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         s += __shfl_xor_sync(0xffffffffu, s, o);
         s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        mx = nanmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         ms += __shfl_xor_sync(0xffffffffu, ms, o);
     }
 }
@@ -53,7 +57,7 @@ norms_pass1(Ptrs8 f, int nfields, Geom g, int mass0, double *partials) {
                 const double v = to_d(p[x]);
                 s += v;
                 s2 += v * v;
-                mx = fmax(mx, fabs(v));
+                mx = nanmax(mx, fabs(v));
                 if (do_mass) ms += exp(v);
             }
         }
@@ -83,12 +87,12 @@ __global__ void norms_pass2(const double *partials, int nblocks, int nfields, do
     double acc = 0.0;
     for (int b = lane; b < nblocks; b += 32) {
         const double v = partials[((int64_t)b * nfields + q) * 4 + c];
-        acc = c == 2 ? fmax(acc, v) : acc + v;
+        acc = c == 2 ? nanmax(acc, v) : acc + v;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const double v = __shfl_xor_sync(0xffffffffu, acc, o);
-        acc = c == 2 ? fmax(acc, v) : acc + v;
+        acc = c == 2 ? nanmax(acc, v) : acc + v;
     }
     if (lane == 0) out[q * 4 + c] = acc;
 }
@@ -136,12 +140,12 @@ __global__ void norms_pass2_packed(const double *partials, int nblocks, int nfie
     double acc = 0.0;
     for (int b = lane; b < nblocks; b += 32) {
         const double v = partials[((int64_t)b * nfields + q) * 4 + c];
-        acc = c == 2 ? fmax(acc, v) : acc + v;
+        acc = c == 2 ? nanmax(acc, v) : acc + v;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const double v = __shfl_xor_sync(0xffffffffu, acc, o);
-        acc = c == 2 ? fmax(acc, v) : acc + v;
+        acc = c == 2 ? nanmax(acc, v) : acc + v;
     }
     if (lane == 0) {
         if (c < 3) out[3 * q + c] = acc;

@@ -198,3 +198,51 @@ def test_binding_structs_match_the_c_layout(tmp_path):
         for f in fs:
             assert vals[k] == getattr(cls, f).offset, (st, f)
             k += 1
+
+
+def _noalloc_call(lib, field_addrs, storage, out_addr, dims=(16, 16, 16), padded=(24, 22, 22), origin=(4, 3, 3)):
+    arr = (ctypes.c_void_p * len(field_addrs))(*field_addrs)
+    d, pd, o = (ctypes.c_int64 * 3)(*dims), (ctypes.c_int64 * 3)(*padded), (ctypes.c_int64 * 3)(*origin)
+    st = lib.stencil_field_norms_noalloc(ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p)), len(field_addrs),
+                                         storage, d, pd, o, 0.0, ctypes.c_void_p(out_addr), None)
+    return st, lib.stencil_last_error_detail(None).decode()
+
+
+@pytest.mark.parametrize("storage,addr", [(_lib.STENCIL_F64, 0x10004), (_lib.STENCIL_F32, 0x10002),
+                                          (_lib.STENCIL_I32, 0x10001), (_lib.STENCIL_BF16, 0x10001)])
+def test_noalloc_norms_rejects_misaligned_fields(lib, storage, addr):
+    # rejected on the host before any launch: a misaligned element address would fault in pass 1
+    st, detail = _noalloc_call(lib, [0x20000, addr], storage, 0x30000)
+    assert st == _lib.STENCIL_EINVAL, detail
+    assert "fields[1] is not aligned" in detail
+
+
+def test_noalloc_norms_rejects_misaligned_output(lib):
+    st, detail = _noalloc_call(lib, [0x20000], _lib.STENCIL_F64, 0x30004)
+    assert st == _lib.STENCIL_EINVAL, detail
+    assert "out_dev is not 8-byte aligned" in detail
+
+
+def test_noalloc_binding_checks_its_tensors():
+    # the Python binding refuses tensors that the kernels would read or write out of bounds
+    torch = pytest.importorskip("torch")
+    dims, padded, origin = (16, 16, 16), (24, 22, 22), (4, 3, 3)
+    n = padded[0] * padded[1] * padded[2]
+    good_f = [torch.zeros(n, dtype=torch.float64)]
+    good_out = torch.zeros(3, dtype=torch.float64)
+    cases = [
+        (good_f, torch.zeros(3, dtype=torch.float32), "float64"),                 # FP32 result buffer
+        (good_f, torch.zeros(2, dtype=torch.float64), "elements"),                # too short
+        ([torch.zeros(n, dtype=torch.float32)], good_out, "element size"),        # dtype vs storage
+        ([torch.zeros(n - 1, dtype=torch.float64)], good_out, "padded"),          # field too small
+        (good_f, good_out, "CUDA"),                                               # host tensors
+    ]
+    for fields, out, words in cases:
+        with pytest.raises(_lib.StencilError) as e:
+            _lib.stencil_field_norms_noalloc(fields, _lib.STENCIL_F64, dims, padded, origin, 0.0, out)
+        assert e.value.status == _lib.STENCIL_EINVAL
+        assert words in str(e.value), (words, str(e.value))
+    # the mass slot needs one more double
+    with pytest.raises(_lib.StencilError) as e:
+        _lib.stencil_field_norms_noalloc(good_f, _lib.STENCIL_F64, dims, padded, origin, 1.0, good_out)
+    assert "elements" in str(e.value)

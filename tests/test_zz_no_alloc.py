@@ -21,9 +21,10 @@ from paper_2406_08923_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 
-def _noalloc(p, fields, mass_volume):
+def _noalloc(p, fields, mass_volume, out=None):
     n = 3 * len(fields) + (1 if mass_volume > 0 else 0)
-    out = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+    if out is None:
+        out = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
     L.stencil_field_norms_noalloc(fields, p.storage, p.dims, p.padded, p.origin, mass_volume, out)
     torch.cuda.synchronize()
     return out.cpu().numpy()
@@ -58,3 +59,25 @@ def test_rejects_more_fields_than_the_static_scratch_holds(cuda_lib):
         L.stencil_field_norms_noalloc(f * 9, p.storage, p.dims, p.padded, p.origin, 0.0, out)
     assert e.value.status == L.STENCIL_EINVAL
     assert "at most 8 fields" in str(e.value)
+
+
+def test_a_call_allocates_no_device_memory(cuda_lib):
+    # the property the entry point exists for: after a warm-up call (which loads the kernels and
+    # looks up the scratch array's address), a call leaves the device's free memory and
+    # PyTorch's allocator untouched
+    shape = (40, 36, 44)
+    p, par = mhd_plan(shape, L.STENCIL_F32)
+    f = p.alloc()
+    p.upload(f, synth.mhd_fields(shape, seed=6))
+    vol = par.dx[0] * par.dx[1] * par.dx[2]
+    out = torch.full((25,), float("nan"), dtype=torch.float64, device="cuda")
+    first = _noalloc(p, f, vol, out)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    L.stencil_field_norms_noalloc(f, p.storage, p.dims, p.padded, p.origin, vol, out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert torch.cuda.memory_allocated() == alloc0
+    assert free1 == free0, f"free device memory changed by {free0 - free1} bytes"
+    np.testing.assert_array_equal(out.cpu().numpy(), first)
