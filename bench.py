@@ -78,7 +78,11 @@ def _traffic(case, variant_name):
 # unit count: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz boost.
 FP64_PEAK_TFLOPS = 1.25
 FP64_PIPE_TINSTR = 2 * 152 * 2.07e9 / 1e12  # FP64 instructions (DFMA, DADD, DMUL alike) per s
-MHD_F64_INSTR, MHD_F64_FLOP = 600, 836      # per cell-substep, ncu sass counts of the MHD kernel
+# Algorithmic FP64 work of one MHD cell-substep (mean over the 3 RK substeps): the pruned
+# 6th-order derivatives (600 flop), the right-hand side of Eqs. A1-A4 and the 2N-storage RK
+# update, counted by tests/mhd_flops.py (checked against the oracle in test_mhd_flops.py).
+MHD_FLOPS_PER_CELL_SUBSTEP = 2465 / 3
+MHD_F64_INSTR = 600  # FP64 instructions per cell-substep the kernel executes (ncu sass counts)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
@@ -660,17 +664,21 @@ def run_extras(L, synth, stream, hbm_peak, args):
     # config 3: fused 8-field MHD, 256^3 FP64, 20 RK3 steps
     cells = MHD_N ** 3
     res = mhd_job(L, synth, L.STENCIL_F64, MHD_N, MHD_STEPS, w, 1, stream)
-    # FP64 instructions per cell-substep, counted by ncu (sass dadd + dfma + dmul, substep 0 at
-    # 128^3: 600 per cell, 836 flop); the FP64 pipe retires 2 per clock per SM
+    # algorithmic flops per cell-substep (Eqs. A1-A4 + RK3) against the FP64 FMA peak; the
+    # FP64 pipe's utilisation (instructions the kernel executes, ncu) beside it
+    tf = cells * MHD_FLOPS_PER_CELL_SUBSTEP / (res["ms_substep"] / 1e3) / 1e12
     ips = cells * MHD_F64_INSTR / (res["ms_substep"] / 1e3)
     out["mhd8_256_fp64_20steps"] = {
         "ms_per_job": round(res["ms_job"], 3), "ms_per_substep": round(res["ms_substep"], 4),
         "mcell_substep_updates_per_s": round(cells / (res["ms_substep"] / 1e3) / 1e6, 1),
         "variant": res["variant"], "finite": res["finite"], "mass": res["mass"],
-        "roofline": _roof("alu", ips / 1e12, FP64_PIPE_TINSTR, "T FP64 instr/s",
-                          note="600 FP64 instructions (836 flop) per cell-substep, ncu; FP64 pipe peak "
-                               "2 instr/clk/SM x 152 SMs x 2.07 GHz"),
-        "fp64_tflops": round(cells * MHD_F64_FLOP / (res["ms_substep"] / 1e3) / 1e12, 4),
+        "roofline": _roof("alu", tf, FP64_PEAK_TFLOPS, "TFLOP/s",
+                          note=f"{MHD_FLOPS_PER_CELL_SUBSTEP:.2f} algorithmic flop per cell-substep "
+                               "(tests/mhd_flops.py; an FMA is 2 flop) against the FP64 FMA peak "
+                               "2 x 2 flop/clk/SM x 152 SMs x 2.07 GHz"),
+        "fp64_pipe": {"instr_per_cell_substep": MHD_F64_INSTR, "achieved_tinstr_s": round(ips / 1e12, 4),
+                      "peak_tinstr_s": round(FP64_PIPE_TINSTR, 4),
+                      "utilisation": round(ips / 1e12 / FP64_PIPE_TINSTR, 4)},
         "paper_ideal_hbm_frac": round(cells * 128.0 / (res["ms_substep"] / 1e3) / 1e9 / hbm_peak, 4)}
     res["plan"].close()
     # config 4: 384^3 FP32 / BF16 storage, Kahan-compensated RK
