@@ -461,6 +461,66 @@ def run_serving_leg(n_requests=1024, load=0.7, fp64_subset=96, sweep=(0.5, 1.2))
     }
 
 
+def run_accuracy_leg(L, synth, stream, n=MHD_N_LOWP, nsteps=MHD_STEPS):
+    """Accuracy of the FP32 and BF16 storage paths of the 8-field system at 384^3 over 20 RK3
+    steps, against the FP64 path of the same library (which matches the FP64 oracle within
+    1e-12 at 256^3 over 20 steps, tests/test_gpu_full_size.py): after every step, per field,
+    relative L2 and L-infinity error over the interior, and the drift of the mass
+    sum exp(lnrho) dV.  Each low-precision state after k steps is one stencil_step(k) call from
+    the initial state, as the benchmark runs it; the FP64 reference steps one RK3 step at a
+    time (it carries no Kahan terms, so that is the same arithmetic)."""
+    import torch
+    f8 = synth.mhd_fields(n, seed=synth.SEED_MHD_LOWP)
+
+    def plan(storage):
+        par = L.mhd_params(n)
+        compute = L.STENCIL_F64 if storage == L.STENCIL_F64 else L.STENCIL_F32
+        p = L.Plan(3, (n, n, n), 3, 8, L.STENCIL_BC_PERIODIC, L.STENCIL_MHD8, storage, compute, params=par)
+        a, b = p.alloc(), p.alloc()
+        p.upload(a, f8)
+        p.halo_fill(a)
+        return p, a, b, par
+
+    ref, ra, rb, par = plan(L.STENCIL_F64)
+    vol = par.dx[0] * par.dx[1] * par.dx[2]
+    low = {name: plan(st)[:3] for name, st in (("fp32", L.STENCIL_F32), ("bf16", L.STENCIL_BF16))}
+    m0 = float(ref.norms(ra)[-1])
+    out = {name: {"worst_rel_l2": [0.0] * 8, "worst_rel_linf": [0.0] * 8, "per_step_worst": []} for name in low}
+    for k in range(1, nsteps + 1):
+        ref.step(ra, rb, 1, stream)
+        ra, rb = rb, ra
+        rint = [ref.interior(t) for t in ra]
+        for name, (p, a, b) in low.items():
+            p.step(a, b, k, stream)
+            worst = 0.0
+            for q in range(8):
+                got = p.interior(b[q]).double()
+                d = got - rint[q]
+                e2 = float(torch.linalg.vector_norm(d) / torch.linalg.vector_norm(rint[q]))
+                ei = float(d.abs().max() / rint[q].abs().max())
+                out[name]["worst_rel_l2"][q] = max(out[name]["worst_rel_l2"][q], e2)
+                out[name]["worst_rel_linf"][q] = max(out[name]["worst_rel_linf"][q], ei)
+                worst = max(worst, e2, ei)
+            out[name]["per_step_worst"].append(round(worst, 8))
+            if k == nsteps:
+                m = float(p.norms(b)[-1])
+                out[name]["mass_drift_after_20_steps"] = (m - m0) / m0
+    out["fp64_mass_drift_after_20_steps"] = (float(ref.norms(ra)[-1]) - m0) / m0
+    names = synth.MHD_FIELDS
+    for name in low:
+        for key in ("worst_rel_l2", "worst_rel_linf"):
+            out[name][key] = {f: float(f"{v:.3e}") for f, v in zip(names, out[name][key])}
+        out[name]["bound"] = 1e-5 if name == "fp32" else 1e-2
+    for p, *_ in [(ref,)] + list(low.values()):
+        p.close()
+    del ra, rb, low
+    torch.cuda.empty_cache()
+    out["reference"] = ("the library's FP64 path at the same size (FP64 oracle parity within 1e-12 "
+                        "in tests/test_gpu_full_size.py); mass = sum exp(lnrho) dV, drift relative to the "
+                        "initial FP64 state; mass_volume = %.6e" % vol)
+    return out
+
+
 def cpu_baseline(seconds_target=10.0):
     """The FP64 oracle, as it stands, on the host cores: a bounded sample of the headline
     workload (256^3 heat field, a number of Euler steps chosen to take ~10 s)."""
@@ -694,6 +754,8 @@ def run_extras(L, synth, stream, hbm_peak, args):
                      "roofline": _roof("hbm", gbs, hbm_peak, "GB/s",
                                        note=f"{avg_vals:.1f} values x {bpc} B per cell-substep")}
         res["plan"].close()
+    # config 4 accuracy: FP32 / BF16 storage against the FP64 path, every step of 20
+    out["mhd8_384_accuracy_20steps"] = run_accuracy_leg(L, synth, stream)
     return out
 
 

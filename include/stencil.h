@@ -65,8 +65,15 @@ typedef enum stencil_dtype {
 } stencil_dtype;
 
 typedef enum stencil_bc {
-    STENCIL_BC_PERIODIC = 0, /* beta(f, i) = f_{i mod n}: library fills the halo */
-    STENCIL_BC_CALLER = 1    /* caller fills the halo; one pass per stencil_step call */
+    STENCIL_BC_PERIODIC = 0,   /* beta(f, i) = f_{i mod n}: library fills the halo */
+    STENCIL_BC_CALLER = 1,     /* caller fills the halo; one pass per stencil_step call */
+    STENCIL_BC_PERIODIC_XY = 2 /* 3D DIFFUSION / MHD8 z-slab of a grid decomposed along z: x and
+                                  y periodic (library), the z halo (r planes below and above the
+                                  interior, whole padded planes) supplied by the caller before
+                                  every pass -- the neighbouring slabs' edge planes.  One pass
+                                  per call: stencil_step(nsteps = 1) for DIFFUSION,
+                                  stencil_substep for MHD8.  The z halo of fields_out is
+                                  unspecified on return (the caller overwrites it). */
 } stencil_bc;
 
 typedef enum stencil_kind {
@@ -102,7 +109,8 @@ enum { STENCIL_MHD_LNRHO = 0, STENCIL_MHD_UX, STENCIL_MHD_UY, STENCIL_MHD_UZ,
  *
  *   ndim     1 (XCORR, MAXFILTER), 1..3 (DIFFUSION) or 3 (MHD8).
  *   dims     interior extents (nx, ny, nz); entries beyond ndim are ignored.  With periodic
- *            boundaries each used extent must be >= 2*radius + 1.
+ *            boundaries each used extent must be >= 2*radius + 1 (STENCIL_BC_PERIODIC_XY: nx
+ *            and ny, and nz >= radius).
  *   radius   stencil radius r: 0..1024 for XCORR (radius > 4: F64 and F32 only; the radius
  *            sweep of Sec. 5.2) and MAXFILTER; 1..4 for DIFFUSION (the central Laplacian of
  *            order 2r; r = 3 is the 6th-order, 19-point step of Eq. 7; the other radii serve the
@@ -161,7 +169,9 @@ stencil_status stencil_layout(stencil_t plan, int64_t padded[3], int64_t pitch[3
  * interior of fields_in is not modified.  With STENCIL_BC_PERIODIC the halo of fields_in
  * is (re)filled first and the halo of fields_out is valid on return; with
  * STENCIL_BC_CALLER the halo of fields_in must be filled by the caller, nsteps must be 1
- * and the kind must be XCORR, MAXFILTER or DIFFUSION.  Asynchronous on `stream`: no host sync, no
+ * and the kind must be XCORR, MAXFILTER or DIFFUSION; with STENCIL_BC_PERIODIC_XY (DIFFUSION
+ * only -- MHD8 z-slabs use stencil_substep) nsteps must be 1, the caller supplies the z halo
+ * of fields_in and the library its x/y images.  Asynchronous on `stream`: no host sync, no
  * allocation, safe to capture in a CUDA graph.  Bounded device waits that expire are
  * reported by the next stencil_sync / stencil_field_norms on the plan.
  */
@@ -169,8 +179,25 @@ stencil_status stencil_step(stencil_t plan, void *const *fields_in, void *const 
                             int nsteps, void *stream);
 
 /* stencil_halo_fill -- fill the halo of each field with the periodic image of its interior
- * (Eq. 2 with periodic beta).  No-op for STENCIL_BC_CALLER.  Asynchronous on `stream`. */
+ * (Eq. 2 with periodic beta).  No-op for STENCIL_BC_CALLER; for STENCIL_BC_PERIODIC_XY only the
+ * x/y images, on every padded plane (the z-halo planes included, from their own cells).
+ * Asynchronous on `stream`. */
 stencil_status stencil_halo_fill(stencil_t plan, void *const *fields, void *stream);
+
+/*
+ * stencil_substep -- one substep s (0, 1, 2) of the 3-stage Runge-Kutta step of an MHD8 plan
+ * (Sec. 3.3; the 2N-storage scheme w <- alpha_s w + dt RHS(f), f <- f + beta_s w of Eqs. A1-A4).
+ *
+ * Three calls with s = 0, 1, 2, ping-ponging fields_in / fields_out, equal one
+ * stencil_step(nsteps = 1).  It exists for decomposed grids (STENCIL_BC_PERIODIC_XY), whose z
+ * halo must be exchanged between substeps; it also accepts periodic plans.  The RK register w
+ * lives in the plan and carries from substep to substep; for FP32/BF16 storage the Kahan
+ * terms are cleared at s = 0.  fields_in / fields_out: 8 device pointers each in the plan's
+ * layout, not aliasing.  The halo of fields_in is (re)filled first per the plan's boundary
+ * mode.  Asynchronous on `stream`; EINVAL for a non-MHD8 plan or s outside 0..2.
+ */
+stencil_status stencil_substep(stencil_t plan, void *const *fields_in, void *const *fields_out,
+                               int substep, void *stream);
 
 /*
  * stencil_mhd_rhs -- evaluate only the MHD right-hand side phi(gamma(psi(f))) (Sec. 3.3,

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(HERE, "libstencil.so")
 # enums (include/stencil.h)
 STENCIL_OK, STENCIL_EINVAL, STENCIL_ENOMEM, STENCIL_ECUDA, STENCIL_EUNSUPPORTED, STENCIL_ETIMEOUT = range(6)
 STENCIL_I32, STENCIL_F64, STENCIL_F32, STENCIL_BF16 = range(4)
-STENCIL_BC_PERIODIC, STENCIL_BC_CALLER = range(2)
+STENCIL_BC_PERIODIC, STENCIL_BC_CALLER, STENCIL_BC_PERIODIC_XY = range(3)
 STENCIL_XCORR, STENCIL_DIFFUSION, STENCIL_MHD8, STENCIL_MAXFILTER = range(4)
 
 EXPORTED = (
@@ -31,7 +31,7 @@ EXPORTED = (
     "stencil_set_variant", "stencil_autotune", "stencil_field_norms_noalloc", "stencil_selftest_wait",
     "stencil_server_create", "stencil_server_destroy", "stencil_server_submit", "stencil_server_progress",
     "stencil_server_poll", "stencil_server_stats", "stencil_server_sync", "stencil_server_last_error_detail",
-    "stencil_server_cancel",
+    "stencil_server_cancel", "stencil_substep",
 )
 
 STENCIL_REQ_PENDING, STENCIL_REQ_ACTIVE, STENCIL_REQ_COMPLETING, STENCIL_REQ_DONE, STENCIL_REQ_CANCELLED = range(5)
@@ -78,6 +78,7 @@ def load():
                                    ctypes.POINTER(I64)]),
             "stencil_step": (I, [P, PP, PP, I, P]),
             "stencil_halo_fill": (I, [P, PP, P]),
+            "stencil_substep": (I, [P, PP, PP, I, P]),
             "stencil_mhd_rhs": (I, [P, PP, PP, P]),
             "stencil_field_norms": (I, [P, PP, ctypes.POINTER(D), P]),
             "stencil_sync": (I, [P, P]),
@@ -162,6 +163,12 @@ def stencil_step(h, fields_in, fields_out, nsteps, stream=None):
     pi, ki = _ptrs(fields_in)
     po, ko = _ptrs(fields_out)
     _check(load().stencil_step(h, pi, po, nsteps, _stream(stream)), "stencil_step", h)
+
+
+def stencil_substep(h, fields_in, fields_out, substep, stream=None):
+    pi, ki = _ptrs(fields_in)
+    po, ko = _ptrs(fields_out)
+    _check(load().stencil_substep(h, pi, po, int(substep), _stream(stream)), "stencil_substep", h)
 
 
 def stencil_halo_fill(h, fields, stream=None):
@@ -378,6 +385,9 @@ class Plan:
     # -- calls
     def step(self, fin, fout, nsteps=1, stream=None):
         stencil_step(self.h, fin, fout, nsteps, stream)
+
+    def substep(self, fin, fout, substep, stream=None):
+        stencil_substep(self.h, fin, fout, substep, stream)
 
     def halo_fill(self, fields, stream=None):
         stencil_halo_fill(self.h, fields, stream)

@@ -237,7 +237,9 @@ stencil_status stencil_create(int ndim, const int64_t dims[3], int radius, const
     *out = nullptr;
     if (!dims) return fail(nullptr, STENCIL_EINVAL, "dims is NULL");
     if ((int)kind < 0 || (int)kind > 3) return fail(nullptr, STENCIL_EINVAL, "unknown kind");
-    if ((int)bc < 0 || (int)bc > 1) return fail(nullptr, STENCIL_EINVAL, "unknown boundary condition");
+    if ((int)bc < 0 || (int)bc > 2) return fail(nullptr, STENCIL_EINVAL, "unknown boundary condition");
+    if (bc == STENCIL_BC_PERIODIC_XY && (ndim != 3 || (kind != STENCIL_DIFFUSION && kind != STENCIL_MHD8)))
+        return fail(nullptr, STENCIL_EUNSUPPORTED, "STENCIL_BC_PERIODIC_XY needs a 3D DIFFUSION or MHD8 plan");
     if ((int)storage < 0 || (int)storage > 3 || (int)compute < 0 || (int)compute > 3)
         return fail(nullptr, STENCIL_EINVAL, "unknown dtype");
     if (ndim < 1 || ndim > 3) return fail(nullptr, STENCIL_EINVAL, "ndim must be 1, 2 or 3");
@@ -282,8 +284,9 @@ stencil_status stencil_create(int ndim, const int64_t dims[3], int radius, const
                 return fail(nullptr, STENCIL_EUNSUPPORTED, "DIFFUSION supports F64/F64 and F32/F32");
         } else {
             if (nfields != 8) return fail(nullptr, STENCIL_EINVAL, "MHD8 needs nfields = 8");
-            if (bc != STENCIL_BC_PERIODIC)
-                return fail(nullptr, STENCIL_EUNSUPPORTED, "MHD8 supports periodic boundaries only");
+            if (bc == STENCIL_BC_CALLER)
+                return fail(nullptr, STENCIL_EUNSUPPORTED,
+                            "MHD8 supports periodic boundaries (or periodic x/y with a caller z halo)");
             if (!((storage == STENCIL_F64 && compute == STENCIL_F64) ||
                   (storage == STENCIL_F32 && compute == STENCIL_F32) ||
                   (storage == STENCIL_BF16 && compute == STENCIL_F32)))
@@ -298,6 +301,12 @@ stencil_status stencil_create(int ndim, const int64_t dims[3], int radius, const
         for (int a = 0; a < ndim; ++a)
             if (dims[a] < 2 * radius + 1)
                 return fail(nullptr, STENCIL_EINVAL, "periodic extents must be >= 2*radius+1");
+    if (bc == STENCIL_BC_PERIODIC_XY) {
+        if (dims[0] < 2 * radius + 1 || dims[1] < 2 * radius + 1)
+            return fail(nullptr, STENCIL_EINVAL, "periodic extents must be >= 2*radius+1");
+        if (dims[2] < radius)
+            return fail(nullptr, STENCIL_EINVAL, "a z-slab needs at least radius planes");
+    }
 
     stencil_plan *p = new (std::nothrow) stencil_plan;
     if (!p) return fail(nullptr, STENCIL_ENOMEM, "host allocation of the plan failed");
@@ -473,9 +482,9 @@ stencil_status stencil_halo_fill(stencil_t p, void *const *fields, void *stream)
     stencil_status st = check_device(p);
     if (st != STENCIL_OK) return st;
     if ((st = check_ptrs(p, fields, "fields")) != STENCIL_OK) return st;
-    if (p->bc != STENCIL_BC_PERIODIC) return STENCIL_OK;
+    if (p->bc == STENCIL_BC_CALLER) return STENCIL_OK;
     CK(p, launch_halo_fill(p->geom, p->radius, p->esize, ptrs(fields, p->nfields), p->nfields,
-                           (cudaStream_t)stream),
+                           (cudaStream_t)stream, p->bc == STENCIL_BC_PERIODIC),
        "halo_fill launch");
     return STENCIL_OK;
 }
@@ -532,8 +541,8 @@ static stencil_status run_pass(stencil_t p, void *const *src, void *const *dst, 
             CK(p, launch_diffusion2d(storage_code(p->storage), &m, dst[0], g, p->dcoef, periodic, p->err, s),
                "diffusion (2D) launch");
         else
-            CK(p, launch_diffusion(storage_code(p->storage), &m, dst[0], g, p->dcoef, periodic, p->err, s,
-                                   p->variant),
+            CK(p, launch_diffusion(storage_code(p->storage), &m, dst[0], g, p->dcoef, p->bc != STENCIL_BC_CALLER,
+                                   p->err, s, p->variant),
                "diffusion launch");
         return STENCIL_OK;
     }
@@ -562,6 +571,8 @@ stencil_status stencil_step(stencil_t p, void *const *fin, void *const *fout, in
             if (fin[q] == fout[r]) return fail(p, STENCIL_EINVAL, "fields_in and fields_out alias");
     if (nsteps < 0) return fail(p, STENCIL_EINVAL, "nsteps must be >= 0");
     const bool periodic = p->bc == STENCIL_BC_PERIODIC;
+    if (p->bc == STENCIL_BC_PERIODIC_XY && p->kind == STENCIL_MHD8)
+        return fail(p, STENCIL_EINVAL, "an MHD8 z-slab advances one RK substep per call (stencil_substep)");
     if (!periodic && nsteps != 1)
         return fail(p, STENCIL_EINVAL, "caller-filled boundaries allow exactly one step per call");
     cudaStream_t s = (cudaStream_t)stream;
@@ -569,8 +580,7 @@ stencil_status stencil_step(stencil_t p, void *const *fin, void *const *fout, in
     if (nsteps == 0) {
         for (int q = 0; q < p->nfields; ++q)
             CK(p, cudaMemcpyAsync(fout[q], fin[q], p->bytes_per_field, cudaMemcpyDeviceToDevice, s), "copy");
-        if (periodic) return stencil_halo_fill(p, fout, stream);
-        return STENCIL_OK;
+        return stencil_halo_fill(p, fout, stream);
     }
 
     // pass list
@@ -602,8 +612,8 @@ stencil_status stencil_step(stencil_t p, void *const *fin, void *const *fout, in
         npass = p->kind == STENCIL_MHD8 ? 3 * nsteps : nsteps;
         sweeps.assign(npass, 1);
     }
-    if (periodic && !xcorr_like)
-        CK(p, launch_halo_fill(p->geom, p->radius, p->esize, ptrs(fin, p->nfields), p->nfields, s),
+    if (p->bc != STENCIL_BC_CALLER && !xcorr_like)
+        CK(p, launch_halo_fill(p->geom, p->radius, p->esize, ptrs(fin, p->nfields), p->nfields, s, periodic),
            "halo_fill launch");
     if (p->kind == STENCIL_MHD8 && p->storage != STENCIL_F64)
         for (int q = 0; q < 8; ++q) CK(p, cudaMemsetAsync(p->kc[q], 0, ncell * p->esize, s), "clear Kahan terms");
@@ -619,6 +629,27 @@ stencil_status stencil_step(stencil_t p, void *const *fin, void *const *fout, in
     return STENCIL_OK;
 }
 
+stencil_status stencil_substep(stencil_t p, void *const *fin, void *const *fout, int substep, void *stream) {
+    if (!p) return fail(nullptr, STENCIL_EINVAL, "plan is NULL");
+    if (p->kind != STENCIL_MHD8) return fail(p, STENCIL_EINVAL, "stencil_substep needs an MHD8 plan");
+    if (substep < 0 || substep > 2) return fail(p, STENCIL_EINVAL, "substep must be 0, 1 or 2");
+    stencil_status st = check_device(p);
+    if (st != STENCIL_OK) return st;
+    if ((st = check_ptrs(p, fin, "fields_in")) != STENCIL_OK) return st;
+    if ((st = check_ptrs(p, fout, "fields_out")) != STENCIL_OK) return st;
+    for (int q = 0; q < 8; ++q)
+        for (int r = 0; r < 8; ++r)
+            if (fin[q] == fout[r]) return fail(p, STENCIL_EINVAL, "fields_in and fields_out alias");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(p, launch_halo_fill(p->geom, p->radius, p->esize, ptrs(fin, 8), 8, s, p->bc == STENCIL_BC_PERIODIC),
+       "halo_fill launch");
+    if (substep == 0 && p->storage != STENCIL_F64) {
+        const size_t ncell = (size_t)(p->geom.n[0] * p->geom.n[1] * p->geom.n[2]);
+        for (int q = 0; q < 8; ++q) CK(p, cudaMemsetAsync(p->kc[q], 0, ncell * p->esize, s), "clear Kahan terms");
+    }
+    return run_pass(p, fin, fout, 1, substep, s);
+}
+
 stencil_status stencil_mhd_rhs(stencil_t p, void *const *fields, void *const *rhs, void *stream) {
     if (!p) return fail(nullptr, STENCIL_EINVAL, "plan is NULL");
     if (p->kind != STENCIL_MHD8) return fail(p, STENCIL_EINVAL, "stencil_mhd_rhs needs an MHD8 plan");
@@ -627,8 +658,8 @@ stencil_status stencil_mhd_rhs(stencil_t p, void *const *fields, void *const *rh
     if ((st = check_ptrs(p, fields, "fields")) != STENCIL_OK) return st;
     if ((st = check_ptrs(p, rhs, "rhs")) != STENCIL_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    if (p->bc == STENCIL_BC_PERIODIC)
-        CK(p, launch_halo_fill(p->geom, p->radius, p->esize, ptrs(fields, 8), 8, s), "halo_fill launch");
+    CK(p, launch_halo_fill(p->geom, p->radius, p->esize, ptrs(fields, 8), 8, s, p->bc == STENCIL_BC_PERIODIC),
+       "halo_fill launch");
     int box[3];
     mhd_box(storage_code(p->storage), p->variant, box);
     MhdMaps maps;

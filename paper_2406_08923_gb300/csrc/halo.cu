@@ -4,20 +4,24 @@
 // images (index arithmetic modulo the interior extent on each axis), so no ordering between
 // faces, edges and corners is needed.  Grid: x = blocks striding over the halo cells of one
 // padded z-plane, y = padded z-plane, z = field.
+//
+// With zwrap = 0 (x and y periodic, the z halo supplied by the caller, as in a z-slab of a
+// decomposed grid) every padded plane, the z-halo planes included, gets the x/y periodic
+// images of its own cells and no plane is copied along z.
 #include "internal.h"
 
 namespace stn {
 
 template <typename T>
-__global__ void halo_fill_kernel(Ptrs8 f, Geom g, int r) {
+__global__ void halo_fill_kernel(Ptrs8 f, Geom g, int r, int zwrap) {
     T *base = static_cast<T *>(f.p[blockIdx.z]);
     const int64_t nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const int64_t hy = ny > 1 ? r : 0, hz = nz > 1 ? r : 0;
     const int64_t wx = nx + 2 * r, wy = ny + 2 * hy;
     const int64_t kr = blockIdx.y;  // z in the used range [0, nz + 2 hz)
-    const bool halo_plane = (kr < hz) || (kr >= nz + hz);
+    const bool halo_plane = zwrap && ((kr < hz) || (kr >= nz + hz));
     const int64_t count = halo_plane ? wx * wy : 2 * hy * wx + ny * 2 * r;
-    const int64_t sk = ((kr - hz) % nz + nz) % nz;
+    const int64_t sk = zwrap ? ((kr - hz) % nz + nz) % nz : kr - hz;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < count;
          q += (int64_t)gridDim.x * blockDim.x) {
         int64_t xr, yr;
@@ -43,16 +47,16 @@ __global__ void halo_fill_kernel(Ptrs8 f, Geom g, int r) {
 }
 
 cudaError_t launch_halo_fill(const Geom &g, int r, int esize, const Ptrs8 &f, int nfields,
-                             cudaStream_t s) {
+                             cudaStream_t s, bool zwrap) {
     if (r == 0) return cudaSuccess;
     const int64_t hz = g.n[2] > 1 ? r : 0;
     dim3 grid(1, (unsigned)(g.n[2] + 2 * hz), (unsigned)nfields);
     const int64_t per_plane = (g.n[0] + 2 * r) * (g.n[1] + 2 * (g.n[1] > 1 ? r : 0));
     grid.x = (unsigned)std::min<int64_t>(64, (per_plane + 255) / 256);
     switch (esize) {
-    case 2: halo_fill_kernel<uint16_t><<<grid, 256, 0, s>>>(f, g, r); break;
-    case 4: halo_fill_kernel<uint32_t><<<grid, 256, 0, s>>>(f, g, r); break;
-    case 8: halo_fill_kernel<uint64_t><<<grid, 256, 0, s>>>(f, g, r); break;
+    case 2: halo_fill_kernel<uint16_t><<<grid, 256, 0, s>>>(f, g, r, zwrap ? 1 : 0); break;
+    case 4: halo_fill_kernel<uint32_t><<<grid, 256, 0, s>>>(f, g, r, zwrap ? 1 : 0); break;
+    case 8: halo_fill_kernel<uint64_t><<<grid, 256, 0, s>>>(f, g, r, zwrap ? 1 : 0); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

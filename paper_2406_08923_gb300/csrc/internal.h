@@ -27,8 +27,9 @@ struct Ptrs8 {
 };
 
 // Periodic halo fill (Eq. 2, periodic beta) of `nfields` fields of element size `esize`.
+// zwrap = false: x/y images only, on every padded plane (z halo owned by the caller).
 cudaError_t launch_halo_fill(const Geom &g, int r, int esize, const Ptrs8 &f, int nfields,
-                             cudaStream_t s);
+                             cudaStream_t s, bool zwrap = true);
 
 // XCORR (Eq. 3): `sweeps` sweeps in one launch.  dtype: 0 = int32 (mod 2^32), 1 = f64,
 // 2 = f32.  periodic: halo read by wrapping interior indices (any sweeps <= max);

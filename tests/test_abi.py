@@ -57,7 +57,7 @@ def _create(lib, ndim=3, dims=(16, 16, 16), radius=3, coeffs=None, nfields=1, bc
     if coeffs is not None:
         keep = np.ascontiguousarray(coeffs, dtype=np.int32 if storage == 0 else np.float64)
         cp, nc = keep.ctypes.data_as(ctypes.c_void_p), keep.size
-    p = _lib.heat_params(16) if params else None
+    p = (_lib.mhd_params(16) if kind == 2 else _lib.heat_params(16)) if params else None
     h = ctypes.c_void_p()
     st = lib.stencil_create(ndim, d, radius, cp, nc, nfields, bc, kind, storage, compute,
                             ctypes.byref(p) if p is not None else None, ctypes.byref(h))
@@ -81,6 +81,11 @@ def _create(lib, ndim=3, dims=(16, 16, 16), radius=3, coeffs=None, nfields=1, bc
     (dict(kind=2, nfields=8, ndim=2, dims=(16, 16, 1)), _lib.STENCIL_EUNSUPPORTED),  # MHD8 is 3D
     (dict(ndim=2, dims=(16, 6, 1), radius=3), _lib.STENCIL_EINVAL),  # periodic extent < 2r+1
     (dict(kind=2, nfields=8, bc=1), _lib.STENCIL_EUNSUPPORTED),  # MHD8 needs periodic
+    (dict(bc=3), _lib.STENCIL_EINVAL),                           # unknown boundary mode
+    (dict(bc=2, ndim=2, dims=(16, 16, 1)), _lib.STENCIL_EUNSUPPORTED),  # z-slabs are 3D
+    (dict(bc=2, kind=0, ndim=1, dims=(64, 1, 1), coeffs=[1.0, 2.0, 1.0], radius=1), _lib.STENCIL_EUNSUPPORTED),
+    (dict(bc=2, dims=(16, 16, 2)), _lib.STENCIL_EINVAL),          # slab thinner than the radius
+    (dict(bc=2, dims=(6, 16, 16)), _lib.STENCIL_EINVAL),          # periodic x extent < 2r+1
     (dict(kind=2, nfields=8, storage=0, compute=0), _lib.STENCIL_EUNSUPPORTED),
     (dict(kind=0, ndim=1, dims=(64, 1, 1), radius=3, nfields=1, coeffs=[1] * 6, storage=0, compute=0), _lib.STENCIL_EINVAL),
     (dict(kind=0, ndim=1, dims=(64, 1, 1), radius=5, nfields=1, coeffs=[1] * 11, storage=0, compute=0), _lib.STENCIL_EUNSUPPORTED),
@@ -100,11 +105,20 @@ def test_create_rejects_invalid_arguments(lib, kw, expect):
     assert detail
 
 
+@pytest.mark.parametrize("kw", [dict(bc=2, dims=(16, 16, 3)), dict(bc=2, kind=2, nfields=8, dims=(16, 16, 5))])
+def test_z_slab_plans_are_accepted(lib, kw):
+    st, plan, detail = _create(lib, **kw)
+    assert st in (0, _lib.STENCIL_ECUDA), detail
+    if st == 0:
+        lib.stencil_destroy(plan)
+
+
 def test_null_plan_calls_are_rejected(lib):
     assert lib.stencil_layout(None, None, None, None, None) == _lib.STENCIL_EINVAL
     assert lib.stencil_step(None, None, None, 1, None) == _lib.STENCIL_EINVAL
     assert lib.stencil_sync(None, None) == _lib.STENCIL_EINVAL
     assert lib.stencil_set_variant(None, 0) == _lib.STENCIL_EINVAL
+    assert lib.stencil_substep(None, None, None, 0, None) == _lib.STENCIL_EINVAL
     lib.stencil_destroy(None)
 
 

@@ -45,7 +45,7 @@ def test_rhs_against_oracle(cuda_lib, storage, shape):
     p.upload(a, f8)
     ref = oracle.mhd_rhs(_rounded(f8, storage), oracle_mhd_params(par))
     ctype = torch.float64 if storage == L.STENCIL_F64 else torch.float32
-    tol = 1e-12 if storage == L.STENCIL_F64 else 2e-5
+    tol = 1e-12 if storage == L.STENCIL_F64 else 1e-5
     for v in range(p.variant()[1]):
         p.set_variant(v)
         rhs = [torch.zeros(shape, dtype=ctype, device="cuda") for _ in range(8)]
@@ -145,7 +145,7 @@ def test_heat_conduction_rhs_against_oracle(cuda_lib, storage):
     ref0 = oracle.mhd_rhs(_rounded(f8, storage), oracle_mhd_params(L.mhd_params(shape)))
     assert rel_l2(ref[7] - ref0[7], ref0[7]) > 1e-3  # the term is not negligible in this case
     ctype = torch.float64 if storage == L.STENCIL_F64 else torch.float32
-    tol = 1e-12 if storage == L.STENCIL_F64 else 2e-5
+    tol = 1e-12 if storage == L.STENCIL_F64 else 1e-5
     for v in range(p.variant()[1]):
         p.set_variant(v)
         rhs = [torch.zeros(shape, dtype=ctype, device="cuda") for _ in range(8)]
