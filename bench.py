@@ -261,7 +261,7 @@ def mhd_job(L, synth, storage, n, steps, warmup, reps, stream):
     ms_halo = _timed(lambda: p.halo_fill(a, stream), 5, stream)
     ms_sub = (ms_job - ms_halo) / (3 * steps)
     norms = p.norms(b)
-    return {"plan": p, "ms_job": ms_job, "ms_substep": ms_sub, "variant": p.variant()[2],
+    return {"plan": p, "fields": b, "ms_job": ms_job, "ms_substep": ms_sub, "variant": p.variant()[2],
             "mass": float(norms[-1]), "finite": bool(np.all(np.isfinite(norms)))}
 
 
@@ -418,6 +418,25 @@ def run_serving_leg(n_requests=1024, load=0.7, fp64_subset=96, sweep=(0.5, 1.2))
                           "mcell_updates_per_s": round(u2 / w2 / 1e6, 1), "p50_ms": round(l2["p50_ms"], 2),
                           "p99_ms": round(l2["p99_ms"], 2), "peak_gb": round(p2 / 1e9, 2)})
     serving.poisson_arrivals(reqs, load * cap_rps)
+    # ragged sizes: 128 requests with n not rounded (most edges not a multiple of 4 or 8, so
+    # the batched kernels take their element-wise edge paths), saturation and open loop
+    rag = serving.make_requests(128, seed=serving.SEED_SERVE + 1, round_to=1)
+    for r in rag:
+        templates.get(r.kind, r.n)
+    for r in rag:
+        r.arrival = 0.0
+    wall_r, peak_r, _ = serving.serve(rag, templates)
+    cap_r = len(rag) / wall_r
+    serving.poisson_arrivals(rag, load * cap_r)
+    wall_ro, _, upd_ro = serving.serve(rag, templates)
+    lat_r = serving.latency_stats(rag)
+    ragged = {"requests": len(rag), "n_not_multiple_of_8": sum(r.n % 8 != 0 for r in rag),
+              "work_gcell_updates": round(sum(r.work() for r in rag) / 1e9, 2),
+              "saturation": {"wall_s": round(wall_r, 3), "requests_per_s": round(cap_r, 1),
+                             "mcell_updates_per_s": round(sum(r.work() for r in rag) / wall_r / 1e6, 1)},
+              "open_loop": {"load": load, "rate_rps": round(load * cap_r, 1), "p50_ms": round(lat_r["p50_ms"], 2),
+                            "p99_ms": round(lat_r["p99_ms"], 2),
+                            "mcell_updates_per_s": round(upd_ro / wall_ro / 1e6, 1)}}
     # 3. per-grid FP64 path on a subset, FIFO latencies under the same arrivals
     sub = sorted(reqs, key=lambda r: r.arrival)[:fp64_subset]
     arr = [r.arrival for r in sub]
@@ -439,8 +458,9 @@ def run_serving_leg(n_requests=1024, load=0.7, fp64_subset=96, sweep=(0.5, 1.2))
     thr64 = work_sub / wall64 / 1e6
     torch.cuda.synchronize()
     return {
-        "requests": n_requests, "mix": "n log-uniform 32..192 (multiples of 8), kinds uniform {xcorr1d n^3, heat3d, mhd8}, "
-                                        "10-50 steps, FP32, Poisson arrivals",
+        "requests": n_requests, "mix": "n log-uniform 32..192 (rounded to multiples of 8, so that one pinned input "
+                                        "template per kind and size is kept; ragged_sizes runs unrounded n), kinds "
+                                        "uniform {xcorr1d n^3, heat3d, mhd8}, 10-50 steps, FP32, Poisson arrivals",
         "budget_gb": 120, "template_gen_s": round(t_gen, 1),
         "work_gcell_updates": round(work / 1e9, 2),
         "saturation": {"wall_s": round(wall_sat, 3), "requests_per_s": round(cap_rps, 1),
@@ -449,6 +469,7 @@ def run_serving_leg(n_requests=1024, load=0.7, fp64_subset=96, sweep=(0.5, 1.2))
                       "mcell_updates_per_s": round(thr, 1), "p50_ms": round(lat["p50_ms"], 2),
                       "p99_ms": round(lat["p99_ms"], 2), "peak_gb": round(peak / 1e9, 2)},
         "load_sweep": sweep_out,
+        "ragged_sizes": ragged,
         "per_grid_fp64_subset": {"requests": len(sub), "wall_s": round(wall64, 3),
                                  "mcell_updates_per_s": round(thr64, 1),
                                  "p50_ms": round(float(np.percentile(lat64, 50) * 1e3), 2),
@@ -632,10 +653,8 @@ def run_ours(args):
     h_in.copy_(a[0].cpu())
     d_in = p.alloc()
 
-    def e2e():
-        d_in[0].copy_(h_in, non_blocking=True)
-        p.step(d_in, b, HEAT_STEPS, stream)
-        h_out.copy_(b[0], non_blocking=True)
+    def e2e():  # one C-ABI call: H2D of the input, the 100-step job, D2H of the result, sync
+        p.step_host([h_in], [h_out], d_in, b, HEAT_STEPS, stream)
 
     e2e()
     ms_e2e = _max_over_ranks(_timed(e2e, max(3, args.steps // 2), stream), dist)
@@ -668,7 +687,8 @@ def run_ours(args):
                          "bytes_per_cell": bytes_cell},
         "kernel_ms_avg": round(ms_kernel, 5), "halo_fill_ms": round(ms_halo, 5),
         "e2e": {"value": round(world * cells * HEAT_STEPS / (ms_e2e / 1e3) / 1e6, 3), "unit": "Mcell-updates/s",
-                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                "call": "stencil_step_host (pinned host buffers in, 100-step job, host buffers out, stream sync)"},
         "gpu_launches": args.steps * (HEAT_STEPS + 1),
         "clocks": clocks,
         "per_stencil": extras,
@@ -740,6 +760,23 @@ def run_extras(L, synth, stream, hbm_peak, args):
                       "peak_tinstr_s": round(FP64_PIPE_TINSTR, 4),
                       "utilisation": round(ips / 1e12 / FP64_PIPE_TINSTR, 4)},
         "paper_ideal_hbm_frac": round(cells * 128.0 / (res["ms_substep"] / 1e3) / 1e9 / hbm_peak, 4)}
+    # norms (a7): the two-pass FP64 reduction over the 8 fields of the 256^3 state, one read of
+    # each interior (8 B per cell and field), through the allocation-free entry point so that a
+    # call is one device-side job (stencil_field_norms also copies to the host and synchronises)
+    import torch
+    mp, fields = res["plan"], res["fields"]
+    nout = torch.empty(3 * 8 + 1, dtype=torch.float64, device="cuda")
+    vol = mp.params.dx[0] * mp.params.dx[1] * mp.params.dx[2]
+    norm_call = lambda: L.stencil_field_norms_noalloc(fields, mp.storage, mp.dims, mp.padded, mp.origin, vol, nout,
+                                                      stream)
+    norm_call()
+    ms_norm = _timed(norm_call, 20, stream)
+    gbs = cells * 8 * 8 / (ms_norm / 1e3) / 1e9
+    out["norms_8x256_fp64"] = {
+        "ms_per_call": round(ms_norm, 4), "launches_per_call": 2,
+        "roofline": _roof("hbm", gbs, hbm_peak, "GB/s",
+                          note="one read of 8 fields x 256^3 interior cells x 8 B per call (sum, sum f^2, "
+                               "max |f|, mass sum exp(lnrho)); 2 launches")}
     res["plan"].close()
     # config 4: 384^3 FP32 / BF16 storage, Kahan-compensated RK
     cells = MHD_N_LOWP ** 3

@@ -178,6 +178,20 @@ stencil_status stencil_layout(stencil_t plan, int64_t padded[3], int64_t pitch[3
 stencil_status stencil_step(stencil_t plan, void *const *fields_in, void *const *fields_out,
                             int nsteps, void *stream);
 
+/*
+ * stencil_step_host -- stencil_step with the fields in host memory, for callers that keep
+ * their state on the host: copies each host_in field (nfields arrays of bytes_per_field bytes
+ * in the plan's padded layout, see stencil_layout; only the interior is significant for
+ * periodic plans) into dev_in, runs stencil_step(dev_in -> dev_out, nsteps), and copies each
+ * dev_out field back into host_out.  dev_in / dev_out are caller-owned device field sets as
+ * for stencil_step (dev_in is overwritten).  Host arrays should be page-locked for the copies
+ * to run asynchronously.  Synchronises `stream` before returning; errors as stencil_step,
+ * ETIMEOUT as stencil_sync.  (Sec. 2.4: f' = zeta(f^) evaluated on the device, the arrays
+ * staged through it.)
+ */
+stencil_status stencil_step_host(stencil_t plan, const void *const *host_in, void *const *host_out,
+                                 void *const *dev_in, void *const *dev_out, int nsteps, void *stream);
+
 /* stencil_halo_fill -- fill the halo of each field with the periodic image of its interior
  * (Eq. 2 with periodic beta).  No-op for STENCIL_BC_CALLER; for STENCIL_BC_PERIODIC_XY only the
  * x/y images, on every padded plane (the z-halo planes included, from their own cells).

@@ -31,7 +31,7 @@ EXPORTED = (
     "stencil_set_variant", "stencil_autotune", "stencil_field_norms_noalloc", "stencil_selftest_wait",
     "stencil_server_create", "stencil_server_destroy", "stencil_server_submit", "stencil_server_progress",
     "stencil_server_poll", "stencil_server_stats", "stencil_server_sync", "stencil_server_last_error_detail",
-    "stencil_server_cancel", "stencil_substep",
+    "stencil_server_cancel", "stencil_substep", "stencil_step_host",
 )
 
 STENCIL_REQ_PENDING, STENCIL_REQ_ACTIVE, STENCIL_REQ_COMPLETING, STENCIL_REQ_DONE, STENCIL_REQ_CANCELLED = range(5)
@@ -79,6 +79,7 @@ def load():
             "stencil_step": (I, [P, PP, PP, I, P]),
             "stencil_halo_fill": (I, [P, PP, P]),
             "stencil_substep": (I, [P, PP, PP, I, P]),
+            "stencil_step_host": (I, [P, PP, PP, PP, PP, I, P]),
             "stencil_mhd_rhs": (I, [P, PP, PP, P]),
             "stencil_field_norms": (I, [P, PP, ctypes.POINTER(D), P]),
             "stencil_sync": (I, [P, P]),
@@ -163,6 +164,15 @@ def stencil_step(h, fields_in, fields_out, nsteps, stream=None):
     pi, ki = _ptrs(fields_in)
     po, ko = _ptrs(fields_out)
     _check(load().stencil_step(h, pi, po, nsteps, _stream(stream)), "stencil_step", h)
+
+
+def stencil_step_host(h, host_in, host_out, dev_in, dev_out, nsteps, stream=None):
+    """host_in / host_out: host tensors (page-locked for asynchronous copies) in the padded layout."""
+    hi, khi = _ptrs(host_in)
+    ho, kho = _ptrs(host_out)
+    di, kdi = _ptrs(dev_in)
+    do, kdo = _ptrs(dev_out)
+    _check(load().stencil_step_host(h, hi, ho, di, do, nsteps, _stream(stream)), "stencil_step_host", h)
 
 
 def stencil_substep(h, fields_in, fields_out, substep, stream=None):
@@ -385,6 +395,9 @@ class Plan:
     # -- calls
     def step(self, fin, fout, nsteps=1, stream=None):
         stencil_step(self.h, fin, fout, nsteps, stream)
+
+    def step_host(self, host_in, host_out, dev_in, dev_out, nsteps=1, stream=None):
+        stencil_step_host(self.h, host_in, host_out, dev_in, dev_out, nsteps, stream)
 
     def substep(self, fin, fout, substep, stream=None):
         stencil_substep(self.h, fin, fout, substep, stream)

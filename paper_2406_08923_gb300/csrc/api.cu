@@ -195,6 +195,8 @@ static Ptrs8 ptrs(void *const *f, int n) {
 
 extern "C" {
 
+static stencil_status read_err(stencil_t p, cudaStream_t s);
+
 int stencil_abi_version(void) { return STENCIL_ABI_VERSION; }
 
 const char *stencil_strerror(stencil_status s) {
@@ -627,6 +629,26 @@ stencil_status stencil_step(stencil_t p, void *const *fin, void *const *fout, in
         src = dst;
     }
     return STENCIL_OK;
+}
+
+stencil_status stencil_step_host(stencil_t p, const void *const *host_in, void *const *host_out,
+                                 void *const *dev_in, void *const *dev_out, int nsteps, void *stream) {
+    if (!p) return fail(nullptr, STENCIL_EINVAL, "plan is NULL");
+    if (!host_in || !host_out) return fail(p, STENCIL_EINVAL, "host_in / host_out is NULL");
+    for (int q = 0; q < p->nfields; ++q)
+        if (!host_in[q] || !host_out[q])
+            return fail(p, STENCIL_EINVAL, "host field " + std::to_string(q) + " is NULL");
+    stencil_status st = check_device(p);
+    if (st != STENCIL_OK) return st;
+    if ((st = check_ptrs(p, dev_in, "dev_in")) != STENCIL_OK) return st;
+    if ((st = check_ptrs(p, dev_out, "dev_out")) != STENCIL_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int q = 0; q < p->nfields; ++q)
+        CK(p, cudaMemcpyAsync(dev_in[q], host_in[q], p->bytes_per_field, cudaMemcpyHostToDevice, s), "copy in");
+    if ((st = stencil_step(p, dev_in, dev_out, nsteps, stream)) != STENCIL_OK) return st;
+    for (int q = 0; q < p->nfields; ++q)
+        CK(p, cudaMemcpyAsync(host_out[q], dev_out[q], p->bytes_per_field, cudaMemcpyDeviceToHost, s), "copy out");
+    return read_err(p, s);
 }
 
 stencil_status stencil_substep(stencil_t p, void *const *fin, void *const *fout, int substep, void *stream) {

@@ -24,6 +24,7 @@
 //   * Bounded mbarrier waits; on expiry ERR_TIMEOUT is recorded and the CTA drains its
 //     in-flight loads before returning.
 #include <algorithm>
+#include <cstddef>
 
 #include "mhd_rhs.cuh"
 
@@ -345,14 +346,19 @@ static cudaError_t run(int sub, const MhdMaps &maps, const Ptrs8 &fo, const Ptrs
 
 // Variants per storage type: (TX, TY, NSLOT, min CTAs per SM for the register budget).
 #define MHD_VARIANTS_F64(X) X(32, 4, 8, 1) X(16, 8, 8, 1)
-#define MHD_VARIANTS_F32(X) X(32, 8, 8, 1) X(32, 4, 8, 2) X(16, 8, 8, 2)
-#define MHD_VARIANTS_BF16(X) X(32, 8, 8, 1) X(32, 8, 8, 2) X(32, 4, 8, 3)
+// The 512-thread tiles (32 x 16) hold one CTA per SM: its ring (229.5 KB for FP32) takes the
+// whole shared memory, and the 128-register budget of 512 threads holds the RHS without
+// spills, so 16 warps per SM stream 512 cells per plane (the 128-thread tiles: 8 warps, 256).
+#define MHD_VARIANTS_F32(X) X(32, 8, 8, 1) X(32, 4, 8, 2) X(16, 8, 8, 2) X(32, 16, 8, 1) X(32, 12, 8, 1)
+#define MHD_VARIANTS_BF16(X) X(32, 8, 8, 1) X(32, 8, 8, 2) X(32, 4, 8, 3) X(32, 16, 8, 1) X(64, 8, 8, 1)
 
 static const char *MHD_F64_NAMES[] = {"tx32_ty4_s8_b1", "tx16_ty8_s8_b1"};
-static const char *MHD_F32_NAMES[] = {"tx32_ty8_s8_b1", "tx32_ty4_s8_b2", "tx16_ty8_s8_b2"};
-static const char *MHD_BF16_NAMES[] = {"tx32_ty8_s8_b1", "tx32_ty8_s8_b2", "tx32_ty4_s8_b3"};
+static const char *MHD_F32_NAMES[] = {"tx32_ty8_s8_b1", "tx32_ty4_s8_b2", "tx16_ty8_s8_b2", "tx32_ty16_s8_b1",
+                                      "tx32_ty12_s8_b1"};
+static const char *MHD_BF16_NAMES[] = {"tx32_ty8_s8_b1", "tx32_ty8_s8_b2", "tx32_ty4_s8_b3", "tx32_ty16_s8_b1",
+                                       "tx64_ty8_s8_b1"};
 
-int mhd_num_variants(int storage) { return storage == 1 ? 2 : 3; }
+int mhd_num_variants(int storage) { return storage == 1 ? 2 : 5; }
 
 const char *mhd_variant_name(int storage, int v) {
     if (v < 0 || v >= mhd_num_variants(storage)) return "?";
@@ -426,10 +432,14 @@ mhd_batch_kernel(const BatchHeader *hdr, const BatchMhd *items, float alpha, flo
         const int tx = r % it.tiles_x;
         r /= it.tiles_x;
         const int ty = r % it.tiles_y, tz = r / it.tiles_y;
+        // the problem's constants, with this launch's RK coefficients in place of the table's
+        // (one writer per word: a separate write of alpha / beta would race with the copy)
         constexpr int KW = (int)(sizeof(MK<float>) / sizeof(float));
+        constexpr int IA = (int)(offsetof(MK<float>, alpha) / sizeof(float));
+        constexpr int IB = (int)(offsetof(MK<float>, beta) / sizeof(float));
         for (int i = threadIdx.x; i < KW; i += blockDim.x)
-            reinterpret_cast<float *>(&ks)[i] = reinterpret_cast<const float *>(&it.k)[i];
-        if (threadIdx.x == 0) { ks.alpha = alpha; ks.beta = beta; }
+            reinterpret_cast<float *>(&ks)[i] =
+                i == IA ? alpha : i == IB ? beta : reinterpret_cast<const float *>(&it.k)[i];
         __syncthreads();
         const Geom g = it.g;
         Ptrs8 none{};

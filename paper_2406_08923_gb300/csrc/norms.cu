@@ -15,6 +15,7 @@ namespace stn {
 constexpr int NORM_THREADS = 256;
 constexpr int NORM_BLOCKS = 2 * 152;
 constexpr int NORM_SEG = 4096;
+constexpr int NORM_U = 8;  // loads in flight per thread in pass 1
 
 int norms_blocks() { return NORM_BLOCKS; }
 
@@ -47,20 +48,35 @@ norms_pass1(Ptrs8 f, int nfields, Geom g, int mass0, double *partials) {
     for (int q = 0; q < nfields; ++q) {
         const S *base = static_cast<const S *>(f.p[q]);
         const bool do_mass = mass0 && q == 0;
-        double s = 0.0, s2 = 0.0, mx = 0.0, ms = 0.0;
+        double s = 0.0, s2 = 0.0, ms = 0.0;
+        // max |f| as the bit pattern of |f|: for non-negative doubles the unsigned order of the
+        // patterns is the numeric order, every NaN pattern lies above +inf (so a NaN wins), and
+        // no FP64 compare (a slow-pipe instruction on this GPU) is needed
+        unsigned long long mxb = 0ull;
+        auto add = [&](double v) {
+            s += v;
+            s2 += v * v;
+            mxb = max(mxb, (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull);
+            if (do_mass) ms += exp(v);
+        };
         for (int64_t piece = blockIdx.x; piece < rows * segs; piece += gridDim.x) {
             const int64_t row = piece / segs, sg = piece - row * segs;
             const int64_t y = row % g.n[1], z = row / g.n[1];
             const S *p = base + g.idx(0, y, z);
             const int64_t xe = min(nx, (sg + 1) * NORM_SEG);
-            for (int64_t x = sg * NORM_SEG + threadIdx.x; x < xe; x += NORM_THREADS) {
-                const double v = to_d(p[x]);
-                s += v;
-                s2 += v * v;
-                mx = nanmax(mx, fabs(v));
-                if (do_mass) ms += exp(v);
+            int64_t x = sg * NORM_SEG + threadIdx.x;
+            // NORM_U independent loads in flight per thread, then the same accumulation order
+            // (x, x + NORM_THREADS, ...) as one element at a time
+            for (; x + (NORM_U - 1) * NORM_THREADS < xe; x += NORM_U * NORM_THREADS) {
+                S v[NORM_U];
+#pragma unroll
+                for (int u = 0; u < NORM_U; ++u) v[u] = p[x + u * NORM_THREADS];
+#pragma unroll
+                for (int u = 0; u < NORM_U; ++u) add(to_d(v[u]));
             }
+            for (; x < xe; x += NORM_THREADS) add(to_d(p[x]));
         }
+        double mx = __longlong_as_double((long long)mxb);
         warp_reduce(s, s2, mx, ms);
         if (lane == 0) { red[0][warp] = s; red[1][warp] = s2; red[2][warp] = mx; red[3][warp] = ms; }
         __syncthreads();

@@ -3,8 +3,10 @@ server of libstencil (stencil_server_*), plus the plain per-grid path it is comp
 
 The request mix follows the serving configuration: grid sizes n log-uniform in [32, 192]
 (rounded to a multiple of 8 so that one input template per kind and size can be kept in
-page-locked memory), kinds uniform over {1D cross-correlation of n^3 cells, 3D heat
-equation, 8-field MHD system}, 10..50 steps each, FP32, Poisson arrivals.  Latency is
+page-locked memory; with round_to=1 the sizes are not rounded, and an input of a ragged size
+is the leading n^3 block of the template of the next multiple of 8), kinds uniform over
+{1D cross-correlation of n^3 cells, 3D heat equation, 8-field MHD system}, 10..50 steps each,
+FP32, Poisson arrivals.  Latency is
 measured open-loop: from a request's scheduled arrival time to the moment its result is in
 host memory.
 
@@ -99,6 +101,16 @@ class Templates:
 
     def get(self, kind, n):
         key = (kind, n)
+        if key not in self.cache and n % 8:
+            import torch
+            m = (n + 7) // 8 * 8
+            base = self.get(kind, m)
+            ts = []
+            for t in base:
+                blk = t[:n ** 3] if kind == L.STENCIL_XCORR else t.view(m, m, m)[:n, :n, :n]
+                c = blk.contiguous().clone()
+                ts.append(c.pin_memory() if self.pinned else c)
+            self.cache[key] = ts
         if key not in self.cache:
             import torch
             if kind == L.STENCIL_XCORR:

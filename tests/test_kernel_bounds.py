@@ -179,7 +179,7 @@ def test_tma_loads_start_on_16_byte_boundaries():
     families.append((8, 4, [64, 128], range(1, 5)))            # 3D heat FP64 (TX = 64 VP)
     families.append((4, 4, [128], range(1, 5)))                 # 3D heat FP32
     families += [(e, 4, [32 * vx for vx in (1, 2, 4)], range(1, 5)) for e in (4, 8)]  # 2D heat
-    families += [(e, max(16 // e, 4), [16, 32], [3]) for e in (8, 4, 2)]              # MHD
+    families += [(e, max(16 // e, 4), [16, 32, 64], [3]) for e in (8, 4, 2)]          # MHD
     for esize, hx, txs, radii in families:
         for r in radii:
             assert hx >= r  # the x halo in shared memory covers the stencil
@@ -244,3 +244,30 @@ def test_wide_kernels_stay_in_their_buffers():
             assert (mf - 1) + (w - length) <= span - length  # the last read is a defined run
             nbuf = 2 if r == 0 else 1
             assert (nbuf + 1) * be * esize <= SMEM_MAX
+
+
+# ---------------------------------------------------------------------------------------------
+# MHD (csrc/mhd.cu): every variant's plane ring fits the shared memory of one CTA, and its
+# threads fit the register file at the register count its launch bounds allow.
+
+
+def test_mhd_variants_fit_shared_memory_and_registers():
+    src = _read("mhd.cu")
+    for text in ("static constexpr int TXP = TX + 2 * HX;", "static constexpr int ROWS = TY + 2 * R6;",
+                 "static constexpr int FIELD_ELEMS = ((TXP * ROWS * (int)sizeof(S) + 127) / 128) * 128 / (int)sizeof(S);",
+                 "static constexpr int SLOT_ELEMS = 8 * FIELD_ELEMS;",
+                 "static constexpr size_t SMEM = (size_t)NSLOT * SLOT_ELEMS * sizeof(S) + 128;"):
+        assert text in src, text
+    for esize, macro in ((8, "MHD_VARIANTS_F64"), (4, "MHD_VARIANTS_F32"), (2, "MHD_VARIANTS_BF16")):
+        line = re.search(r"#define " + macro + r"\(X\)(.*)", src).group(1)
+        variants = [tuple(int(v) for v in m) for m in re.findall(r"X\((\d+), (\d+), (\d+), (\d+)\)", line)]
+        assert variants, macro
+        hx = max(16 // esize, 4)
+        for tx, ty, nslot, minb in variants:
+            field = ((tx + 2 * hx) * (ty + 6) * esize + 127) // 128 * 128
+            smem = nslot * 8 * field + 128
+            assert smem <= SMEM_MAX, (macro, tx, ty, smem)
+            assert minb * (smem + 64 + 1024) <= 233472, (macro, tx, ty, minb)  # CTAs per SM
+            threads = tx * ty
+            assert threads <= 1024 and threads % 32 == 0
+            assert 65536 // (threads * minb) >= 64, (macro, tx, ty)  # registers per thread
