@@ -128,6 +128,9 @@ template <typename C> struct MK {
     C cs0sq, gamma, inv_cp, lnrho0, nu, eta, zeta, mu0, inv_mu0, cp_gm1;
     C K;
     C dt, alpha, beta;
+    // derived constants, so that every operand of the explicit arithmetic is a member
+    C gcp, gm1, etamu0, two_nu;  // gamma / cp, gamma - 1, eta mu0, 2 nu
+    C one, mone, half, two, third, mthird;
 };
 
 // Work items of one batched launch.  Every item owns a contiguous range of virtual CTAs
@@ -177,5 +180,7 @@ void diffusion_batch_tile(int *tx, int *ty, int box[3]);
 void mhd_batch_tile(int *tx, int *ty, int box[3]);
 int xcorr_batch_chunk();
 void mhd_scaled_constants(const MhdConst &c, MK<float> *k);
+// FP32 constants of RK substep `sub` (its alpha and beta filled in)
+void mhd_substep_constants(const MhdConst &c, int sub, MK<float> *k);
 
 }  // namespace stn

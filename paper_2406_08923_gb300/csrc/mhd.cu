@@ -30,135 +30,47 @@
 
 namespace stn {
 
-template <typename S, int TX, int TY, int NSLOT>
-struct MhdCfg {
-    static constexpr int HX = 16 / (int)sizeof(S) >= 4 ? 16 / (int)sizeof(S) : 4;
-    static constexpr int TXP = TX + 2 * HX;
-    static constexpr int ROWS = TY + 2 * R6;
-    static constexpr int FIELD_ELEMS = ((TXP * ROWS * (int)sizeof(S) + 127) / 128) * 128 / (int)sizeof(S);
-    static constexpr int SLOT_ELEMS = 8 * FIELD_ELEMS;
-    static constexpr uint32_t BOX_BYTES = TXP * ROWS * sizeof(S);
-    static constexpr size_t SMEM = (size_t)NSLOT * SLOT_ELEMS * sizeof(S) + 128;
-    static_assert((TXP * sizeof(S)) % 16 == 0, "TMA box inner extent must be a multiple of 16 B");
-    static_assert(NSLOT >= 8, "ring holds 7 planes plus at least one in flight");
-    static_assert((NSLOT & (NSLOT - 1)) == 0, "ring depth is a power of two");
-};
-
 // The 7-plane window of all fields around one cell: p[k] points at the cell (field 0) in
-// plane z + k - 3; field q is FE elements further, row neighbours RS elements apart.
+// plane z + k - 3; field q is FE elements further, row neighbours RS elements apart.  Its
+// 6th-order central differences (weights pre-scaled by the grid spacing) are written out one
+// IEEE operation at a time (mhd_rhs.cuh says why).
 template <typename C, typename S, int FE, int RS>
 struct Win {
     const S *p[7];
     __device__ __forceinline__ C at(int q, int k, int dx, int dy) const {
         return to_c<C>(p[k][q * FE + dy * RS + dx]);
     }
+    __device__ __forceinline__ C val(int q) const { return at(q, 3, 0, 0); }
+    // value at offset s along axis (0: x, 1: y, 2: z)
+    __device__ __forceinline__ C ax(int q, int axis, int s) const {
+        return axis == 0 ? at(q, 3, s, 0) : axis == 1 ? at(q, 3, 0, s) : at(q, 3 + s, 0, 0);
+    }
+    // first derivative: c0 (f1 - f-1) + c1 (f2 - f-2) + c2 (f3 - f-3)
+    __device__ __forceinline__ C d1(int q, int axis, const C *c) const {
+        C a = mul(c[0], sub(ax(q, axis, 1), ax(q, axis, -1)));
+        a = fmad(c[1], sub(ax(q, axis, 2), ax(q, axis, -2)), a);
+        return fmad(c[2], sub(ax(q, axis, 3), ax(q, axis, -3)), a);
+    }
+    // second derivative: c0 f0 + c1 (f1 + f-1) + c2 (f2 + f-2) + c3 (f3 + f-3)
+    __device__ __forceinline__ C d2(int q, int axis, C c0, const C *c) const {
+        C a = mul(c0, ax(q, axis, 0));
+        a = fmad(c[0], add(ax(q, axis, 1), ax(q, axis, -1)), a);
+        a = fmad(c[1], add(ax(q, axis, 2), ax(q, axis, -2)), a);
+        return fmad(c[2], add(ax(q, axis, 3), ax(q, axis, -3)), a);
+    }
+    // mixed derivative of axes (a1 < a2), diagonal form:
+    // sum_a m_a [(f(+a,+a) + f(-a,-a)) - (f(+a,-a) + f(-a,+a))]
+    __device__ __forceinline__ C mx(int q, int pair, int s1, int s2) const {
+        return pair == 0 ? at(q, 3, s1, s2) : pair == 1 ? at(q, 3 + s2, s1, 0) : at(q, 3 + s2, 0, s1);
+    }
+    __device__ __forceinline__ C dmix(int q, int pair, const C *m) const {
+        C acc = mul(m[0], sub(add(mx(q, pair, 1, 1), mx(q, pair, -1, -1)), add(mx(q, pair, 1, -1), mx(q, pair, -1, 1))));
+        acc = fmad(m[1], sub(add(mx(q, pair, 2, 2), mx(q, pair, -2, -2)), add(mx(q, pair, 2, -2), mx(q, pair, -2, 2))),
+                   acc);
+        return fmad(m[2], sub(add(mx(q, pair, 3, 3), mx(q, pair, -3, -3)), add(mx(q, pair, 3, -3), mx(q, pair, -3, 3))),
+                    acc);
+    }
 };
-
-// 6th-order central differences on the window (weights pre-scaled by the grid spacing).
-// First derivative along x (axis 0), y (axis 1), z (axis 2).
-template <typename C, typename W>
-__device__ __forceinline__ C d1(const W &w, int q, int axis, const C *c) {
-    auto f = [&](int s) {
-        return axis == 0 ? w.at(q, 3, s, 0) : axis == 1 ? w.at(q, 3, 0, s) : w.at(q, 3 + s, 0, 0);
-    };
-    C a = c[0] * (f(1) - f(-1));
-    a = fma(c[1], f(2) - f(-2), a);
-    return fma(c[2], f(3) - f(-3), a);
-}
-template <typename C, typename W>
-__device__ __forceinline__ C d2(const W &w, int q, int axis, C c0, const C *c) {
-    auto f = [&](int s) {
-        return axis == 0 ? w.at(q, 3, s, 0) : axis == 1 ? w.at(q, 3, 0, s) : w.at(q, 3 + s, 0, 0);
-    };
-    C a = c0 * f(0);
-    a = fma(c[0], f(1) + f(-1), a);
-    a = fma(c[1], f(2) + f(-2), a);
-    return fma(c[2], f(3) + f(-3), a);
-}
-// mixed derivative of axes (a1 < a2): sum_a m_a [(f(+a,+a) + f(-a,-a)) - (f(+a,-a) + f(-a,+a))]
-template <typename C, typename W>
-__device__ __forceinline__ C dmix(const W &w, int q, int pair, const C *m) {
-    auto f = [&](int s1, int s2) {
-        return pair == 0 ? w.at(q, 3, s1, s2) : pair == 1 ? w.at(q, 3 + s2, s1, 0) : w.at(q, 3 + s2, 0, s1);
-    };
-    C acc = m[0] * ((f(1, 1) + f(-1, -1)) - (f(1, -1) + f(-1, 1)));
-    acc = fma(m[1], (f(2, 2) + f(-2, -2)) - (f(2, -2) + f(-2, 2)), acc);
-    return fma(m[2], (f(3, 3) + f(-3, -3)) - (f(3, -3) + f(-3, 3)), acc);
-}
-
-// The right-hand side of Eqs. A1-A4 at one cell (H = C = 0); val[q] = f_q at the cell.  The
-// derivatives are evaluated field by field, only those some term uses (lnrho and s: gradients,
-// plus Laplacians when K != 0; A: the off-diagonal first derivatives and the Hessian), then
-// assembled by mhd_rhs_assemble.
-template <bool CONDUCT, typename C, typename W>
-__device__ __forceinline__ void mhd_rhs_cell(const W &w, const MK<C> &k, C *rhs, C *val) {
-    MhdDerivs<C> d;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) d.val[q] = w.at(q, 3, 0, 0);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        d.glr[a] = d1(w, F_LNRHO, a, k.d1[a]);
-        d.gs[a] = d1(w, F_SS, a, k.d1[a]);
-    }
-    d.laplr = d.laps = C(0);
-    if constexpr (CONDUCT) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            d.laplr += d2(w, F_LNRHO, a, k.d2c[a], k.d2[a]);
-            d.laps += d2(w, F_SS, a, k.d2c[a], k.d2[a]);
-        }
-    }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) d.gdivu[c] = d.gdiva[c] = C(0);
-    // velocity: gu[i][a] = d u_i / d x_a; lap u; grad div u accumulated per component
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const int q = F_UX + c;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) d.gu[c][a] = d1(w, q, a, k.d1[a]);
-        C hxx = d2(w, q, 0, k.d2c[0], k.d2[0]);
-        C hyy = d2(w, q, 1, k.d2c[1], k.d2[1]);
-        C hzz = d2(w, q, 2, k.d2c[2], k.d2[2]);
-        C hxy = dmix(w, q, 0, k.dm[0]);
-        C hxz = dmix(w, q, 1, k.dm[1]);
-        C hyz = dmix(w, q, 2, k.dm[2]);
-        d.lapu[c] = hxx + hyy + hzz;
-        // grad(div u)_x += d_x d_c u_c, etc.
-        const C hc[3] = {c == 0 ? hxx : c == 1 ? hxy : hxz, c == 0 ? hxy : c == 1 ? hyy : hyz,
-                         c == 0 ? hxz : c == 1 ? hyz : hzz};
-        d.gdivu[0] += hc[0];
-        d.gdivu[1] += hc[1];
-        d.gdivu[2] += hc[2];
-    }
-    // vector potential: B = curl A (off-diagonal first derivatives only), j = (grad div A - lap A)/mu0
-    {
-        const C ax_y = d1(w, F_AX, 1, k.d1[1]), ax_z = d1(w, F_AX, 2, k.d1[2]);
-        const C ay_x = d1(w, F_AY, 0, k.d1[0]), ay_z = d1(w, F_AY, 2, k.d1[2]);
-        const C az_x = d1(w, F_AZ, 0, k.d1[0]), az_y = d1(w, F_AZ, 1, k.d1[1]);
-        d.bx = az_y - ay_z;
-        d.by = ax_z - az_x;
-        d.bz = ay_x - ax_y;
-    }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const int q = F_AX + c;
-        C hxx = d2(w, q, 0, k.d2c[0], k.d2[0]);
-        C hyy = d2(w, q, 1, k.d2c[1], k.d2[1]);
-        C hzz = d2(w, q, 2, k.d2c[2], k.d2[2]);
-        C hxy = dmix(w, q, 0, k.dm[0]);
-        C hxz = dmix(w, q, 1, k.dm[1]);
-        C hyz = dmix(w, q, 2, k.dm[2]);
-        d.lapa[c] = hxx + hyy + hzz;
-        const C hc[3] = {c == 0 ? hxx : c == 1 ? hxy : hxz, c == 0 ? hxy : c == 1 ? hyy : hyz,
-                         c == 0 ? hxz : c == 1 ? hyz : hzz};
-        d.gdiva[0] += hc[0];
-        d.gdiva[1] += hc[1];
-        d.gdiva[2] += hc[2];
-    }
-    mhd_rhs_assemble<CONDUCT>(d, k, rhs);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) val[q] = d.val[q];
-}
 
 // One xy-tile of one z-chunk of one RK substep (or RHS evaluation): the whole pipeline of a
 // CTA.  `maps` points at 8 consecutive descriptors (parameter or global memory); `k` may live
@@ -242,17 +154,14 @@ __device__ __forceinline__ bool mhd_tile(const CUtensorMap *maps, const Ptrs8 &f
                 for (int q = 0; q < 8; ++q) static_cast<C *>(rbuf.p[q])[cell] = rhs[q];
             } else {
                 S fnew[8];
+                auto rt = [](C v) { return to_c<C>(to_s<S>(v)); };  // round to the storage type
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
-                    const C wv = first ? k.dt * rhs[q] : fma(k.alpha, wcur[q], k.dt * rhs[q]);
+                    C wv, fv, kv;
+                    rk_update<KAHAN>(k, first != 0, rhs[q], wcur[q], kcur[q], val[q], wv, fv, kv, rt);
                     if (!last) static_cast<S *>(wbuf.p[q])[cell] = to_s<S>(wv);
-                    if (KAHAN) {
-                        const C yv = k.beta * wv - kcur[q];
-                        fnew[q] = to_s<S>(val[q] + yv);
-                        static_cast<S *>(kbuf.p[q])[cell] = to_s<S>((to_c<C>(fnew[q]) - val[q]) - yv);
-                    } else {
-                        fnew[q] = to_s<S>(fma(k.beta, wv, val[q]));
-                    }
+                    if (KAHAN) static_cast<S *>(kbuf.p[q])[cell] = to_s<S>(kv);
+                    fnew[q] = to_s<S>(fv);
                 }
                 if (images && (edge_xy || z < R6 || z >= nz - R6)) {
 #pragma unroll
@@ -288,7 +197,7 @@ mhd_kernel(const __grid_constant__ MhdMaps maps, Ptrs8 fout, Ptrs8 wbuf, Ptrs8 k
     __shared__ __align__(8) uint64_t full[NSLOT];
     (void)Cfg::SMEM;
     mhd_tile<S, C, KAHAN, MODE, TX, TY, NSLOT, CONDUCT>(maps.m, fout, wbuf, kbuf, rbuf, g, k, blockIdx.x, blockIdx.y,
-                                               blockIdx.z, zc, first, last, images, err, ring, full);
+                                                        blockIdx.z, zc, first, last, images, err, ring, full);
 }
 
 // ------------------------------------------------------------------ host side
@@ -307,6 +216,9 @@ static MK<C> make_k(const MhdConst &c, double alpha, double beta) {
     k.cs0sq = (C)c.cs0sq; k.gamma = (C)c.gamma; k.inv_cp = (C)c.inv_cp; k.lnrho0 = (C)c.lnrho0;
     k.nu = (C)c.nu; k.eta = (C)c.eta; k.zeta = (C)c.zeta; k.mu0 = (C)c.mu0; k.inv_mu0 = (C)c.inv_mu0;
     k.cp_gm1 = (C)c.cp_gm1; k.K = (C)c.K; k.dt = (C)c.dt; k.alpha = (C)alpha; k.beta = (C)beta;
+    k.gcp = (C)(c.gamma * c.inv_cp); k.gm1 = (C)(c.gamma - 1.0); k.etamu0 = (C)(c.eta * c.mu0);
+    k.two_nu = (C)(2.0 * c.nu); k.one = (C)1.0; k.mone = (C)-1.0; k.half = (C)0.5; k.two = (C)2.0;
+    k.third = (C)(1.0 / 3.0); k.mthird = (C)(-1.0 / 3.0);
     return k;
 }
 
@@ -478,6 +390,8 @@ void mhd_batch_tile(int *tx, int *ty, int box[3]) {
 }
 
 void mhd_scaled_constants(const MhdConst &c, MK<float> *k) { *k = make_k<float>(c, 0.0, 0.0); }
+
+void mhd_substep_constants(const MhdConst &c, int sub, MK<float> *k) { *k = make_k<float>(c, RK_A[sub], RK_B[sub]); }
 
 cudaError_t launch_mhd_batch(const BatchHeader *hdr, const BatchMhd *items, int sub, unsigned *err, int grid,
                              cudaStream_t s) {

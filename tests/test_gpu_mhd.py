@@ -171,11 +171,11 @@ def test_heat_conduction_steps_against_oracle(cuda_lib):
 
 
 @pytest.mark.parametrize("storage", (L.STENCIL_F32, L.STENCIL_BF16))
-@pytest.mark.parametrize("nx", (70, 72))
+@pytest.mark.parametrize("nx", (70, 71, 72))
 def test_every_variant_is_bit_identical(cuda_lib, storage, nx):
-    # every variant performs the same IEEE operations per cell (only the tile shape and ring
-    # differ), so whole RK3 steps agree bit for bit, periodic images included; both widths
-    # overhang the tiles
+    # every variant performs the same IEEE operations per cell (only the tile shape and the ring
+    # differ), so whole RK3 steps agree bit for bit, periodic images included; every width
+    # (odd and even) overhangs the tiles
     shape = (40, 20, nx)
     f8 = synth.mhd_fields(shape, seed=41) * 20.0
     p, par = mhd_plan(shape, storage)

@@ -174,7 +174,7 @@ def test_tma_loads_start_on_16_byte_boundaries():
     assert "static constexpr int HX = 4;" in _read("diffusion.cu")
     assert "TX = 128, HX = 4" in _read("diffusion_f32.cu")
     assert "TX = 32 * VX, HX = 4" in _read("diffusion2d.cu")
-    assert "HX = 16 / (int)sizeof(S) >= 4 ? 16 / (int)sizeof(S) : 4;" in _read("mhd.cu")
+    assert "HX = 16 / (int)sizeof(S) >= 4 ? 16 / (int)sizeof(S) : 4;" in _read("mhd_rhs.cuh")
     families = []  # (esize, HX, tile widths, radii)
     families.append((8, 4, [64, 128], range(1, 5)))            # 3D heat FP64 (TX = 64 VP)
     families.append((4, 4, [128], range(1, 5)))                 # 3D heat FP32
@@ -252,14 +252,15 @@ def test_wide_kernels_stay_in_their_buffers():
 
 
 def test_mhd_variants_fit_shared_memory_and_registers():
-    src = _read("mhd.cu")
+    src = _read("mhd_rhs.cuh")
     for text in ("static constexpr int TXP = TX + 2 * HX;", "static constexpr int ROWS = TY + 2 * R6;",
                  "static constexpr int FIELD_ELEMS = ((TXP * ROWS * (int)sizeof(S) + 127) / 128) * 128 / (int)sizeof(S);",
                  "static constexpr int SLOT_ELEMS = 8 * FIELD_ELEMS;",
                  "static constexpr size_t SMEM = (size_t)NSLOT * SLOT_ELEMS * sizeof(S) + 128;"):
         assert text in src, text
+    tables = _read("mhd.cu")
     for esize, macro in ((8, "MHD_VARIANTS_F64"), (4, "MHD_VARIANTS_F32"), (2, "MHD_VARIANTS_BF16")):
-        line = re.search(r"#define " + macro + r"\(X\)(.*)", src).group(1)
+        line = re.search(r"#define " + macro + r"\(X\)(.*)", tables).group(1)
         variants = [tuple(int(v) for v in m) for m in re.findall(r"X\((\d+), (\d+), (\d+), (\d+)\)", line)]
         assert variants, macro
         hx = max(16 // esize, 4)
