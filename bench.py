@@ -396,6 +396,11 @@ def run_serving_leg(n_requests=1024, load=0.7, fp64_subset=96, sweep=(0.5, 1.2))
         templates.get(r.kind, r.n)
     t_gen = time.perf_counter() - t_gen
     work = sum(r.work() for r in reqs)
+    # the batched kernels' tile shapes: the autotuner's choice for FP32 plans of each kind (the
+    # FP32 heat and MHD legs above tuned them in this process)
+    probe = L.stencil_server_create(10 ** 9, 4)
+    tiles = {serving.KIND_NAMES[k]: L.stencil_server_variant(probe, k) for k in serving.KINDS}
+    L.stencil_server_destroy(probe)
     # warm-up: a few small requests (module load, graph instantiation, pool growth)
     warm = [serving.Request(i, k, 32, 2) for i, k in enumerate(serving.KINDS)]
     serving.serve(warm, templates)
@@ -461,7 +466,7 @@ def run_serving_leg(n_requests=1024, load=0.7, fp64_subset=96, sweep=(0.5, 1.2))
         "requests": n_requests, "mix": "n log-uniform 32..192 (rounded to multiples of 8, so that one pinned input "
                                         "template per kind and size is kept; ragged_sizes runs unrounded n), kinds "
                                         "uniform {xcorr1d n^3, heat3d, mhd8}, 10-50 steps, FP32, Poisson arrivals",
-        "budget_gb": 120, "template_gen_s": round(t_gen, 1),
+        "budget_gb": 120, "template_gen_s": round(t_gen, 1), "batched_tiles": tiles,
         "work_gcell_updates": round(work / 1e9, 2),
         "saturation": {"wall_s": round(wall_sat, 3), "requests_per_s": round(cap_rps, 1),
                        "mcell_updates_per_s": round(work / wall_sat / 1e6, 1), "peak_gb": round(peak_sat / 1e9, 2)},
@@ -726,6 +731,7 @@ def run_extras(L, synth, stream, hbm_peak, args):
         "ms_per_job": round(res["ms_job"], 4), "kernel_ms_avg": round(res["ms_kernel"], 5),
         "mcell_updates_per_s": round(cells * HEAT_STEPS / (res["ms_job"] / 1e3) / 1e6, 1),
         "variant": res["variant"],
+        "zchunk_mode": res["plan"].autotune_status()[1],
         "roofline": _roof("hbm", gbs, hbm_peak, "GB/s", traffic=_traffic("heat_f32", res["variant"]),
                           note="8 B/cell-update algorithmic; traffic = ncu dram bytes/launch")}
     res["plan"].close()

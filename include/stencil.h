@@ -293,14 +293,29 @@ stencil_status stencil_sync(stencil_t plan, void *stream);
  * thread-block decomposition (Sec. 5.1), stencil_autotune times every variant on the
  * caller's buffers (one warm-up call, then `reps` timed calls of stencil_step(nsteps) with
  * CUDA events on `stream`), discards variants that fail to launch, and keeps the fastest.
- * It overwrites fields_out and synchronises `stream`.  stencil_get_variant reports the
- * current variant, the number of variants and the current variant's name (static string);
- * any output pointer may be NULL.  stencil_set_variant selects one (EINVAL if out of range).
+ * For the z-streaming 3D kernels (DIFFUSION in 3D, MHD8) the search also covers the z-chunk
+ * length each CTA streams: the kernel's own choice, half of it, or twice it.  It overwrites
+ * fields_out and synchronises `stream`.
+ *
+ * The winner is remembered for the problem class -- GPU name and SM count, kind, storage,
+ * radius, boundary, dims and nsteps -- for the rest of the process and, when the environment
+ * variable STENCIL_AUTOTUNE_CACHE names a writable file, in that file (one line appended per
+ * tuned class; read on first use).  A later stencil_autotune of the same class takes the
+ * remembered choice without timing anything.  stencil_autotune_status reports whether the
+ * current choice came from that cache (1) or from timing (0), its z-chunk mode (0, 1, 2) and
+ * the time of one stencil_step(nsteps) call it measured (ms); outputs may be NULL.
+ *
+ * stencil_get_variant reports the current variant, the number of variants and the current
+ * variant's name (static string); any output pointer may be NULL.  stencil_set_variant selects
+ * one (EINVAL if out of range), stencil_set_zmode a z-chunk mode (0 for plans of other kinds;
+ * EINVAL if out of range).  Neither changes the results, only how the work is tiled.
  */
 stencil_status stencil_get_variant(stencil_t plan, int *variant, int *count, const char **name);
 stencil_status stencil_set_variant(stencil_t plan, int variant);
 stencil_status stencil_autotune(stencil_t plan, void *const *fields_in, void *const *fields_out,
                                 int nsteps, int reps, void *stream);
+stencil_status stencil_autotune_status(stencil_t plan, int *from_cache, int *zmode, float *ms);
+stencil_status stencil_set_zmode(stencil_t plan, int zmode);
 
 /*
  * Continuous-batching server.  Many independent problems of different kinds and sizes are
@@ -350,6 +365,11 @@ stencil_status stencil_server_submit(stencil_server_t server, const stencil_requ
  * without waiting for the GPU.  Any output pointer may be NULL. */
 stencil_status stencil_server_progress(stencil_server_t server, int *n_pending, int *n_active,
                                        int *n_done);
+/* Name of the batched kernel's tile shape this server runs for `kind` (static string).  The
+ * heat and MHD kernels each come in two tile shapes; at creation the server takes the shape of
+ * the per-grid variant that stencil_autotune last chose for an FP32 periodic radius-3 plan of
+ * that kind on this GPU (this process, or the STENCIL_AUTOTUNE_CACHE file), else the default. */
+const char *stencil_server_variant(stencil_server_t server, stencil_kind kind);
 /* State of a ticket (STENCIL_REQ_*). */
 stencil_status stencil_server_poll(stencil_server_t server, int64_t ticket, int *state);
 /*

@@ -31,7 +31,8 @@ EXPORTED = (
     "stencil_set_variant", "stencil_autotune", "stencil_field_norms_noalloc", "stencil_selftest_wait",
     "stencil_server_create", "stencil_server_destroy", "stencil_server_submit", "stencil_server_progress",
     "stencil_server_poll", "stencil_server_stats", "stencil_server_sync", "stencil_server_last_error_detail",
-    "stencil_server_cancel", "stencil_substep", "stencil_step_host",
+    "stencil_server_cancel", "stencil_substep", "stencil_step_host", "stencil_autotune_status",
+    "stencil_server_variant", "stencil_set_zmode",
 )
 
 STENCIL_REQ_PENDING, STENCIL_REQ_ACTIVE, STENCIL_REQ_COMPLETING, STENCIL_REQ_DONE, STENCIL_REQ_CANCELLED = range(5)
@@ -88,7 +89,9 @@ def load():
             "stencil_abi_version": (I, []),
             "stencil_get_variant": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(ctypes.c_char_p)]),
             "stencil_set_variant": (I, [P, I]),
+            "stencil_set_zmode": (I, [P, I]),
             "stencil_autotune": (I, [P, PP, PP, I, I, P]),
+            "stencil_autotune_status": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(ctypes.c_float)]),
             "stencil_selftest_wait": (I, [P, I64, P]),
             "stencil_server_create": (I, [I64, I, P, ctypes.POINTER(P)]),
             "stencil_server_destroy": (None, [P]),
@@ -99,6 +102,7 @@ def load():
             "stencil_server_stats": (I, [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)]),
             "stencil_server_sync": (I, [P]),
             "stencil_server_last_error_detail": (ctypes.c_char_p, [P]),
+            "stencil_server_variant": (ctypes.c_char_p, [P, I]),
             "stencil_field_norms_noalloc": (I, [PP, I, I, ctypes.POINTER(I64), ctypes.POINTER(I64),
                                                 ctypes.POINTER(I64), D, P, P]),
         }
@@ -220,6 +224,14 @@ def stencil_autotune(h, fields_in, fields_out, nsteps=1, reps=3, stream=None):
     _check(load().stencil_autotune(h, pi, po, nsteps, reps, _stream(stream)), "stencil_autotune", h)
 
 
+def stencil_autotune_status(h):
+    """(from_cache, zmode, ms) of the plan's current tuned choice."""
+    c, z, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+    _check(load().stencil_autotune_status(h, ctypes.byref(c), ctypes.byref(z), ctypes.byref(ms)),
+           "stencil_autotune_status", h)
+    return bool(c.value), z.value, ms.value
+
+
 def stencil_selftest_wait(h, limit_ns, stream=None):
     _check(load().stencil_selftest_wait(h, int(limit_ns), _stream(stream)), "stencil_selftest_wait", h)
 
@@ -313,6 +325,10 @@ def stencil_server_stats(h):
     _scheck(load().stencil_server_stats(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
             "stencil_server_stats", h)
     return a.value, b.value, c.value
+
+
+def stencil_server_variant(h, kind):
+    return load().stencil_server_variant(h, int(kind)).decode()
 
 
 def stencil_server_sync(h):
@@ -427,6 +443,12 @@ class Plan:
     def autotune(self, fin, fout, nsteps=1, reps=3, stream=None):
         stencil_autotune(self.h, fin, fout, nsteps, reps, stream)
         return self.variant()
+
+    def autotune_status(self):
+        return stencil_autotune_status(self.h)
+
+    def set_zmode(self, zmode):
+        _check(load().stencil_set_zmode(self.h, int(zmode)), "stencil_set_zmode", self.h)
 
 
 def mhd_params(n, dt=None, **kw) -> stencil_params:

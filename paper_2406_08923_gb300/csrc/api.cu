@@ -5,7 +5,12 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -84,6 +89,9 @@ struct stencil_plan {
     unsigned *err = nullptr;
     void *wdev = nullptr;  // XCORR of radius > 4: the 2r+1 weights on the device (storage type)
     int variant = 0;
+    int zmode = 0;           // z-chunk length mode of the streaming kernels (zchunk_len)
+    int tuned_from_cache = 0;
+    float tuned_ms = 0.f;
     std::vector<TmaEntry> tma;
     std::string detail;
 };
@@ -191,6 +199,93 @@ static Ptrs8 ptrs(void *const *f, int n) {
     Ptrs8 r{};
     for (int q = 0; q < n; ++q) r.p[q] = f[q];
     return r;
+}
+
+// ------------------------------------------------------------------ autotuning cache
+// Winners of stencil_autotune, kept for the life of the process and, when the environment
+// variable STENCIL_AUTOTUNE_CACHE names a file, in that file: one line per problem class,
+// "key <TAB> variant name <TAB> z-chunk mode <TAB> ms".  The key holds the GPU's name and SM
+// count, the kind, storage, radius, boundary, dims and steps per call, so a choice is reused only
+// for the same problem on the same kind of GPU.  Later lines win; a damaged line is skipped.
+namespace {
+struct TuneRec {
+    std::string variant;
+    int zmode = 0;
+    float ms = 0.f;
+};
+std::mutex g_tune_mu;
+std::map<std::string, TuneRec> g_tune;
+std::map<std::string, std::string> g_tune_last;  // problem-class prefix (no dims / steps) -> last winner
+std::string g_tune_loaded;                       // path whose lines are in g_tune
+
+void tune_put_locked(const std::string &key, const TuneRec &rec) {
+    g_tune[key] = rec;
+    const size_t cut = key.find("|d3:");
+    if (cut != std::string::npos) g_tune_last[key.substr(0, cut + 4)] = rec.variant;
+}
+
+std::string tune_path() {
+    const char *e = std::getenv("STENCIL_AUTOTUNE_CACHE");
+    return e ? std::string(e) : std::string();
+}
+
+void tune_load_locked(const std::string &path) {
+    if (path.empty() || path == g_tune_loaded) return;
+    g_tune_loaded = path;
+    std::ifstream in(path);
+    std::string line;
+    while (std::getline(in, line)) {
+        std::istringstream ls(line);
+        std::string key, var, zm, ms;
+        if (!std::getline(ls, key, '\t') || !std::getline(ls, var, '\t') || !std::getline(ls, zm, '\t') ||
+            !std::getline(ls, ms))
+            continue;
+        char *end = nullptr;
+        const long z = std::strtol(zm.c_str(), &end, 10);
+        if (end == zm.c_str() || z < 0 || z >= ZMODES || var.empty()) continue;
+        tune_put_locked(key, TuneRec{var, (int)z, std::strtof(ms.c_str(), nullptr)});
+    }
+}
+
+std::string gpu_tag(int dev) {
+    static std::string tags[64];
+    if (dev < 0 || dev >= 64) return "gpu?";
+    if (tags[dev].empty()) {
+        cudaDeviceProp pr{};
+        if (cudaGetDeviceProperties(&pr, dev) != cudaSuccess) return "gpu?";
+        std::string n = pr.name;
+        for (auto &ch : n)
+            if (ch == '\t' || ch == ' ') ch = '_';
+        tags[dev] = n + "_sm" + std::to_string(pr.multiProcessorCount);
+    }
+    return tags[dev];
+}
+}  // namespace
+
+namespace stn {
+int tuned_batch_shape(int kind) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    const std::string pref = gpu_tag(dev) + "|k" + std::to_string(kind) + "|s" + std::to_string((int)STENCIL_F32) +
+                             "|r3|bc" + std::to_string((int)STENCIL_BC_PERIODIC) + "|d3:";
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    tune_load_locked(tune_path());
+    auto it = g_tune_last.find(pref);
+    if (it == g_tune_last.end()) return -1;
+    // the batched shapes: heat 0 = 4 warps x 2 rows, 1 = 8 warps x 2 rows; MHD 0 = 32 x 4 with
+    // two CTAs per SM, 1 = 32 x 12 with one
+    const std::string &v = it->second;
+    if (kind == STENCIL_DIFFUSION) return v.find("by8") != std::string::npos ? 1 : 0;
+    return v.find("_b1") != std::string::npos ? 1 : 0;
+}
+}  // namespace stn
+
+static std::string tune_key(stencil_t p, int nsteps) {
+    std::ostringstream k;
+    k << gpu_tag(p->device) << "|k" << (int)p->kind << "|s" << (int)p->storage << "|r" << p->radius << "|bc"
+      << (int)p->bc << "|d" << p->ndim << ":" << p->geom.n[0] << "x" << p->geom.n[1] << "x" << p->geom.n[2] << "|n"
+      << nsteps;
+    return k.str();
 }
 
 extern "C" {
@@ -544,7 +639,7 @@ static stencil_status run_pass(stencil_t p, void *const *src, void *const *dst, 
                "diffusion (2D) launch");
         else
             CK(p, launch_diffusion(storage_code(p->storage), &m, dst[0], g, p->dcoef, p->bc != STENCIL_BC_CALLER,
-                                   p->err, s, p->variant),
+                                   p->err, s, p->variant, p->zmode),
                "diffusion launch");
         return STENCIL_OK;
     }
@@ -557,7 +652,7 @@ static stencil_status run_pass(stencil_t p, void *const *src, void *const *dst, 
     }
     Ptrs8 none{};
     CK(p, launch_mhd(storage_code(p->storage), 0, sub, maps, ptrs(dst, 8), ptrs(p->w, 8), ptrs(p->kc, 8), none,
-                     g, p->mconst, true, p->err, s, p->variant),
+                     g, p->mconst, true, p->err, s, p->variant, p->zmode),
        "mhd launch");
     return STENCIL_OK;
 }
@@ -691,7 +786,7 @@ stencil_status stencil_mhd_rhs(stencil_t p, void *const *fields, void *const *rh
     }
     Ptrs8 none{};
     CK(p, launch_mhd(storage_code(p->storage), 1, 0, maps, none, none, none, ptrs(rhs, 8), p->geom, p->mconst,
-                     false, p->err, s, p->variant),
+                     false, p->err, s, p->variant, p->zmode),
        "mhd rhs launch");
     return STENCIL_OK;
 }
@@ -785,35 +880,90 @@ stencil_status stencil_set_variant(stencil_t p, int variant) {
     return STENCIL_OK;
 }
 
+// Streaming 3D kernels have a z-chunk length to tune besides the tile shape.
+static int num_zmodes(stencil_t p) {
+    return ((p->kind == STENCIL_DIFFUSION && p->ndim == 3) || p->kind == STENCIL_MHD8) ? ZMODES : 1;
+}
+
 stencil_status stencil_autotune(stencil_t p, void *const *fin, void *const *fout, int nsteps, int reps,
                                 void *stream) {
     if (!p) return fail(nullptr, STENCIL_EINVAL, "plan is NULL");
     if (nsteps < 1 || reps < 1) return fail(p, STENCIL_EINVAL, "nsteps and reps must be >= 1");
+    const std::string key = tune_key(p, nsteps);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        tune_load_locked(tune_path());
+        auto it = g_tune.find(key);
+        if (it != g_tune.end())
+            for (int v = 0; v < num_variants(p); ++v)
+                if (it->second.variant == variant_name(p, v) && it->second.zmode < num_zmodes(p)) {
+                    p->variant = v;
+                    p->zmode = it->second.zmode;
+                    p->tuned_from_cache = 1;
+                    p->tuned_ms = it->second.ms;
+                    return STENCIL_OK;
+                }
+    }
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t e0, e1;
     CK(p, cudaEventCreate(&e0), "cudaEventCreate");
     CK(p, cudaEventCreate(&e1), "cudaEventCreate");
-    const int keep = p->variant;
-    int best = -1;
+    const int keep_v = p->variant, keep_z = p->zmode;
+    int best = -1, best_z = 0;
     float best_ms = 0.f;
-    for (int v = 0; v < num_variants(p); ++v) {
-        p->variant = v;
-        if (stencil_step(p, fin, fout, nsteps, stream) != STENCIL_OK) continue;  // failed launch: discard
-        if (cudaEventRecord(e0, s) != cudaSuccess) break;
-        bool ok = true;
-        for (int r = 0; r < reps && ok; ++r) ok = stencil_step(p, fin, fout, nsteps, stream) == STENCIL_OK;
-        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) break;
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ok && read_err(p, s) == STENCIL_OK && (best < 0 || ms < best_ms)) {
-            best = v;
-            best_ms = ms;
+    for (int v = 0; v < num_variants(p); ++v)
+        for (int z = 0; z < num_zmodes(p); ++z) {
+            p->variant = v;
+            p->zmode = z;
+            if (stencil_step(p, fin, fout, nsteps, stream) != STENCIL_OK) continue;  // failed launch: discard
+            if (cudaEventRecord(e0, s) != cudaSuccess) break;
+            bool ok = true;
+            for (int r = 0; r < reps && ok; ++r) ok = stencil_step(p, fin, fout, nsteps, stream) == STENCIL_OK;
+            if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ok && read_err(p, s) == STENCIL_OK && (best < 0 || ms < best_ms)) {
+                best = v;
+                best_z = z;
+                best_ms = ms;
+            }
         }
-    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    p->variant = best >= 0 ? best : keep;
-    if (best < 0) return fail(p, STENCIL_ECUDA, "no kernel variant launched successfully");
+    if (best < 0) {
+        p->variant = keep_v;
+        p->zmode = keep_z;
+        return fail(p, STENCIL_ECUDA, "no kernel variant launched successfully");
+    }
+    p->variant = best;
+    p->zmode = best_z;
+    p->tuned_from_cache = 0;
+    p->tuned_ms = best_ms / reps;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        const TuneRec rec{variant_name(p, best), best_z, p->tuned_ms};
+        tune_put_locked(key, rec);
+        const std::string path = tune_path();
+        if (!path.empty()) {
+            std::ofstream out(path, std::ios::app);
+            if (out) out << key << '\t' << rec.variant << '\t' << rec.zmode << '\t' << rec.ms << '\n';
+        }
+    }
+    return STENCIL_OK;
+}
+
+stencil_status stencil_set_zmode(stencil_t p, int zmode) {
+    if (!p) return fail(nullptr, STENCIL_EINVAL, "plan is NULL");
+    if (zmode < 0 || zmode >= num_zmodes(p)) return fail(p, STENCIL_EINVAL, "z-chunk mode out of range for this plan");
+    p->zmode = zmode;
+    return STENCIL_OK;
+}
+
+stencil_status stencil_autotune_status(stencil_t p, int *from_cache, int *zmode, float *ms) {
+    if (!p) return fail(nullptr, STENCIL_EINVAL, "plan is NULL");
+    if (from_cache) *from_cache = p->tuned_from_cache;
+    if (zmode) *zmode = p->zmode;
+    if (ms) *ms = p->tuned_ms;
     return STENCIL_OK;
 }
 

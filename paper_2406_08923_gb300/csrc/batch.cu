@@ -133,6 +133,7 @@ struct stencil_server {
     unsigned char *dev_tab = nullptr;
     unsigned *err = nullptr;
     int grid_heat = 0, grid_mhd = 0, grid_xc = 0;
+    int heat_shape = 0, mhd_shape = 0;  // tile shapes of the batched heat / MHD kernels
     bool own_stream = false;
     // one captured graph per pinned table buffer: table upload + every batched launch
     cudaGraph_t graph[2] = {};  // kept alive: exec node updates refer to its nodes
@@ -209,8 +210,8 @@ stencil_status admit(stencil_server_t s, Req *r) {
     // TMA descriptors of both field sets
     if (r->kind != STENCIL_XCORR) {
         int box[3], tx, ty;
-        if (r->kind == STENCIL_DIFFUSION) diffusion_batch_tile(&tx, &ty, box);
-        else mhd_batch_tile(&tx, &ty, box);
+        if (r->kind == STENCIL_DIFFUSION) diffusion_batch_tile(s->heat_shape, &tx, &ty, box);
+        else mhd_batch_tile(s->mhd_shape, &tx, &ty, box);
         for (int k = 0; k < 2; ++k)
             for (int q = 0; q < r->nf; ++q)
                 if (!encode_f32(&r->hmaps[k * r->nf + q], r->set[k][q], r->g, box))
@@ -268,11 +269,12 @@ stencil_status capture_graphs(stencil_server_t s) {
         SCK(s, cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
         cudaError_t e = cudaMemcpyAsync(s->dev_tab, s->host_tab[i], s->table_bytes, cudaMemcpyHostToDevice, s->stream);
         if (e == cudaSuccess)
-            e = launch_diffusion_batch(dhdr, reinterpret_cast<const BatchHeat *>(s->dev_tab + t.off_heat), s->err,
-                                       s->grid_heat, s->stream);
+            e = launch_diffusion_batch(s->heat_shape, dhdr, reinterpret_cast<const BatchHeat *>(s->dev_tab + t.off_heat),
+                                       s->err, s->grid_heat, s->stream);
         for (int sub = 0; sub < 3 && e == cudaSuccess; ++sub)
-            e = launch_mhd_batch(dhdr, reinterpret_cast<const BatchMhd *>(s->dev_tab + t.off_mhd + sub * t.mhd_stride),
-                                 sub, s->err, s->grid_mhd, s->stream);
+            e = launch_mhd_batch(s->mhd_shape, dhdr,
+                                 reinterpret_cast<const BatchMhd *>(s->dev_tab + t.off_mhd + sub * t.mhd_stride), sub,
+                                 s->err, s->grid_mhd, s->stream);
         if (e == cudaSuccess)
             e = launch_xcorr_batch(dhdr, reinterpret_cast<const BatchXcorr *>(s->dev_tab + t.off_xc), s->err,
                                    s->grid_xc, s->stream);
@@ -337,8 +339,12 @@ stencil_status stencil_server_create(int64_t hbm_budget_bytes, int max_active, v
         stencil_server_destroy(s);
         return st;
     }
-    s->grid_heat = diffusion_batch_grid();
-    s->grid_mhd = mhd_batch_grid();
+    // tile shapes: the autotuner's latest choice for FP32 plans of the kind on this GPU (the
+    // batched kernels run the same tile code as the per-grid ones), else the default shape
+    s->heat_shape = std::max(0, tuned_batch_shape(STENCIL_DIFFUSION));
+    s->mhd_shape = std::max(0, tuned_batch_shape(STENCIL_MHD8));
+    s->grid_heat = diffusion_batch_grid(s->heat_shape);
+    s->grid_mhd = mhd_batch_grid(s->mhd_shape);
     s->grid_xc = xcorr_batch_grid();
     stencil_status gst = capture_graphs(s);
     if (gst != STENCIL_OK) {
@@ -427,7 +433,7 @@ stencil_status stencil_server_submit(stencil_server_t s, const stencil_request *
                 for (int i = 0; i < 3; ++i) r->ga[a][i] = (float)(sc * W2[i] / (p.dx[a] * p.dx[a]));
             }
             r->g0 = (float)g0;
-            diffusion_batch_tile(&tx, &ty, box);
+            diffusion_batch_tile(s->heat_shape, &tx, &ty, box);
         } else {
             if (!(p.cp > 0.0) || !(p.gamma > 1.0) || !(p.mu0 > 0.0)) {
                 delete r;
@@ -447,7 +453,7 @@ stencil_status stencil_server_submit(stencil_server_t s, const stencil_request *
             c.nu = p.nu; c.eta = p.eta; c.zeta = p.zeta; c.mu0 = p.mu0; c.inv_mu0 = 1.0 / p.mu0;
             c.cp_gm1 = p.cp * (p.gamma - 1.0); c.K = p.K; c.dt = p.dt;
             mhd_scaled_constants(c, &r->k);
-            mhd_batch_tile(&tx, &ty, box);
+            mhd_batch_tile(s->mhd_shape, &tx, &ty, box);
         }
         const int nz = (int)r->g.n[2];
         r->zc = std::min(nz, 32);
@@ -593,6 +599,14 @@ stencil_status stencil_server_progress(stencil_server_t s, int *n_pending, int *
         *n_done = d;
     }
     return STENCIL_OK;
+}
+
+const char *stencil_server_variant(stencil_server_t s, stencil_kind kind) {
+    if (!s) return "?";
+    if (kind == STENCIL_DIFFUSION) return diffusion_batch_shape_name(s->heat_shape);
+    if (kind == STENCIL_MHD8) return mhd_batch_shape_name(s->mhd_shape);
+    if (kind == STENCIL_XCORR) return "batch_chunk2184_one_sweep";
+    return "?";
 }
 
 stencil_status stencil_server_poll(stencil_server_t s, int64_t ticket, int *state) {

@@ -389,6 +389,11 @@ int choose_zchunks(int tiles, int nz, int slots, double reread_weight) {
     return best;
 }
 
+int zchunk_len(int zc, int nz, int zmode) {
+    const int v = zmode == 1 ? (zc + 1) / 2 : zmode == 2 ? 2 * zc : zc;
+    return std::max(1, std::min(nz, v));
+}
+
 int device_sms() {
     static int sms[64] = {};
     int dev = 0;
@@ -400,7 +405,7 @@ int device_sms() {
 
 template <typename T, int VP, int BY, int RY, int ZB, int NSLOT, bool PK, int R>
 static cudaError_t run(const CUtensorMap *map, void *out, const Geom &g, const DiffCoef &dc, bool images,
-                       unsigned *err, cudaStream_t s) {
+                       unsigned *err, cudaStream_t s, int zmode) {
     using Cfg = DiffCfg<T, VP, BY, RY, ZB, NSLOT, R>;
     DC<T> c;
     c.g0 = (T)dc.g0;
@@ -426,7 +431,7 @@ static cudaError_t run(const CUtensorMap *map, void *out, const Geom &g, const D
     // chunks are short (4 planes): tens of waves of small CTAs keep the pipe evenly fed through
     // every CTA's start-up and the grid's tail (5 % faster than whole waves of long chunks at
     // 256^3).
-    const int zc = std::min(nz, 4);
+    const int zc = zchunk_len(std::min(nz, 4), nz, zmode);
     dim3 grid(tx, ty, (unsigned)((nz + zc - 1) / zc));
     return launch_pdl(k, grid, dim3(32 * BY), Cfg::SMEM, s, *map, static_cast<T *>(out), g, c, zc, images ? 1 : 0,
                       err);
@@ -474,12 +479,12 @@ void diffusion_box(int dtype, int r, int v, int box[3]) {
 
 template <int R>
 static cudaError_t dispatch_f64(int variant, const CUtensorMap *map, void *out, const Geom &g, const DiffCoef &c,
-                                bool images, unsigned *err, cudaStream_t s) {
+                                bool images, unsigned *err, cudaStream_t s, int zmode) {
     using T = double;
     int i = 0;
     cudaError_t res = cudaErrorInvalidValue;
 #define X(VP, BY, RY, ZB, NS, PK) \
-    if (i++ == variant) res = run<T, VP, BY, RY, ZB, NS, PK, R>(map, out, g, c, images, err, s);
+    if (i++ == variant) res = run<T, VP, BY, RY, ZB, NS, PK, R>(map, out, g, c, images, err, s, zmode);
     if constexpr (R == 3) {
         DIFF_VARIANTS_F64(X)
     } else {
@@ -490,14 +495,14 @@ static cudaError_t dispatch_f64(int variant, const CUtensorMap *map, void *out, 
 }
 
 cudaError_t launch_diffusion(int dtype, const CUtensorMap *map, void *out, const Geom &g, const DiffCoef &c,
-                             bool images, unsigned *err, cudaStream_t s, int variant) {
-    if (dtype == 2) return launch_diffusion_f32(map, static_cast<float *>(out), g, c, images, err, s, variant);
+                             bool images, unsigned *err, cudaStream_t s, int variant, int zmode) {
+    if (dtype == 2) return launch_diffusion_f32(map, static_cast<float *>(out), g, c, images, err, s, variant, zmode);
     if (dtype != 1) return cudaErrorInvalidValue;
     switch (c.r) {
-    case 1: return dispatch_f64<1>(variant, map, out, g, c, images, err, s);
-    case 2: return dispatch_f64<2>(variant, map, out, g, c, images, err, s);
-    case 3: return dispatch_f64<3>(variant, map, out, g, c, images, err, s);
-    case 4: return dispatch_f64<4>(variant, map, out, g, c, images, err, s);
+    case 1: return dispatch_f64<1>(variant, map, out, g, c, images, err, s, zmode);
+    case 2: return dispatch_f64<2>(variant, map, out, g, c, images, err, s, zmode);
+    case 3: return dispatch_f64<3>(variant, map, out, g, c, images, err, s, zmode);
+    case 4: return dispatch_f64<4>(variant, map, out, g, c, images, err, s, zmode);
     default: return cudaErrorInvalidValue;
     }
 }

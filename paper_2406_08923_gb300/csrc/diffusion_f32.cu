@@ -312,7 +312,7 @@ Coef32 coef32(const DiffCoef &dc) {
 
 template <int BY, int RY, int ZB, int NSLOT, int R, int MINB, bool XVEC>
 cudaError_t run(const CUtensorMap *map, float *out, const Geom &g, const Coef32 &c, bool images, unsigned *err,
-                cudaStream_t s) {
+                cudaStream_t s, int zmode) {
     using Cfg = H32<BY, RY, ZB, NSLOT, R>;
     auto k = heat32_kernel<BY, RY, ZB, NSLOT, R, MINB, XVEC>;
     static int occ[64] = {};  // resident CTAs per SM, per device
@@ -331,7 +331,7 @@ cudaError_t run(const CUtensorMap *map, float *out, const Geom &g, const Coef32 
     const int tx = (int)((g.n[0] + Cfg::TX - 1) / Cfg::TX), ty = (int)((g.n[1] + Cfg::TY - 1) / Cfg::TY);
     const int nz = (int)g.n[2];
     const int chunks = choose_zchunks(tx * ty, nz, occ[dev] * device_sms(), 0.5);
-    const int zc = (nz + chunks - 1) / chunks;
+    const int zc = zchunk_len((nz + chunks - 1) / chunks, nz, zmode);
     dim3 grid(tx, ty, (unsigned)((nz + zc - 1) / zc));
     return launch_pdl(k, grid, dim3(32 * BY), Cfg::SMEM, s, *map, out, g, c, zc, images ? 1 : 0, err);
 }
@@ -354,14 +354,14 @@ const char *const NAMES_OTHER[] = {"?", "f32_r1_by4_ry2_zb2_s8_m3", "f32_r2_by4_
 
 template <int R>
 cudaError_t dispatch(int variant, const CUtensorMap *map, float *out, const Geom &g, const Coef32 &c, bool images,
-                     unsigned *err, cudaStream_t s) {
+                     unsigned *err, cudaStream_t s, int zmode) {
     const bool xv = xvec_ok(g);
     int i = 0;
     cudaError_t res = cudaErrorInvalidValue;
 #define X(BY, RY, ZB, NS, MB)                                                          \
     if (i++ == variant)                                                                \
-        res = xv ? run<BY, RY, ZB, NS, R, MB, true>(map, out, g, c, images, err, s) \
-                 : run<BY, RY, ZB, NS, R, MB, false>(map, out, g, c, images, err, s);
+        res = xv ? run<BY, RY, ZB, NS, R, MB, true>(map, out, g, c, images, err, s, zmode) \
+                 : run<BY, RY, ZB, NS, R, MB, false>(map, out, g, c, images, err, s, zmode);
     if constexpr (R == 3) {
         HEAT32_VARIANTS_R3(X)
     } else {
@@ -396,27 +396,34 @@ void diffusion_f32_box(int r, int v, int box[3]) {
 }
 
 cudaError_t launch_diffusion_f32(const CUtensorMap *map, float *out, const Geom &g, const DiffCoef &dc, bool images,
-                                 unsigned *err, cudaStream_t s, int variant) {
+                                 unsigned *err, cudaStream_t s, int variant, int zmode) {
     const Coef32 c = coef32(dc);
     switch (dc.r) {
-    case 1: return dispatch<1>(variant, map, out, g, c, images, err, s);
-    case 2: return dispatch<2>(variant, map, out, g, c, images, err, s);
-    case 3: return dispatch<3>(variant, map, out, g, c, images, err, s);
-    case 4: return dispatch<4>(variant, map, out, g, c, images, err, s);
+    case 1: return dispatch<1>(variant, map, out, g, c, images, err, s, zmode);
+    case 2: return dispatch<2>(variant, map, out, g, c, images, err, s, zmode);
+    case 3: return dispatch<3>(variant, map, out, g, c, images, err, s, zmode);
+    case 4: return dispatch<4>(variant, map, out, g, c, images, err, s, zmode);
     default: return cudaErrorInvalidValue;
     }
 }
 
 // ------------------------------------------------------------------ batched (serving)
 
-// The tile shape of variant f32_by4_ry2_zb2_s8_m3.
+// Tile shapes of the batched kernel (the server picks one per run from the autotuner's choice
+// for FP32 heat plans): 0 = 128 x 8 cells (4 warps x 2 rows, the tile of the per-grid variants
+// f32_by4_ry2_*), 1 = 128 x 16 (8 warps x 2 rows, f32_by8_ry2_*).
 namespace {
-constexpr int DB_BY = 4, DB_RY = 2, DB_ZB = 2, DB_NSLOT = 8, DB_MINB = 2;
-using DbCfg = H32<DB_BY, DB_RY, DB_ZB, DB_NSLOT, R6>;
+template <int SH> struct DbShape;
+template <> struct DbShape<0> { static constexpr int BY = 4, RY = 2, MINB = 2; };
+template <> struct DbShape<1> { static constexpr int BY = 8, RY = 2, MINB = 2; };
+constexpr int DB_ZB = 2, DB_NSLOT = 8;
+template <int SH> using DbCfg = H32<DbShape<SH>::BY, DbShape<SH>::RY, DB_ZB, DB_NSLOT, R6>;
 }  // namespace
 
-__global__ void __launch_bounds__(32 * DB_BY, DB_MINB)
+template <int SH>
+__global__ void __launch_bounds__(32 * DbShape<SH>::BY, DbShape<SH>::MINB)
 diffusion_batch_kernel(const BatchHeader *hdr, const BatchHeat *items, unsigned *err) {
+    constexpr int BY = DbShape<SH>::BY, RY = DbShape<SH>::RY;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *ring = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     __shared__ __align__(8) uint64_t full[DB_NSLOT];
@@ -440,39 +447,50 @@ diffusion_batch_kernel(const BatchHeader *hdr, const BatchHeat *items, unsigned 
         }
         const Geom g = it.g;
         const bool ok = xvec_ok(g)
-                            ? heat32_tile<DB_BY, DB_RY, DB_ZB, DB_NSLOT, R6, true, false>(it.map, it.out, g, c, tx, ty, tz, it.zc,
-                                                                               1, err, ring, full)
-                            : heat32_tile<DB_BY, DB_RY, DB_ZB, DB_NSLOT, R6, false, false>(it.map, it.out, g, c, tx, ty, tz,
-                                                                                it.zc, 1, err, ring, full);
+                            ? heat32_tile<BY, RY, DB_ZB, DB_NSLOT, R6, true, false>(it.map, it.out, g, c, tx, ty, tz, it.zc,
+                                                                                 1, err, ring, full)
+                            : heat32_tile<BY, RY, DB_ZB, DB_NSLOT, R6, false, false>(it.map, it.out, g, c, tx, ty, tz,
+                                                                                  it.zc, 1, err, ring, full);
         __syncthreads();
         if (!ok) return;
     }
 }
 
-int diffusion_batch_grid() {
+template <int SH> static int batch_grid_t() {
     static int grid[64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return 152;
     if (!grid[dev]) {
-        cudaFuncSetAttribute(diffusion_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DbCfg::SMEM);
+        cudaFuncSetAttribute(diffusion_batch_kernel<SH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)DbCfg<SH>::SMEM);
         int o = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, diffusion_batch_kernel, 32 * DB_BY, DbCfg::SMEM);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, diffusion_batch_kernel<SH>, 32 * DbShape<SH>::BY,
+                                                      DbCfg<SH>::SMEM);
         grid[dev] = std::max(o, 1) * device_sms();
     }
     return grid[dev];
 }
 
-void diffusion_batch_tile(int *tx, int *ty, int box[3]) {
-    *tx = DbCfg::TX;
-    *ty = DbCfg::TY;
-    box[0] = DbCfg::TXP;
-    box[1] = DbCfg::ROWS;
+int diffusion_batch_grid(int shape) { return shape == 1 ? batch_grid_t<1>() : batch_grid_t<0>(); }
+
+const char *diffusion_batch_shape_name(int shape) {
+    return shape == 1 ? "batch_by8_ry2_zb2_s8" : "batch_by4_ry2_zb2_s8";
+}
+
+void diffusion_batch_tile(int shape, int *tx, int *ty, int box[3]) {
+    *tx = shape == 1 ? DbCfg<1>::TX : DbCfg<0>::TX;
+    *ty = shape == 1 ? DbCfg<1>::TY : DbCfg<0>::TY;
+    box[0] = shape == 1 ? DbCfg<1>::TXP : DbCfg<0>::TXP;
+    box[1] = shape == 1 ? DbCfg<1>::ROWS : DbCfg<0>::ROWS;
     box[2] = 1;
 }
 
-cudaError_t launch_diffusion_batch(const BatchHeader *hdr, const BatchHeat *items, unsigned *err, int grid,
+cudaError_t launch_diffusion_batch(int shape, const BatchHeader *hdr, const BatchHeat *items, unsigned *err, int grid,
                                    cudaStream_t s) {
-    diffusion_batch_kernel<<<grid, 32 * DB_BY, DbCfg::SMEM, s>>>(hdr, items, err);
+    if (shape == 1)
+        diffusion_batch_kernel<1><<<grid, 32 * DbShape<1>::BY, DbCfg<1>::SMEM, s>>>(hdr, items, err);
+    else
+        diffusion_batch_kernel<0><<<grid, 32 * DbShape<0>::BY, DbCfg<0>::SMEM, s>>>(hdr, items, err);
     return cudaGetLastError();
 }
 

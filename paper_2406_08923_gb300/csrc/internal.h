@@ -52,6 +52,11 @@ cudaError_t launch_maxfilter(int dtype, int r, const void *in, void *out, const 
 // Grid sizing shared by the z-streaming kernels: number of z-chunks that best fills whole
 // waves of `slots` resident CTAs (see diffusion.cu), and the SM count of the current device.
 int choose_zchunks(int tiles, int nz, int slots, double reread_weight);
+// z-chunk length of a launch: the kernel's own choice `zc` (zmode 0), half of it (zmode 1, more
+// and shorter chunks) or twice it (zmode 2, fewer and longer), within 1..nz.  The autotuner
+// searches the mode next to the tile shape.
+int zchunk_len(int zc, int nz, int zmode);
+constexpr int ZMODES = 3;
 int device_sms();
 
 // DIFFUSION (Eqs. 4-7): one folded forward-Euler step with the order-2r central Laplacian of
@@ -65,7 +70,7 @@ struct DiffCoef {
 // 3D
 cudaError_t launch_diffusion(int dtype, const CUtensorMap *map_in, void *out, const Geom &g,
                              const DiffCoef &c, bool images, unsigned *err, cudaStream_t s,
-                             int variant);
+                             int variant, int zmode = 0);
 int diffusion_num_variants(int dtype, int r);
 const char *diffusion_variant_name(int dtype, int r, int variant);
 void diffusion_box(int dtype, int r, int variant, int box[3]);  // TMA box (x, y, z) of a variant
@@ -74,7 +79,7 @@ int diffusion_f32_num_variants(int r);
 const char *diffusion_f32_variant_name(int r, int variant);
 void diffusion_f32_box(int r, int variant, int box[3]);
 cudaError_t launch_diffusion_f32(const CUtensorMap *map_in, float *out, const Geom &g, const DiffCoef &c,
-                                 bool images, unsigned *err, cudaStream_t s, int variant);
+                                 bool images, unsigned *err, cudaStream_t s, int variant, int zmode = 0);
 // 2D (diffusion2d.cu): one TMA tile per CTA, no streaming axis.
 cudaError_t launch_diffusion2d(int dtype, const CUtensorMap *map_in, void *out, const Geom &g, const DiffCoef &c,
                                bool images, unsigned *err, cudaStream_t s);
@@ -101,7 +106,7 @@ struct MhdMaps {
 cudaError_t launch_mhd(int storage, int mode, int sub, const MhdMaps &maps, const Ptrs8 &fout,
                        const Ptrs8 &w, const Ptrs8 &kc, const Ptrs8 &rhs, const Geom &g,
                        const MhdConst &k, bool images, unsigned *err, cudaStream_t s,
-                       int variant);
+                       int variant, int zmode = 0);
 void mhd_box(int storage, int variant, int box[3]);
 int mhd_num_variants(int storage);
 const char *mhd_variant_name(int storage, int variant);
@@ -166,18 +171,25 @@ struct BatchHeader {
     int n_heat, heat_ctas, n_mhd, mhd_ctas, n_xc, xc_ctas, pad_[2];
 };
 
-cudaError_t launch_diffusion_batch(const BatchHeader *hdr, const BatchHeat *items, unsigned *err, int grid,
+// `shape`: the batched kernel's tile shape, 0 or 1 (see diffusion_f32.cu / mhd.cu)
+cudaError_t launch_diffusion_batch(int shape, const BatchHeader *hdr, const BatchHeat *items, unsigned *err, int grid,
                                    cudaStream_t s);
-cudaError_t launch_mhd_batch(const BatchHeader *hdr, const BatchMhd *items, int sub, unsigned *err, int grid,
-                             cudaStream_t s);
+cudaError_t launch_mhd_batch(int shape, const BatchHeader *hdr, const BatchMhd *items, int sub, unsigned *err,
+                             int grid, cudaStream_t s);
 cudaError_t launch_xcorr_batch(const BatchHeader *hdr, const BatchXcorr *items, unsigned *err, int grid,
                                cudaStream_t s);
 // persistent grid sizes (resident CTAs on the current device) and tile shapes of the batched kernels
-int diffusion_batch_grid();
-int mhd_batch_grid();
+int diffusion_batch_grid(int shape);
+int mhd_batch_grid(int shape);
 int xcorr_batch_grid();
-void diffusion_batch_tile(int *tx, int *ty, int box[3]);
-void mhd_batch_tile(int *tx, int *ty, int box[3]);
+void diffusion_batch_tile(int shape, int *tx, int *ty, int box[3]);
+void mhd_batch_tile(int shape, int *tx, int *ty, int box[3]);
+const char *diffusion_batch_shape_name(int shape);
+const char *mhd_batch_shape_name(int shape);
+// The batched tile shape (0 or 1) matching the tile of the per-grid variant the autotuner
+// last chose for FP32 plans of `kind` (STENCIL_DIFFUSION or STENCIL_MHD8) on the current
+// device, in this process or in the autotuning cache file; -1 if nothing was tuned (api.cu).
+int tuned_batch_shape(int kind);
 int xcorr_batch_chunk();
 void mhd_scaled_constants(const MhdConst &c, MK<float> *k);
 // FP32 constants of RK substep `sub` (its alpha and beta filled in)

@@ -229,7 +229,7 @@ static const double RK_B[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
 template <typename S, typename C, bool KAHAN, int MODE, int TX, int TY, int NSLOT, int MINB, bool CONDUCT>
 static cudaError_t run(int sub, const MhdMaps &maps, const Ptrs8 &fo, const Ptrs8 &w, const Ptrs8 &kc,
                        const Ptrs8 &rhs, const Geom &g, const MhdConst &c, bool images, unsigned *err,
-                       cudaStream_t s) {
+                       cudaStream_t s, int zmode) {
     using Cfg = MhdCfg<S, TX, TY, NSLOT>;
     auto kern = mhd_kernel<S, C, KAHAN, MODE, TX, TY, NSLOT, MINB, CONDUCT>;
     static int occ[64] = {};  // resident CTAs per SM, per device
@@ -249,7 +249,7 @@ static cudaError_t run(int sub, const MhdMaps &maps, const Ptrs8 &fo, const Ptrs
     const int tx = (int)((g.n[0] + TX - 1) / TX), ty = (int)((g.n[1] + TY - 1) / TY);
     const int nz = (int)g.n[2];
     const int chunks = choose_zchunks(tx * ty, nz, occ[dev] * device_sms(), 0.5);
-    const int zc = (nz + chunks - 1) / chunks;
+    const int zc = zchunk_len((nz + chunks - 1) / chunks, nz, zmode);
     dim3 grid(tx, ty, (unsigned)((nz + zc - 1) / zc));
     kern<<<grid, TX * TY, Cfg::SMEM, s>>>(maps, fo, w, kc, rhs, g, k, zc, sub == 0 ? 1 : 0, sub == 2 ? 1 : 0,
                                           images ? 1 : 0, err);
@@ -291,7 +291,7 @@ void mhd_box(int storage, int v, int box[3]) {
 
 cudaError_t launch_mhd(int storage, int mode, int sub, const MhdMaps &maps, const Ptrs8 &fo, const Ptrs8 &w,
                        const Ptrs8 &kc, const Ptrs8 &rhs, const Geom &g, const MhdConst &c, bool images,
-                       unsigned *err, cudaStream_t s, int variant) {
+                       unsigned *err, cudaStream_t s, int variant, int zmode) {
     int i = 0;
     cudaError_t res = cudaErrorInvalidValue;
     // the conduction term of A3 is compiled in only for launches with K != 0
@@ -299,11 +299,11 @@ cudaError_t launch_mhd(int storage, int mode, int sub, const MhdMaps &maps, cons
 #define X(TX, TY, NS, MB)                                                                                  \
     if (i++ == variant) {                                                                                  \
         if (mode == 0)                                                                                     \
-            res = cond ? run<S, C, KH, 0, TX, TY, NS, MB, true>(sub, maps, fo, w, kc, rhs, g, c, images, err, s) \
-                       : run<S, C, KH, 0, TX, TY, NS, MB, false>(sub, maps, fo, w, kc, rhs, g, c, images, err, s); \
+            res = cond ? run<S, C, KH, 0, TX, TY, NS, MB, true>(sub, maps, fo, w, kc, rhs, g, c, images, err, s, zmode) \
+                       : run<S, C, KH, 0, TX, TY, NS, MB, false>(sub, maps, fo, w, kc, rhs, g, c, images, err, s, zmode); \
         else                                                                                               \
-            res = cond ? run<S, C, KH, 1, TX, TY, NS, MB, true>(sub, maps, fo, w, kc, rhs, g, c, images, err, s) \
-                       : run<S, C, KH, 1, TX, TY, NS, MB, false>(sub, maps, fo, w, kc, rhs, g, c, images, err, s); \
+            res = cond ? run<S, C, KH, 1, TX, TY, NS, MB, true>(sub, maps, fo, w, kc, rhs, g, c, images, err, s, zmode) \
+                       : run<S, C, KH, 1, TX, TY, NS, MB, false>(sub, maps, fo, w, kc, rhs, g, c, images, err, s, zmode); \
     }
     if (storage == 1) {
         using S = double; using C = double; constexpr bool KH = false;
@@ -321,13 +321,20 @@ cudaError_t launch_mhd(int storage, int mode, int sub, const MhdMaps &maps, cons
 
 // ------------------------------------------------------------------ batched (serving)
 
-// FP32 storage, Kahan-compensated RK, the tile shape of variant tx32_ty4_s8_b2.
-constexpr int MB_TX = 32, MB_TY = 4, MB_NSLOT = 8;
-using MbCfg = MhdCfg<float, MB_TX, MB_TY, MB_NSLOT>;
+// FP32 storage, Kahan-compensated RK.  Tile shapes (the server picks one per run from the
+// autotuner's choice for FP32 MHD plans): 0 = 32 x 4 cells, two CTAs per SM (the tile of
+// variant tx32_ty4_s8_b2), 1 = 32 x 12, one CTA per SM (tx32_ty12_s8_b1).
+template <int SH> struct MbShape;
+template <> struct MbShape<0> { static constexpr int TX = 32, TY = 4, MINB = 2; };
+template <> struct MbShape<1> { static constexpr int TX = 32, TY = 12, MINB = 1; };
+constexpr int MB_NSLOT = 8;
+template <int SH> using MbCfg = MhdCfg<float, MbShape<SH>::TX, MbShape<SH>::TY, MB_NSLOT>;
 
-__global__ void __launch_bounds__(MB_TX *MB_TY, 2)
+template <int SH>
+__global__ void __launch_bounds__(MbShape<SH>::TX *MbShape<SH>::TY, MbShape<SH>::MINB)
 mhd_batch_kernel(const BatchHeader *hdr, const BatchMhd *items, float alpha, float beta, int first, int last,
                  unsigned *err) {
+    constexpr int TX = MbShape<SH>::TX, TY = MbShape<SH>::TY;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *ring = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     __shared__ __align__(8) uint64_t full[MB_NSLOT];
@@ -357,35 +364,39 @@ mhd_batch_kernel(const BatchHeader *hdr, const BatchMhd *items, float alpha, flo
         Ptrs8 none{};
         const bool ok =
             it.k.K != 0.f
-                ? mhd_tile<float, float, true, 0, MB_TX, MB_TY, MB_NSLOT, true>(it.maps, it.fout, it.w, it.kc, none, g, ks,
-                                                                              tx, ty, tz, it.zc, first, last, 1, err,
-                                                                              ring, full)
-                : mhd_tile<float, float, true, 0, MB_TX, MB_TY, MB_NSLOT, false>(it.maps, it.fout, it.w, it.kc, none, g,
-                                                                               ks, tx, ty, tz, it.zc, first, last, 1,
-                                                                               err, ring, full);
+                ? mhd_tile<float, float, true, 0, TX, TY, MB_NSLOT, true>(it.maps, it.fout, it.w, it.kc, none, g, ks, tx,
+                                                                          ty, tz, it.zc, first, last, 1, err, ring, full)
+                : mhd_tile<float, float, true, 0, TX, TY, MB_NSLOT, false>(it.maps, it.fout, it.w, it.kc, none, g, ks,
+                                                                           tx, ty, tz, it.zc, first, last, 1, err, ring,
+                                                                           full);
         __syncthreads();
         if (!ok) return;
     }
 }
 
-int mhd_batch_grid() {
+template <int SH> static int mhd_batch_grid_t() {
     static int grid[64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return 152;
     if (!grid[dev]) {
-        cudaFuncSetAttribute(mhd_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MbCfg::SMEM);
+        cudaFuncSetAttribute(mhd_batch_kernel<SH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MbCfg<SH>::SMEM);
         int o = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, mhd_batch_kernel, MB_TX * MB_TY, MbCfg::SMEM);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, mhd_batch_kernel<SH>, MbShape<SH>::TX * MbShape<SH>::TY,
+                                                      MbCfg<SH>::SMEM);
         grid[dev] = std::max(o, 1) * device_sms();
     }
     return grid[dev];
 }
 
-void mhd_batch_tile(int *tx, int *ty, int box[3]) {
-    *tx = MB_TX;
-    *ty = MB_TY;
-    box[0] = MB_TX + 2 * MbCfg::HX;
-    box[1] = MB_TY + 2 * R6;
+int mhd_batch_grid(int shape) { return shape == 1 ? mhd_batch_grid_t<1>() : mhd_batch_grid_t<0>(); }
+
+const char *mhd_batch_shape_name(int shape) { return shape == 1 ? "batch_tx32_ty12_s8" : "batch_tx32_ty4_s8"; }
+
+void mhd_batch_tile(int shape, int *tx, int *ty, int box[3]) {
+    *tx = shape == 1 ? MbShape<1>::TX : MbShape<0>::TX;
+    *ty = shape == 1 ? MbShape<1>::TY : MbShape<0>::TY;
+    box[0] = *tx + 2 * MbCfg<0>::HX;
+    box[1] = *ty + 2 * R6;
     box[2] = 1;
 }
 
@@ -393,10 +404,16 @@ void mhd_scaled_constants(const MhdConst &c, MK<float> *k) { *k = make_k<float>(
 
 void mhd_substep_constants(const MhdConst &c, int sub, MK<float> *k) { *k = make_k<float>(c, RK_A[sub], RK_B[sub]); }
 
-cudaError_t launch_mhd_batch(const BatchHeader *hdr, const BatchMhd *items, int sub, unsigned *err, int grid,
-                             cudaStream_t s) {
-    mhd_batch_kernel<<<grid, MB_TX * MB_TY, MbCfg::SMEM, s>>>(hdr, items, (float)RK_A[sub], (float)RK_B[sub],
-                                                              sub == 0 ? 1 : 0, sub == 2 ? 1 : 0, err);
+cudaError_t launch_mhd_batch(int shape, const BatchHeader *hdr, const BatchMhd *items, int sub, unsigned *err,
+                             int grid, cudaStream_t s) {
+    const float a = (float)RK_A[sub], b = (float)RK_B[sub];
+    const int first = sub == 0 ? 1 : 0, last = sub == 2 ? 1 : 0;
+    if (shape == 1)
+        mhd_batch_kernel<1><<<grid, MbShape<1>::TX * MbShape<1>::TY, MbCfg<1>::SMEM, s>>>(hdr, items, a, b, first, last,
+                                                                                           err);
+    else
+        mhd_batch_kernel<0><<<grid, MbShape<0>::TX * MbShape<0>::TY, MbCfg<0>::SMEM, s>>>(hdr, items, a, b, first, last,
+                                                                                           err);
     return cudaGetLastError();
 }
 
