@@ -50,22 +50,25 @@ def _peaks():
 # DRAM traffic per launch of the dominant kernel from one ncu capture (profiles/), valid only
 # while the kernel source is unchanged (first 16 hex digits of sha256 of each file).
 NCU_TRAFFIC = {
-    # dram__bytes_read.sum + dram__bytes_write.sum per launch (mean of 3 launches, 1-pass capture)
-    "heat_f64": {"variant": "vx2_by4_ry1_zb2_s8", "bytes": 145016576 + 107296427,
-                 "src": {"diffusion.cu": "ab9ca43e704d3e8a", "common.cuh": "3f7458d1c75ca5f9"}},
-    # 256^3, mean of 3 launches (1-pass capture)
-    "heat_f32": {"variant": "f32_by4_ry2_zb2_s8_m3", "bytes": 81985963 + 25849515,
-                 "src": {"diffusion_f32.cu": "790dce206050e090", "common.cuh": "3f7458d1c75ca5f9"}},
-    # 512^3, mean of 3 launches (1-pass capture)
-    "heat_f32_512": {"variant": "f32_by8_ry2_zb2_s8_m2", "bytes": 586108416 + 523425109,
-                     "src": {"diffusion_f32.cu": "790dce206050e090", "common.cuh": "3f7458d1c75ca5f9"}},
+    # dram__bytes_read.sum + dram__bytes_write.sum per launch, mean of 3 launches of a 1-pass capture at
+    # the bench sizes (profiles/dram_traffic_full_size.md); MHD: the mean over the 3 RK substeps
+    "heat_f64": {"variant": "vx2_by4_ry1_zb2_s8", "zmode": 0, "bytes": 145052587 + 107249835,
+                "src": {"diffusion.cu": "35a97c5945caac31", "common.cuh": "3f7458d1c75ca5f9"}},
+    "heat_f32": {"variant": "f32_by4_ry2_zb2_s8_m3", "zmode": 0, "bytes": 82138965 + 25750272,
+                "src": {"diffusion_f32.cu": "1fba3bb13079ab17", "common.cuh": "3f7458d1c75ca5f9"}},
+    "heat_f32_512": {"variant": "f32_by8_ry2_zb2_s8_m2", "zmode": 0, "bytes": 586134528 + 523691008,
+                "src": {"diffusion_f32.cu": "1fba3bb13079ab17", "common.cuh": "3f7458d1c75ca5f9"}},
+    "mhd_f32": {"variant": "tx32_ty12_s8_b1", "zmode": 0, "bytes": 5662824619 + 4940957696,
+                "src": {"mhd.cu": "30a002e933a67717", "mhd_rhs.cuh": "be5b445fecd5703b", "common.cuh": "3f7458d1c75ca5f9"}},
+    "mhd_bf16": {"variant": "tx32_ty8_s8_b2", "zmode": 0, "bytes": 3912996437 + 2612448085,
+                "src": {"mhd.cu": "30a002e933a67717", "mhd_rhs.cuh": "be5b445fecd5703b", "common.cuh": "3f7458d1c75ca5f9"}},
 }
 
 
-def _traffic(case, variant_name):
+def _traffic(case, variant_name, zmode=0):
     import hashlib
     rec = NCU_TRAFFIC.get(case)
-    if not rec or rec["variant"] != variant_name:
+    if not rec or rec["variant"] != variant_name or rec.get("zmode", 0) != zmode:
         return None
     for f, h in rec["src"].items():
         path = os.path.join(ROOT, "paper_2406_08923_gb300", "csrc", f)
@@ -732,7 +735,8 @@ def run_extras(L, synth, stream, hbm_peak, args):
         "mcell_updates_per_s": round(cells * HEAT_STEPS / (res["ms_job"] / 1e3) / 1e6, 1),
         "variant": res["variant"],
         "zchunk_mode": res["plan"].autotune_status()[1],
-        "roofline": _roof("hbm", gbs, hbm_peak, "GB/s", traffic=_traffic("heat_f32", res["variant"]),
+        "roofline": _roof("hbm", gbs, hbm_peak, "GB/s",
+                          traffic=_traffic("heat_f32", res["variant"], res["plan"].autotune_status()[1]),
                           note="8 B/cell-update algorithmic; traffic = ncu dram bytes/launch")}
     res["plan"].close()
     # config 2 FP32 at 512^3: the two 540 MB fields far exceed the 126 MB L2
@@ -744,7 +748,9 @@ def run_extras(L, synth, stream, hbm_peak, args):
         "ms_per_job": round(res["ms_job"], 4), "kernel_ms_avg": round(res["ms_kernel"], 5),
         "mcell_updates_per_s": round(cells5 * (HEAT_STEPS // 4) / (res["ms_job"] / 1e3) / 1e6, 1),
         "variant": res["variant"],
-        "roofline": _roof("hbm", gbs, hbm_peak, "GB/s", traffic=_traffic("heat_f32_512", res["variant"]),
+        "zchunk_mode": res["plan"].autotune_status()[1],
+        "roofline": _roof("hbm", gbs, hbm_peak, "GB/s",
+                          traffic=_traffic("heat_f32_512", res["variant"], res["plan"].autotune_status()[1]),
                           note="8 B/cell-update algorithmic; traffic = ncu dram bytes/launch")}
     res["plan"].close()
     # config 3: fused 8-field MHD, 256^3 FP64, 20 RK3 steps
@@ -791,11 +797,16 @@ def run_extras(L, synth, stream, hbm_peak, args):
         # per cell-substep: f_in, f_out, w r/w, c r/w over 8 fields (avg over the 3 substeps)
         avg_vals = 8 * (1 + 1 + (1 + 2 + 1) / 3.0 + 2)
         gbs = cells * avg_vals * bpc / (res["ms_substep"] / 1e3) / 1e9
+        zm = res["plan"].autotune_status()[1]
         out[name] = {"ms_per_job": round(res["ms_job"], 3), "ms_per_substep": round(res["ms_substep"], 4),
                      "mcell_substep_updates_per_s": round(cells / (res["ms_substep"] / 1e3) / 1e6, 1),
-                     "variant": res["variant"], "finite": res["finite"], "mass": res["mass"],
+                     "variant": res["variant"], "zchunk_mode": zm, "finite": res["finite"], "mass": res["mass"],
                      "roofline": _roof("hbm", gbs, hbm_peak, "GB/s",
-                                       note=f"{avg_vals:.1f} values x {bpc} B per cell-substep")}
+                                       traffic=_traffic("mhd_f32" if st == L.STENCIL_F32 else "mhd_bf16",
+                                                        res["variant"], zm),
+                                       note=f"{avg_vals:.1f} values x {bpc} B per cell-substep (mean of the 3 "
+                                            "RK substeps); traffic = ncu dram bytes per launch, mean of the 3 "
+                                            "substeps")}
         res["plan"].close()
     # config 4 accuracy: FP32 / BF16 storage against the FP64 path, every step of 20
     out["mhd8_384_accuracy_20steps"] = run_accuracy_leg(L, synth, stream)

@@ -47,6 +47,7 @@ def test_traffic_record_is_tied_to_variant_and_sources():
     for case, rec in b.NCU_TRAFFIC.items():
         assert b._traffic(case, rec["variant"]) == rec["bytes"], case  # sources unchanged since capture
         assert b._traffic(case, rec["variant"] + "_other") is None
+        assert b._traffic(case, rec["variant"], rec["zmode"] + 1) is None  # another z-chunk length
     assert b._traffic("no_such_case", "x") is None
 
 
