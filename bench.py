@@ -11,10 +11,11 @@ exceed the 126 MB L2, so no flush is needed between iterations.
 The JSON line also carries, per the other stencil workloads (1D cross-correlation, FP32 heat,
 fused 8-field MHD in FP64 and in FP32/BF16 storage), their own throughput and roofline.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-extras]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-extras] [--zslab]
 
 Under torchrun (N > 1) every rank solves its own independent grid (weak scaling, no
-data-path collective); the time is the max over ranks.  --impl reference times the FP64 CPU
+data-path collective); the time is the max over ranks.  --zslab instead decomposes the one
+256^3 grid along z over the ranks (strong scaling, a 3-plane halo exchange per Euler step).  --impl reference times the FP64 CPU
 oracle on the host cores on a bounded sample of the same workload.
 """
 from __future__ import annotations
@@ -710,6 +711,55 @@ def run_ours(args):
     return 0
 
 
+def run_zslab(args):
+    """The headline job on one grid decomposed along z over the N ranks (strong scaling): each
+    rank owns 256/N planes as a STENCIL_BC_PERIODIC_XY plan, and every Euler step first
+    exchanges the 3-plane z halos with the neighbouring ranks (NCCL point-to-point; with one
+    rank the slab wraps onto itself by a device copy).  Prints the same metric as the default
+    run, with "scaling": "strong"."""
+    import torch
+
+    from paper_2406_08923_gb300 import _lib as L
+    from paper_2406_08923_gb300 import synth
+    from paper_2406_08923_gb300.zslab import ZSlabPlan
+    rank, world, dist = _dist()
+    L.load()
+    stream = torch.cuda.current_stream()
+    n = HEAT_N
+    sp = ZSlabPlan(L.STENCIL_DIFFUSION, (n, n, n), L.STENCIL_F64, L.heat_params(n), rank, world)
+    sp.plan.set_variant(HEADLINE_VARIANT)
+    a, b = sp.alloc(), sp.alloc()
+    sp.upload(a, [synth.heat_field(n)])
+    for _ in range(args.warmup):
+        sp.step(a, b, HEAT_STEPS, stream)
+    _barrier(dist)
+    torch.cuda.synchronize()
+    dev = torch.cuda.current_device()
+    with Clocks(dev) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            sp.step(a, b, HEAT_STEPS, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    _barrier(dist)
+    ms = _max_over_ranks(e0.elapsed_time(e1) / args.steps, dist)
+    line = {"metric": "heat3d_256_fp64_mcell_updates_per_s", "value": round(n ** 3 * HEAT_STEPS / (ms / 1e3) / 1e6, 3),
+            "unit": "Mcell-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "heat3d_r3_256^3_fp64_periodic_euler_dt0.1dx2_100steps",
+                       "parallelism": f"z-slab decomposition of one grid over {world} rank(s), "
+                                      f"{sp.z1 - sp.z0} planes on rank {rank}, 3-plane halo exchange per step",
+                       "kernel_variant": sp.plan.variant()[2]},
+            "gpu_launches": args.steps * HEAT_STEPS * 2, "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_extras(L, synth, stream, hbm_peak, args):
     out = {}
     w, r = 1, 3
@@ -898,6 +948,8 @@ def main():
     ap.add_argument("--radius", type=int, default=None, help="stencil radius for the 1D / 2D --case workloads")
     ap.add_argument("--serving", action="store_true", help="serving configuration only (one JSON line)")
     ap.add_argument("--radius-sweep", action="store_true", help="diffusion radius sweep only (one JSON line)")
+    ap.add_argument("--zslab", action="store_true",
+                    help="the headline job on one grid decomposed along z over the ranks (strong scaling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -905,6 +957,8 @@ def main():
         return run_reference(args)
     if args.case:
         return run_case(args)
+    if args.zslab:
+        return run_zslab(args)
     if args.radius_sweep:
         import torch
 
