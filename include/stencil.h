@@ -297,6 +297,16 @@ stencil_status stencil_sync(stencil_t plan, void *stream);
  * length each CTA streams: the kernel's own choice, half of it, or twice it.  It overwrites
  * fields_out and synchronises `stream`.
  *
+ * 3D FP32 DIFFUSION has each tile shape in two schedules: one launch per Euler step, and a
+ * persistent schedule (variant names ending in "_persist") that runs all nsteps steps of a
+ * stencil_step call in one cooperative launch, each tile waiting only for the tiles whose
+ * cells it reads to finish the previous step (bounded waits; an expired wait ends the call
+ * with STENCIL_ETIMEOUT from the next synchronising call).  Results are bit-identical to the
+ * per-step schedule.  Its synchronisation words are allocated by the plan on first use
+ * (24 bytes + 8 bytes per tile), so the first call must not be made while `stream` is
+ * being captured into a CUDA graph (EINVAL); later calls may be captured.  Two calls of one
+ * plan must not run concurrently on different streams.
+ *
  * The winner is remembered for the problem class -- GPU name and SM count, kind, storage,
  * radius, boundary, dims and nsteps -- for the rest of the process and, when the environment
  * variable STENCIL_AUTOTUNE_CACHE names a writable file, in that file (one line appended per

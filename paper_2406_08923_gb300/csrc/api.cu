@@ -88,6 +88,8 @@ struct stencil_plan {
     double *red_out = nullptr;
     unsigned *err = nullptr;
     void *wdev = nullptr;  // XCORR of radius > 4: the 2r+1 weights on the device (storage type)
+    unsigned long long *psync = nullptr;  // sync words of the persistent heat schedule (persist.cuh)
+    int64_t psync_words = 0;
     int variant = 0;
     int zmode = 0;           // z-chunk length mode of the streaming kernels (zchunk_len)
     int tuned_from_cache = 0;
@@ -145,6 +147,9 @@ static void free_scratch(stencil_t p) {
     if (p->red_out) cudaFree(p->red_out);
     if (p->err) cudaFree(p->err);
     if (p->wdev) cudaFree(p->wdev);
+    if (p->psync) cudaFree(p->psync);
+    p->psync = nullptr;
+    p->psync_words = 0;
     p->partials = p->red_out = nullptr;
     p->err = nullptr;
     p->wdev = nullptr;
@@ -657,6 +662,49 @@ static stencil_status run_pass(stencil_t p, void *const *src, void *const *dst, 
     return STENCIL_OK;
 }
 
+// All nsteps steps of a 3D heat plan whose variant has the persistent schedule: one halo fill
+// of the input, then one cooperative launch.  The plan's sync words grow to the launch's unit
+// count on first use (not while the stream is being captured into a graph).
+static stencil_status step_persistent(stencil_t p, void *const *fin, void *const *fout, int nsteps,
+                                      cudaStream_t s) {
+    const int dt = storage_code(p->storage);
+    int64_t units = 0;
+    CK(p, launch_diffusion_persist(dt, nullptr, nullptr, nullptr, p->geom, p->dcoef, false, nsteps, nullptr, 0,
+                                   p->err, s, p->variant, p->zmode, &units),
+       "persistent heat schedule (unit count)");
+    const int64_t need = PERSIST_HDR + units;
+    if (need > p->psync_words) {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        CK(p, cudaStreamIsCapturing(s, &cap), "cudaStreamIsCapturing");
+        if (cap != cudaStreamCaptureStatusNone)
+            return fail(p, STENCIL_EINVAL,
+                        "the persistent schedule allocates its sync words on first use: run it once before "
+                        "capturing it into a graph");
+        CK(p, cudaStreamSynchronize(s), "cudaStreamSynchronize");
+        if (p->psync) cudaFree(p->psync);
+        p->psync = nullptr;
+        p->psync_words = 0;
+        CK(p, cudaMalloc(&p->psync, need * sizeof(unsigned long long)), "cudaMalloc (sync words)");
+        CK(p, cudaMemsetAsync(p->psync, 0, need * sizeof(unsigned long long), s), "cudaMemsetAsync (sync words)");
+        p->psync_words = need;
+    }
+    if (p->bc != STENCIL_BC_CALLER)
+        CK(p, launch_halo_fill(p->geom, p->radius, p->esize, ptrs(fin, 1), 1, s, p->bc == STENCIL_BC_PERIODIC),
+           "halo_fill launch");
+    int box[3];
+    diffusion_box(dt, p->radius, p->variant, box);
+    CUtensorMap maps[3];
+    const void *bufs[3] = {fin[0], p->tmp[0], fout[0]};
+    for (int i = 0; i < 3; ++i) {
+        stencil_status st = tma_map(p, bufs[i], box, &maps[i]);
+        if (st != STENCIL_OK) return st;
+    }
+    CK(p, launch_diffusion_persist(dt, maps, p->tmp[0], fout[0], p->geom, p->dcoef, p->bc != STENCIL_BC_CALLER,
+                                   nsteps, p->psync, p->psync_words, p->err, s, p->variant, p->zmode, &units),
+       "persistent heat launch");
+    return STENCIL_OK;
+}
+
 stencil_status stencil_step(stencil_t p, void *const *fin, void *const *fout, int nsteps, void *stream) {
     if (!p) return fail(nullptr, STENCIL_EINVAL, "plan is NULL");
     stencil_status st = check_device(p);
@@ -679,6 +727,10 @@ stencil_status stencil_step(stencil_t p, void *const *fin, void *const *fout, in
             CK(p, cudaMemcpyAsync(fout[q], fin[q], p->bytes_per_field, cudaMemcpyDeviceToDevice, s), "copy");
         return stencil_halo_fill(p, fout, stream);
     }
+
+    if (p->kind == STENCIL_DIFFUSION && p->ndim == 3 &&
+        diffusion_persistent(storage_code(p->storage), p->radius, p->variant))
+        return step_persistent(p, fin, fout, nsteps, s);
 
     // pass list
     std::vector<int> sweeps;  // XCORR (and 1D DIFFUSION): sweeps per launch; others: one entry per pass

@@ -297,6 +297,50 @@ heat32_kernel(const __grid_constant__ CUtensorMap map_in, float *__restrict__ ou
                                                   images, err, ring, full);
 }
 
+// Persistent schedule: all nsteps steps in one cooperative launch, units published per step
+// and face-neighbour waits instead of kernel boundaries (persist.cuh).  Step s reads the
+// field written by step s-1 (the input for s = 0) and writes `out` when nsteps - 1 - s is
+// even, `tmp` otherwise, so the last step writes `out` and the input is only read.
+template <int BY, int RY, int ZB, int NSLOT, int R, int MINB, bool XVEC>
+__global__ void __launch_bounds__(32 * BY, MINB)
+heat32_persist_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ CUtensorMap map_tmp,
+                      const __grid_constant__ CUtensorMap map_out, float *tmp, float *out, Geom g, Coef32 c,
+                      PersistGrid pg, int nsteps, int images, unsigned long long *sync, unsigned *err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float *ring = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    __shared__ __align__(8) uint64_t full[NSLOT];
+    __shared__ unsigned long long s_base;
+    if (threadIdx.x == 0) s_base = ld_relaxed_u64(sync);  // written by the previous launch
+    __syncthreads();
+    const unsigned long long base = s_base;
+    const int W = pg.units();
+    bool ok = true;
+    for (int s = 0; ok && s < nsteps; ++s) {
+        const bool to_out = ((nsteps - 1 - s) & 1) == 0;
+        float *dst = to_out ? out : tmp;
+        const CUtensorMap *src = s == 0 ? &map_in : (to_out ? &map_tmp : &map_out);
+        for (int u = blockIdx.x; ok && u < W; u += gridDim.x) {
+            const int t0 = u % pg.nt[0], t1 = (u / pg.nt[0]) % pg.nt[1], t2 = u / (pg.nt[0] * pg.nt[1]);
+            if (s > 0) ok = wait_face_neighbours<R>(sync, pg, g, t0, t1, t2, base + s, base + 1);
+            if (ok) {
+                if (threadIdx.x == 0) fence_proxy_async_global();  // acquired stores -> this CTA's TMA loads
+                ok = heat32_tile<BY, RY, ZB, NSLOT, R, XVEC, false>(src, dst, g, c, t0, t1, t2, pg.tl[2], images, err,
+                                                                     ring, full);
+            }
+            fence_proxy_async_global();  // this thread's stores -> TMA loads of the next step
+            __syncthreads();
+            if (ok && threadIdx.x == 0) {
+                publish_unit(sync, u, base + s + 1);
+                for (int k = 0; k < NSLOT; ++k) mbar_inval(&full[k]);  // initialised again by the next unit
+            }
+        }
+    }
+    if (threadIdx.x == 0) {
+        if (!ok) atomicOr(err, ERR_TIMEOUT);
+        persist_exit(sync, base, nsteps, !ok);
+    }
+}
+
 // Vector x-images need nx a multiple of 4 and one spare padding element beyond each x halo.
 __host__ __device__ bool xvec_ok(const Geom &g) {
     return g.n[0] % 4 == 0 && g.n[0] >= 8 && g.off[0] >= 4 && g.pad[0] >= g.off[0] + g.n[0] + 4;
@@ -310,30 +354,79 @@ Coef32 coef32(const DiffCoef &dc) {
     return c;
 }
 
+// Resident CTAs per SM of kernel k (cached per device), after raising its shared-memory limit.
+template <typename K> cudaError_t occupancy(K k, int threads, size_t smem, int cache[64], int *occ) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!cache[dev]) {
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int o = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, threads, smem);
+        if (e != cudaSuccess) return e;
+        cache[dev] = std::max(o, 1);
+    }
+    *occ = cache[dev];
+    return cudaSuccess;
+}
+
+// Unit decomposition shared by both schedules: 128 x TY tiles of the xy-plane, z split into
+// chunks so that the units fill the resident CTA slots (choose_zchunks), then zmode.
+template <int BY, int RY, int ZB, int NSLOT, int R>
+PersistGrid units_of(const Geom &g, int slots, int zmode) {
+    using Cfg = H32<BY, RY, ZB, NSLOT, R>;
+    const int tx = (int)((g.n[0] + Cfg::TX - 1) / Cfg::TX), ty = (int)((g.n[1] + Cfg::TY - 1) / Cfg::TY);
+    const int nz = (int)g.n[2];
+    const int chunks = choose_zchunks(tx * ty, nz, slots, 0.5);
+    const int zc = zchunk_len((nz + chunks - 1) / chunks, nz, zmode);
+    return PersistGrid{{tx, ty, (nz + zc - 1) / zc}, {Cfg::TX, Cfg::TY, zc}};
+}
+
 template <int BY, int RY, int ZB, int NSLOT, int R, int MINB, bool XVEC>
 cudaError_t run(const CUtensorMap *map, float *out, const Geom &g, const Coef32 &c, bool images, unsigned *err,
                 cudaStream_t s, int zmode) {
     using Cfg = H32<BY, RY, ZB, NSLOT, R>;
     auto k = heat32_kernel<BY, RY, ZB, NSLOT, R, MINB, XVEC>;
-    static int occ[64] = {};  // resident CTAs per SM, per device
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    static int occ_cache[64] = {};
+    int occ = 0;
+    cudaError_t e = occupancy(k, 32 * BY, Cfg::SMEM, occ_cache, &occ);
     if (e != cudaSuccess) return e;
-    if (dev >= 64) return cudaErrorInvalidDevice;
-    if (!occ[dev]) {
-        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
-        if (e != cudaSuccess) return e;
-        int o = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, 32 * BY, Cfg::SMEM);
-        if (e != cudaSuccess) return e;
-        occ[dev] = std::max(o, 1);
-    }
-    const int tx = (int)((g.n[0] + Cfg::TX - 1) / Cfg::TX), ty = (int)((g.n[1] + Cfg::TY - 1) / Cfg::TY);
-    const int nz = (int)g.n[2];
-    const int chunks = choose_zchunks(tx * ty, nz, occ[dev] * device_sms(), 0.5);
-    const int zc = zchunk_len((nz + chunks - 1) / chunks, nz, zmode);
-    dim3 grid(tx, ty, (unsigned)((nz + zc - 1) / zc));
-    return launch_pdl(k, grid, dim3(32 * BY), Cfg::SMEM, s, *map, out, g, c, zc, images ? 1 : 0, err);
+    const PersistGrid pg = units_of<BY, RY, ZB, NSLOT, R>(g, occ * device_sms(), zmode);
+    dim3 grid(pg.nt[0], pg.nt[1], pg.nt[2]);
+    return launch_pdl(k, grid, dim3(32 * BY), Cfg::SMEM, s, *map, out, g, c, pg.tl[2], images ? 1 : 0, err);
+}
+
+// Persistent schedule.  With sync == nullptr only reports the number of units (the sync
+// buffer needs PERSIST_HDR + units words).
+template <int BY, int RY, int ZB, int NSLOT, int R, int MINB, bool XVEC>
+cudaError_t run_persist(const CUtensorMap *maps, float *tmp, float *out, const Geom &g, const Coef32 &c, bool images,
+                        int nsteps, unsigned long long *sync, int64_t sync_words, unsigned *err, cudaStream_t s,
+                        int zmode, int64_t *units) {
+    using Cfg = H32<BY, RY, ZB, NSLOT, R>;
+    auto k = heat32_persist_kernel<BY, RY, ZB, NSLOT, R, MINB, XVEC>;
+    static int occ_cache[64] = {};
+    int occ = 0;
+    cudaError_t e = occupancy(k, 32 * BY, Cfg::SMEM, occ_cache, &occ);
+    if (e != cudaSuccess) return e;
+    const PersistGrid pg = units_of<BY, RY, ZB, NSLOT, R>(g, occ * device_sms(), zmode);
+    const int W = pg.units();
+    if (units) *units = W;
+    if (!sync) return cudaSuccess;
+    if (PERSIST_HDR + (int64_t)W > sync_words) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)std::min(W, occ * device_sms()));
+    cfg.blockDim = dim3(32 * BY);
+    cfg.dynamicSmemBytes = Cfg::SMEM;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;  // every CTA resident: the neighbour waits rely on it
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, maps[0], maps[1], maps[2], tmp, out, g, c, pg, nsteps, images ? 1 : 0, sync,
+                              err);
 }
 
 // Variant tables: (BY warps, RY rows, ZB planes per iteration, NSLOT ring depth, MINB resident
@@ -347,10 +440,21 @@ cudaError_t run(const CUtensorMap *map, float *out, const Geom &g, const Coef32 
     X(8, 2, 2, 8, 2)
 #define HEAT32_VARIANTS_OTHER(X) X(4, 2, 2, 8, 3)
 
-const char *const NAMES_R3[] = {"f32_by4_ry2_zb2_s8_m3", "f32_by4_ry1_zb2_s8_m4", "f32_by8_ry1_zb2_s8_m2",
-                                "f32_by4_ry1_zb2_s8_m3", "f32_by8_ry2_zb2_s8_m2"};
-const char *const NAMES_OTHER[] = {"?", "f32_r1_by4_ry2_zb2_s8_m3", "f32_r2_by4_ry2_zb2_s8_m3", "?",
-                                   "f32_r4_by4_ry2_zb2_s8_m3"};
+// Each tile shape comes in both schedules: variants 0 .. n-1 launch once per step (PDL),
+// variants n .. 2n-1 run all steps of a call in one persistent launch (suffix "_persist").
+constexpr int N_R3 = 5, N_OTHER = 1;
+const char *const NAMES_R3[] = {"f32_by4_ry2_zb2_s8_m3",         "f32_by4_ry1_zb2_s8_m4",
+                                "f32_by8_ry1_zb2_s8_m2",         "f32_by4_ry1_zb2_s8_m3",
+                                "f32_by8_ry2_zb2_s8_m2",         "f32_by4_ry2_zb2_s8_m3_persist",
+                                "f32_by4_ry1_zb2_s8_m4_persist", "f32_by8_ry1_zb2_s8_m2_persist",
+                                "f32_by4_ry1_zb2_s8_m3_persist", "f32_by8_ry2_zb2_s8_m2_persist"};
+const char *const NAMES_OTHER[][2] = {{"?", "?"},
+                                      {"f32_r1_by4_ry2_zb2_s8_m3", "f32_r1_by4_ry2_zb2_s8_m3_persist"},
+                                      {"f32_r2_by4_ry2_zb2_s8_m3", "f32_r2_by4_ry2_zb2_s8_m3_persist"},
+                                      {"?", "?"},
+                                      {"f32_r4_by4_ry2_zb2_s8_m3", "f32_r4_by4_ry2_zb2_s8_m3_persist"}};
+
+constexpr int n_shapes(int r) { return r == 3 ? N_R3 : N_OTHER; }
 
 template <int R>
 cudaError_t dispatch(int variant, const CUtensorMap *map, float *out, const Geom &g, const Coef32 &c, bool images,
@@ -371,17 +475,41 @@ cudaError_t dispatch(int variant, const CUtensorMap *map, float *out, const Geom
     return res;
 }
 
+template <int R>
+cudaError_t dispatch_persist(int shape, const CUtensorMap *maps, float *tmp, float *out, const Geom &g,
+                             const Coef32 &c, bool images, int nsteps, unsigned long long *sync, int64_t sync_words,
+                             unsigned *err, cudaStream_t s, int zmode, int64_t *units) {
+    const bool xv = xvec_ok(g);
+    int i = 0;
+    cudaError_t res = cudaErrorInvalidValue;
+#define X(BY, RY, ZB, NS, MB)                                                                                   \
+    if (i++ == shape)                                                                                           \
+        res = xv ? run_persist<BY, RY, ZB, NS, R, MB, true>(maps, tmp, out, g, c, images, nsteps, sync, sync_words, \
+                                                            err, s, zmode, units)                               \
+                 : run_persist<BY, RY, ZB, NS, R, MB, false>(maps, tmp, out, g, c, images, nsteps, sync,         \
+                                                             sync_words, err, s, zmode, units);
+    if constexpr (R == 3) {
+        HEAT32_VARIANTS_R3(X)
+    } else {
+        HEAT32_VARIANTS_OTHER(X)
+    }
+#undef X
+    return res;
+}
+
 }  // namespace
 
-int diffusion_f32_num_variants(int r) { return r == 3 ? 5 : (r >= 1 && r <= 4 ? 1 : 0); }
+int diffusion_f32_num_variants(int r) { return r >= 1 && r <= 4 ? 2 * n_shapes(r) : 0; }
+
+bool diffusion_f32_persistent(int r, int v) { return v >= n_shapes(r) && v < diffusion_f32_num_variants(r); }
 
 const char *diffusion_f32_variant_name(int r, int v) {
     if (v < 0 || v >= diffusion_f32_num_variants(r)) return "?";
-    return r == 3 ? NAMES_R3[v] : NAMES_OTHER[r];
+    return r == 3 ? NAMES_R3[v] : NAMES_OTHER[r][v];
 }
 
 void diffusion_f32_box(int r, int v, int box[3]) {
-    (void)v;  // every variant has the 128-wide tile; the rows depend on BY RY
+    v %= n_shapes(r);  // both schedules of a shape load the same box
     int i = 0;
     box[0] = H32<1, 1, 2, 8, 1>::TXP;
     box[2] = 1;
@@ -395,8 +523,37 @@ void diffusion_f32_box(int r, int v, int box[3]) {
 #undef X
 }
 
+cudaError_t launch_diffusion_f32_persist(const CUtensorMap *maps, float *tmp, float *out, const Geom &g,
+                                         const DiffCoef &dc, bool images, int nsteps, unsigned long long *sync,
+                                         int64_t sync_words, unsigned *err, cudaStream_t s, int variant, int zmode,
+                                         int64_t *units) {
+    if (!diffusion_f32_persistent(dc.r, variant)) return cudaErrorInvalidValue;
+    const Coef32 c = coef32(dc);
+    const int shape = variant - n_shapes(dc.r);
+    switch (dc.r) {
+    case 1: return dispatch_persist<1>(shape, maps, tmp, out, g, c, images, nsteps, sync, sync_words, err, s, zmode, units);
+    case 2: return dispatch_persist<2>(shape, maps, tmp, out, g, c, images, nsteps, sync, sync_words, err, s, zmode, units);
+    case 3: return dispatch_persist<3>(shape, maps, tmp, out, g, c, images, nsteps, sync, sync_words, err, s, zmode, units);
+    case 4: return dispatch_persist<4>(shape, maps, tmp, out, g, c, images, nsteps, sync, sync_words, err, s, zmode, units);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// Persistent variants exist for FP32 storage only (dtype 2).
+bool diffusion_persistent(int dtype, int r, int v) { return dtype == 2 && diffusion_f32_persistent(r, v); }
+
+cudaError_t launch_diffusion_persist(int dtype, const CUtensorMap *maps, void *tmp, void *out, const Geom &g,
+                                     const DiffCoef &c, bool images, int nsteps, unsigned long long *sync,
+                                     int64_t sync_words, unsigned *err, cudaStream_t s, int variant, int zmode,
+                                     int64_t *units) {
+    if (dtype != 2) return cudaErrorInvalidValue;
+    return launch_diffusion_f32_persist(maps, static_cast<float *>(tmp), static_cast<float *>(out), g, c, images,
+                                        nsteps, sync, sync_words, err, s, variant, zmode, units);
+}
+
 cudaError_t launch_diffusion_f32(const CUtensorMap *map, float *out, const Geom &g, const DiffCoef &dc, bool images,
                                  unsigned *err, cudaStream_t s, int variant, int zmode) {
+    if (diffusion_f32_persistent(dc.r, variant)) return cudaErrorInvalidValue;  // one launch per call
     const Coef32 c = coef32(dc);
     switch (dc.r) {
     case 1: return dispatch<1>(variant, map, out, g, c, images, err, s, zmode);

@@ -2,6 +2,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "persist.cuh"
 
 namespace stn {
 
@@ -74,12 +75,27 @@ cudaError_t launch_diffusion(int dtype, const CUtensorMap *map_in, void *out, co
 int diffusion_num_variants(int dtype, int r);
 const char *diffusion_variant_name(int dtype, int r, int variant);
 void diffusion_box(int dtype, int r, int variant, int box[3]);  // TMA box (x, y, z) of a variant
+// Persistent variants run all nsteps steps of a call in one cooperative launch (persist.cuh):
+// step s reads the field written by step s-1 (maps[0], the input, for s = 0) and writes `out`
+// when nsteps - 1 - s is even, `tmp` otherwise; maps = {in, tmp, out}.  `sync` is a zeroed
+// buffer of at least PERSIST_HDR + units 64-bit words kept between calls; with sync == nullptr
+// the call only reports the launch's unit count in *units.
+bool diffusion_persistent(int dtype, int r, int variant);
+cudaError_t launch_diffusion_persist(int dtype, const CUtensorMap *maps, void *tmp, void *out, const Geom &g,
+                                     const DiffCoef &c, bool images, int nsteps, unsigned long long *sync,
+                                     int64_t sync_words, unsigned *err, cudaStream_t s, int variant, int zmode,
+                                     int64_t *units);
 // The FP32 kernel family (diffusion_f32.cu), reached through the functions above for dtype 2.
 int diffusion_f32_num_variants(int r);
 const char *diffusion_f32_variant_name(int r, int variant);
 void diffusion_f32_box(int r, int variant, int box[3]);
 cudaError_t launch_diffusion_f32(const CUtensorMap *map_in, float *out, const Geom &g, const DiffCoef &c,
                                  bool images, unsigned *err, cudaStream_t s, int variant, int zmode = 0);
+bool diffusion_f32_persistent(int r, int variant);
+cudaError_t launch_diffusion_f32_persist(const CUtensorMap *maps, float *tmp, float *out, const Geom &g,
+                                         const DiffCoef &c, bool images, int nsteps, unsigned long long *sync,
+                                         int64_t sync_words, unsigned *err, cudaStream_t s, int variant, int zmode,
+                                         int64_t *units);
 // 2D (diffusion2d.cu): one TMA tile per CTA, no streaming axis.
 cudaError_t launch_diffusion2d(int dtype, const CUtensorMap *map_in, void *out, const Geom &g, const DiffCoef &c,
                                bool images, unsigned *err, cudaStream_t s);
