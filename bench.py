@@ -59,10 +59,10 @@ NCU_TRAFFIC = {
                 "src": {"diffusion_f32.cu": "e7b76b56f8dd9baa", "common.cuh": "3f7458d1c75ca5f9"}},
     "heat_f32_512": {"variant": "f32_by8_ry2_zb2_s8_m2", "zmode": 0, "bytes": 586106795 + 523721984,
                 "src": {"diffusion_f32.cu": "e7b76b56f8dd9baa", "common.cuh": "3f7458d1c75ca5f9"}},
-    "mhd_f32": {"variant": "tx32_ty12_s8_b1", "zmode": 0, "bytes": 5662824619 + 4940957696,
-                "src": {"mhd.cu": "30a002e933a67717", "mhd_rhs.cuh": "be5b445fecd5703b", "common.cuh": "3f7458d1c75ca5f9"}},
-    "mhd_bf16": {"variant": "tx32_ty8_s8_b2", "zmode": 0, "bytes": 3912996437 + 2612448085,
-                "src": {"mhd.cu": "30a002e933a67717", "mhd_rhs.cuh": "be5b445fecd5703b", "common.cuh": "3f7458d1c75ca5f9"}},
+    "mhd_f32": {"variant": "tx32_ty12_s8_b1", "zmode": 0, "bytes": 5625796608 + 4938428587,
+                "src": {"mhd.cu": "63e9a0cd3f94e750", "mhd_rhs.cuh": "be5b445fecd5703b", "common.cuh": "3f7458d1c75ca5f9"}},
+    "mhd_bf16": {"variant": "tx32_ty8_s8_b2", "zmode": 0, "bytes": 3373316011 + 2582517248,
+                "src": {"mhd.cu": "63e9a0cd3f94e750", "mhd_rhs.cuh": "be5b445fecd5703b", "common.cuh": "3f7458d1c75ca5f9"}},
 }
 
 

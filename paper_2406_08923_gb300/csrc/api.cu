@@ -82,8 +82,8 @@ struct stencil_plan {
     MhdConst mconst{};
     // library-owned scratch
     void *tmp[8] = {};  // second field set for ping-pong (padded layout)
-    void *w[8] = {};    // RK register (dense interior, storage type)
-    void *kc[8] = {};   // Kahan compensation (dense interior, storage type)
+    void *w[8] = {};    // MHD8: w[0] the RK register (dense interior, storage type, 8 fields
+    void *kc[8] = {};   // interleaved per cell); kc[0] the Kahan terms, same layout
     double *partials = nullptr;
     double *red_out = nullptr;
     unsigned *err = nullptr;
@@ -525,9 +525,8 @@ stencil_status stencil_create(int ndim, const int64_t dims[3], int radius, const
     const size_t ncell = (size_t)(g.n[0] * g.n[1] * g.n[2]);
     for (int q = 0; q < nfields && okay; ++q) okay = alloc(&p->tmp[q], p->bytes_per_field, "cudaMalloc(ping-pong field)");
     if (kind == STENCIL_MHD8) {
-        for (int q = 0; q < 8 && okay; ++q) okay = alloc(&p->w[q], ncell * p->esize, "cudaMalloc(RK register)");
-        if (storage != STENCIL_F64)
-            for (int q = 0; q < 8 && okay; ++q) okay = alloc(&p->kc[q], ncell * p->esize, "cudaMalloc(Kahan term)");
+        okay = alloc(&p->w[0], 8 * ncell * p->esize, "cudaMalloc(RK register)");
+        if (okay && storage != STENCIL_F64) okay = alloc(&p->kc[0], 8 * ncell * p->esize, "cudaMalloc(Kahan terms)");
     }
     if (okay) okay = alloc((void **)&p->partials, sizeof(double) * norms_blocks() * nfields * 4, "cudaMalloc(norm partials)");
     if (okay) okay = alloc((void **)&p->red_out, sizeof(double) * nfields * 4, "cudaMalloc(norm result)");
@@ -656,7 +655,7 @@ static stencil_status run_pass(stencil_t p, void *const *src, void *const *dst, 
         if (st != STENCIL_OK) return st;
     }
     Ptrs8 none{};
-    CK(p, launch_mhd(storage_code(p->storage), 0, sub, maps, ptrs(dst, 8), ptrs(p->w, 8), ptrs(p->kc, 8), none,
+    CK(p, launch_mhd(storage_code(p->storage), 0, sub, maps, ptrs(dst, 8), p->w[0], p->kc[0], none,
                      g, p->mconst, true, p->err, s, p->variant, p->zmode),
        "mhd launch");
     return STENCIL_OK;
@@ -765,7 +764,7 @@ stencil_status stencil_step(stencil_t p, void *const *fin, void *const *fout, in
         CK(p, launch_halo_fill(p->geom, p->radius, p->esize, ptrs(fin, p->nfields), p->nfields, s, periodic),
            "halo_fill launch");
     if (p->kind == STENCIL_MHD8 && p->storage != STENCIL_F64)
-        for (int q = 0; q < 8; ++q) CK(p, cudaMemsetAsync(p->kc[q], 0, ncell * p->esize, s), "clear Kahan terms");
+        CK(p, cudaMemsetAsync(p->kc[0], 0, 8 * ncell * p->esize, s), "clear Kahan terms");
 
     // ping-pong so that the last pass writes fields_out and fields_in is only read
     void *const *src = fin;
@@ -814,7 +813,7 @@ stencil_status stencil_substep(stencil_t p, void *const *fin, void *const *fout,
        "halo_fill launch");
     if (substep == 0 && p->storage != STENCIL_F64) {
         const size_t ncell = (size_t)(p->geom.n[0] * p->geom.n[1] * p->geom.n[2]);
-        for (int q = 0; q < 8; ++q) CK(p, cudaMemsetAsync(p->kc[q], 0, ncell * p->esize, s), "clear Kahan terms");
+        CK(p, cudaMemsetAsync(p->kc[0], 0, 8 * ncell * p->esize, s), "clear Kahan terms");
     }
     return run_pass(p, fin, fout, 1, substep, s);
 }
@@ -837,7 +836,7 @@ stencil_status stencil_mhd_rhs(stencil_t p, void *const *fields, void *const *rh
         if (st != STENCIL_OK) return st;
     }
     Ptrs8 none{};
-    CK(p, launch_mhd(storage_code(p->storage), 1, 0, maps, none, none, none, ptrs(rhs, 8), p->geom, p->mconst,
+    CK(p, launch_mhd(storage_code(p->storage), 1, 0, maps, none, nullptr, nullptr, ptrs(rhs, 8), p->geom, p->mconst,
                      false, p->err, s, p->variant, p->zmode),
        "mhd rhs launch");
     return STENCIL_OK;

@@ -99,7 +99,7 @@ struct Req {
     size_t bytes = 0;
     void *base = nullptr;
     float *set[2][8] = {};
-    float *w[8] = {}, *kc[8] = {};
+    float *w = nullptr, *kc = nullptr;  // RK register and Kahan terms, 8 fields interleaved per cell
     CUtensorMap *dmaps = nullptr;  // [2][nf] descriptors in device memory
     CUtensorMap hmaps[16];         // host copy the upload reads from (lives as long as the request)
     int tiles[3] = {1, 1, 1}, zc = 1;
@@ -193,8 +193,10 @@ stencil_status admit(stencil_server_t s, Req *r) {
         for (int q = 0; q < r->nf; ++q, p += fb) r->set[k][q] = reinterpret_cast<float *>(p);
     if (r->kind == STENCIL_MHD8) {
         const size_t db = up256(r->ncell * sizeof(float));
-        for (int q = 0; q < 8; ++q, p += db) r->w[q] = reinterpret_cast<float *>(p);
-        for (int q = 0; q < 8; ++q, p += db) r->kc[q] = reinterpret_cast<float *>(p);
+        r->w = reinterpret_cast<float *>(p);
+        p += 8 * db;
+        r->kc = reinterpret_cast<float *>(p);
+        p += 8 * db;
     }
     r->dmaps = reinterpret_cast<CUtensorMap *>(p);
     // upload the dense initial fields into set 1 (as staging), pack into set 0 with halos
@@ -206,7 +208,7 @@ stencil_status admit(stencil_server_t s, Req *r) {
         SCK(s, cudaGetLastError(), "pack launch");
     }
     if (r->kind == STENCIL_MHD8)
-        for (int q = 0; q < 8; ++q) SCK(s, cudaMemsetAsync(r->kc[q], 0, r->ncell * sizeof(float), st), "clear Kahan");
+        SCK(s, cudaMemsetAsync(r->kc, 0, 8 * r->ncell * sizeof(float), st), "clear Kahan");
     // TMA descriptors of both field sets
     if (r->kind != STENCIL_XCORR) {
         int box[3], tx, ty;
@@ -540,11 +542,9 @@ stencil_status stencil_server_progress(stencil_server_t s, int *n_pending, int *
                     BatchMhd &it = reinterpret_cast<BatchMhd *>(h + off_mhd + sub * mhd_stride)[hdr->n_mhd];
                     const int src = r->cur ^ (sub & 1);
                     it.maps = r->dmaps + src * 8;
-                    for (int q = 0; q < 8; ++q) {
-                        it.fout.p[q] = r->set[src ^ 1][q];
-                        it.w.p[q] = r->w[q];
-                        it.kc.p[q] = r->kc[q];
-                    }
+                    for (int q = 0; q < 8; ++q) it.fout.p[q] = r->set[src ^ 1][q];
+                    it.w = r->w;
+                    it.kc = r->kc;
                     it.g = r->g;
                     it.k = r->k;
                     it.zc = r->zc;

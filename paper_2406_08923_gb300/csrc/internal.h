@@ -119,8 +119,11 @@ struct MhdMaps {
 
 // mode 0: RK substep `sub` (0..2) writing f_out (+images), w and (for Kahan) c;
 // mode 1: right-hand side only, written densely to rhs (compute type).
+// The RK register w and the Kahan terms c are one array each, in the storage type, with the 8
+// fields of a cell next to each other (element 8 cell + q; `cell` the dense interior index),
+// so a cell's 8 values move as 16-byte vectors.
 cudaError_t launch_mhd(int storage, int mode, int sub, const MhdMaps &maps, const Ptrs8 &fout,
-                       const Ptrs8 &w, const Ptrs8 &kc, const Ptrs8 &rhs, const Geom &g,
+                       void *w, void *kc, const Ptrs8 &rhs, const Geom &g,
                        const MhdConst &k, bool images, unsigned *err, cudaStream_t s,
                        int variant, int zmode = 0);
 void mhd_box(int storage, int variant, int box[3]);
@@ -168,7 +171,8 @@ struct BatchHeat {
 };
 struct BatchMhd {
     const CUtensorMap *maps;  // 8 consecutive descriptors of the source field set
-    Ptrs8 fout, w, kc;
+    Ptrs8 fout;
+    float *w, *kc;  // RK register and Kahan terms, 8 fields interleaved per cell (launch_mhd)
     Geom g;
     MK<float> k;  // alpha/beta filled in per launch
     int zc, tiles_x, tiles_y, tiles_z;

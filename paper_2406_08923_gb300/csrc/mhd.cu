@@ -72,12 +72,45 @@ struct Win {
     }
 };
 
+// The 8 interleaved values of one cell in the RK register / Kahan arrays (16-byte aligned):
+// loaded and stored as 16-byte vectors.
+template <typename S, typename C>
+__device__ __forceinline__ void load8(const S *p, C (&v)[8]) {
+    if constexpr (sizeof(S) == 2) {
+        const uint4 a = *reinterpret_cast<const uint4 *>(p);
+        const S *e = reinterpret_cast<const S *>(&a);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = to_c<C>(e[q]);
+    } else {
+        constexpr int PER = 16 / (int)sizeof(S);  // values per 16-byte vector
+#pragma unroll
+        for (int h = 0; h < 8 / PER; ++h) {
+            const uint4 a = reinterpret_cast<const uint4 *>(p)[h];
+            const S *e = reinterpret_cast<const S *>(&a);
+#pragma unroll
+            for (int u = 0; u < PER; ++u) v[h * PER + u] = to_c<C>(e[u]);
+        }
+    }
+}
+template <typename S>
+__device__ __forceinline__ void store8(S *p, const S (&v)[8]) {
+    constexpr int PER = 16 / (int)sizeof(S);
+#pragma unroll
+    for (int h = 0; h < 8 / PER; ++h) {
+        uint4 a;
+        S *e = reinterpret_cast<S *>(&a);
+#pragma unroll
+        for (int u = 0; u < PER; ++u) e[u] = v[h * PER + u];
+        reinterpret_cast<uint4 *>(p)[h] = a;
+    }
+}
+
 // One xy-tile of one z-chunk of one RK substep (or RHS evaluation): the whole pipeline of a
 // CTA.  `maps` points at 8 consecutive descriptors (parameter or global memory); `k` may live
 // in parameter or shared memory.  Returns false if a bounded wait expired.
 template <typename S, typename C, bool KAHAN, int MODE, int TX, int TY, int NSLOT, bool CONDUCT>
-__device__ __forceinline__ bool mhd_tile(const CUtensorMap *maps, const Ptrs8 &fout, const Ptrs8 &wbuf,
-                                         const Ptrs8 &kbuf, const Ptrs8 &rbuf, const Geom &g, const MK<C> &k,
+__device__ __forceinline__ bool mhd_tile(const CUtensorMap *maps, const Ptrs8 &fout, S *wbuf, S *kbuf,
+                                         const Ptrs8 &rbuf, const Geom &g, const MK<C> &k,
                                          int tile_x, int tile_y, int tile_z, int zc, int first, int last,
                                          int images, unsigned *err, S *ring, uint64_t *full) {
     using Cfg = MhdCfg<S, TX, TY, NSLOT>;
@@ -123,10 +156,9 @@ __device__ __forceinline__ bool mhd_tile(const CUtensorMap *maps, const Ptrs8 &f
     C wpre[8], kpre[8];
     auto prefetch = [&](int64_t c) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            wpre[q] = (MODE == 0 && !first) ? to_c<C>(static_cast<const S *>(wbuf.p[q])[c]) : C(0);
-            kpre[q] = (MODE == 0 && KAHAN) ? to_c<C>(static_cast<const S *>(kbuf.p[q])[c]) : C(0);
-        }
+        for (int q = 0; q < 8; ++q) wpre[q] = kpre[q] = C(0);
+        if (MODE == 0 && !first) load8<S, C>(wbuf + 8 * c, wpre);
+        if (MODE == 0 && KAHAN) load8<S, C>(kbuf + 8 * c, kpre);
     };
     if (active && zc0 < zend) prefetch(cell);
 
@@ -153,16 +185,18 @@ __device__ __forceinline__ bool mhd_tile(const CUtensorMap *maps, const Ptrs8 &f
 #pragma unroll
                 for (int q = 0; q < 8; ++q) static_cast<C *>(rbuf.p[q])[cell] = rhs[q];
             } else {
-                S fnew[8];
+                S fnew[8], wst[8], kst[8];
                 auto rt = [](C v) { return to_c<C>(to_s<S>(v)); };  // round to the storage type
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     C wv, fv, kv;
                     rk_update<KAHAN>(k, first != 0, rhs[q], wcur[q], kcur[q], val[q], wv, fv, kv, rt);
-                    if (!last) static_cast<S *>(wbuf.p[q])[cell] = to_s<S>(wv);
-                    if (KAHAN) static_cast<S *>(kbuf.p[q])[cell] = to_s<S>(kv);
+                    wst[q] = to_s<S>(wv);
+                    kst[q] = to_s<S>(kv);
                     fnew[q] = to_s<S>(fv);
                 }
+                if (!last) store8<S>(wbuf + 8 * cell, wst);
+                if (KAHAN) store8<S>(kbuf + 8 * cell, kst);
                 if (images && (edge_xy || z < R6 || z >= nz - R6)) {
 #pragma unroll
                     for (int q = 0; q < 8; ++q)
@@ -189,7 +223,7 @@ __device__ __forceinline__ bool mhd_tile(const CUtensorMap *maps, const Ptrs8 &f
 
 template <typename S, typename C, bool KAHAN, int MODE, int TX, int TY, int NSLOT, int MINB, bool CONDUCT>
 __global__ void __launch_bounds__(TX *TY, MINB)
-mhd_kernel(const __grid_constant__ MhdMaps maps, Ptrs8 fout, Ptrs8 wbuf, Ptrs8 kbuf, Ptrs8 rbuf, Geom g,
+mhd_kernel(const __grid_constant__ MhdMaps maps, Ptrs8 fout, S *wbuf, S *kbuf, Ptrs8 rbuf, Geom g,
            MK<C> k, int zc, int first, int last, int images, unsigned *err) {
     using Cfg = MhdCfg<S, TX, TY, NSLOT>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -227,7 +261,7 @@ static const double RK_A[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0};
 static const double RK_B[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
 
 template <typename S, typename C, bool KAHAN, int MODE, int TX, int TY, int NSLOT, int MINB, bool CONDUCT>
-static cudaError_t run(int sub, const MhdMaps &maps, const Ptrs8 &fo, const Ptrs8 &w, const Ptrs8 &kc,
+static cudaError_t run(int sub, const MhdMaps &maps, const Ptrs8 &fo, void *w, void *kc,
                        const Ptrs8 &rhs, const Geom &g, const MhdConst &c, bool images, unsigned *err,
                        cudaStream_t s, int zmode) {
     using Cfg = MhdCfg<S, TX, TY, NSLOT>;
@@ -251,8 +285,8 @@ static cudaError_t run(int sub, const MhdMaps &maps, const Ptrs8 &fo, const Ptrs
     const int chunks = choose_zchunks(tx * ty, nz, occ[dev] * device_sms(), 0.5);
     const int zc = zchunk_len((nz + chunks - 1) / chunks, nz, zmode);
     dim3 grid(tx, ty, (unsigned)((nz + zc - 1) / zc));
-    kern<<<grid, TX * TY, Cfg::SMEM, s>>>(maps, fo, w, kc, rhs, g, k, zc, sub == 0 ? 1 : 0, sub == 2 ? 1 : 0,
-                                          images ? 1 : 0, err);
+    kern<<<grid, TX * TY, Cfg::SMEM, s>>>(maps, fo, static_cast<S *>(w), static_cast<S *>(kc), rhs, g, k, zc,
+                                          sub == 0 ? 1 : 0, sub == 2 ? 1 : 0, images ? 1 : 0, err);
     return cudaGetLastError();
 }
 
@@ -289,8 +323,8 @@ void mhd_box(int storage, int v, int box[3]) {
 #undef X
 }
 
-cudaError_t launch_mhd(int storage, int mode, int sub, const MhdMaps &maps, const Ptrs8 &fo, const Ptrs8 &w,
-                       const Ptrs8 &kc, const Ptrs8 &rhs, const Geom &g, const MhdConst &c, bool images,
+cudaError_t launch_mhd(int storage, int mode, int sub, const MhdMaps &maps, const Ptrs8 &fo, void *w, void *kc,
+                       const Ptrs8 &rhs, const Geom &g, const MhdConst &c, bool images,
                        unsigned *err, cudaStream_t s, int variant, int zmode) {
     int i = 0;
     cudaError_t res = cudaErrorInvalidValue;
