@@ -66,16 +66,23 @@ NCU_TRAFFIC = {
 }
 
 
+def _traffic_records(case):
+    """The capture records of a case: one record, or a list (one per captured variant / z-chunk mode)."""
+    rec = NCU_TRAFFIC.get(case)
+    return [] if rec is None else (rec if isinstance(rec, list) else [rec])
+
+
 def _traffic(case, variant_name, zmode=0):
     import hashlib
-    rec = NCU_TRAFFIC.get(case)
-    if not rec or rec["variant"] != variant_name or rec.get("zmode", 0) != zmode:
-        return None
-    for f, h in rec["src"].items():
-        path = os.path.join(ROOT, "paper_2406_08923_gb300", "csrc", f)
-        if hashlib.sha256(open(path, "rb").read()).hexdigest()[:16] != h:
-            return None
-    return rec["bytes"]
+    for rec in _traffic_records(case):
+        if rec["variant"] != variant_name or rec.get("zmode", 0) != zmode:
+            continue
+        for f, h in rec["src"].items():
+            path = os.path.join(ROOT, "paper_2406_08923_gb300", "csrc", f)
+            if hashlib.sha256(open(path, "rb").read()).hexdigest()[:16] != h:
+                return None
+        return rec["bytes"]
+    return None
 
 
 # FP64 vector FMA rate of GB300 (nominal 1.25 TFLOP/s dense, recipe table); FP32 from the
@@ -925,12 +932,14 @@ def run_case(args):
         a, b = p.alloc(), p.alloc()
         p.upload(a, [data])
     p.set_variant(args.variant)
+    if args.zmode:
+        p.set_zmode(args.zmode)
     for _ in range(args.warmup):
         p.step(a, b, steps, stream)
     ms = _timed(lambda: p.step(a, b, steps, stream), args.steps, stream)
     p.sync()
     print(json.dumps({"case": args.case, "n": n, "radius": args.radius, "steps_per_job": steps,
-                      "variant": p.variant()[2], "ms_per_job": round(ms, 4)}), flush=True)
+                      "variant": p.variant()[2], "zmode": args.zmode, "ms_per_job": round(ms, 4)}), flush=True)
     return 0
 
 
@@ -945,6 +954,7 @@ def main():
     ap.add_argument("--case", default=None, choices=sorted(CASES),
                     help="run one workload only (no autotune), e.g. for an ncu capture")
     ap.add_argument("--n", type=int, default=None, help="grid size for --case")
+    ap.add_argument("--zmode", type=int, default=0, help="z-chunk mode for --case (3D streaming kernels)")
     ap.add_argument("--variant", type=int, default=0, help="kernel variant for --case")
     ap.add_argument("--job-steps", type=int, default=None, help="steps per job for --case")
     ap.add_argument("--radius", type=int, default=None, help="stencil radius for the 1D / 2D --case workloads")

@@ -44,10 +44,16 @@ def test_reference_arm_json_line():
 
 def test_traffic_record_is_tied_to_variant_and_sources():
     b = _bench_module()
-    for case, rec in b.NCU_TRAFFIC.items():
-        assert b._traffic(case, rec["variant"]) == rec["bytes"], case  # sources unchanged since capture
-        assert b._traffic(case, rec["variant"] + "_other") is None
-        assert b._traffic(case, rec["variant"], rec["zmode"] + 1) is None  # another z-chunk length
+    for case in b.NCU_TRAFFIC:
+        recs = b._traffic_records(case)
+        keys = {(r["variant"], r["zmode"]) for r in recs}
+        assert len(keys) == len(recs), case  # one record per variant and z-chunk mode
+        for rec in recs:
+            # sources unchanged since the capture
+            assert b._traffic(case, rec["variant"], rec["zmode"]) == rec["bytes"], (case, rec["variant"])
+            assert b._traffic(case, rec["variant"] + "_other", rec["zmode"]) is None
+            if (rec["variant"], rec["zmode"] + 1) not in keys:
+                assert b._traffic(case, rec["variant"], rec["zmode"] + 1) is None  # another z-chunk length
     assert b._traffic("no_such_case", "x") is None
 
 
