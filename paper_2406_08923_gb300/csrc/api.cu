@@ -278,7 +278,7 @@ int tuned_batch_shape(int kind) {
     auto it = g_tune_last.find(pref);
     if (it == g_tune_last.end()) return -1;
     // the batched shapes: heat 0 = 4 warps x 2 rows, 1 = 8 warps x 2 rows; MHD 0 = 32 x 4 with
-    // two CTAs per SM, 1 = 32 x 12 with one
+    // two CTAs per SM, 1 = 32 x 8 with one
     const std::string &v = it->second;
     if (kind == STENCIL_DIFFUSION) return v.find("by8") != std::string::npos ? 1 : 0;
     return v.find("_b1") != std::string::npos ? 1 : 0;

@@ -90,7 +90,7 @@ def _serve_one(kind, n, steps, templates):
 
 
 @pytest.mark.parametrize("kind,variants,names", [
-    (L.STENCIL_MHD8, ("tx32_ty4_s8_b2", "tx32_ty12_s8_b1"), ("batch_tx32_ty4_s8", "batch_tx32_ty12_s8")),
+    (L.STENCIL_MHD8, ("tx32_ty4_s8_b2", "tx32_ty12_s8_b1"), ("batch_tx32_ty4_s8", "batch_tx32_ty8_s8")),
     (L.STENCIL_DIFFUSION, ("f32_by4_ry2_zb2_s8_m3", "f32_by8_ry2_zb2_s8_m2"),
      ("batch_by4_ry2_zb2_s8", "batch_by8_ry2_zb2_s8"))])
 def test_server_takes_the_tuned_tile_shape(cuda_lib, tmp_path, monkeypatch, kind, variants, names):
