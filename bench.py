@@ -50,7 +50,7 @@ def _peaks():
 
 # DRAM traffic per launch of the dominant kernel from one ncu capture (profiles/), valid only
 # while the kernel source is unchanged (first 16 hex digits of sha256 of each file).
-SRC_MHD = {"mhd.cu": "63e9a0cd3f94e750", "mhd_rhs.cuh": "be5b445fecd5703b", "common.cuh": "3f7458d1c75ca5f9"}
+SRC_MHD = {"mhd.cu": "e859a4f254b7f575", "mhd_rhs.cuh": "be5b445fecd5703b", "common.cuh": "3f7458d1c75ca5f9"}
 NCU_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum per launch, mean of 3 launches of a 1-pass capture at
     # the bench sizes (profiles/dram_traffic_full_size.md); MHD: the mean over the 3 RK substeps
@@ -61,13 +61,13 @@ NCU_TRAFFIC = {
     "heat_f32_512": {"variant": "f32_by8_ry2_zb2_s8_m2", "zmode": 0, "bytes": 586106795 + 523721984,
                 "src": {"diffusion_f32.cu": "e7b76b56f8dd9baa", "common.cuh": "3f7458d1c75ca5f9"}},
     "mhd_f32": [
-        {"variant": "tx32_ty12_s8_b1", "zmode": 0, "bytes": 5625796608 + 4938428587, "src": SRC_MHD},
-        {"variant": "tx32_ty12_s8_b1", "zmode": 1, "bytes": 5371607552 + 4895969792, "src": SRC_MHD},
+        {"variant": "tx32_ty12_s8_b1", "zmode": 0, "bytes": 5635756032 + 4938529792, "src": SRC_MHD},
+        {"variant": "tx32_ty12_s8_b1", "zmode": 1, "bytes": 5371785643 + 4896083285, "src": SRC_MHD},
     ],
     "mhd_bf16": [
-        {"variant": "tx32_ty8_s8_b2", "zmode": 0, "bytes": 3373316011 + 2582517248, "src": SRC_MHD},
-        {"variant": "tx32_ty4_s8_b3", "zmode": 0, "bytes": 2717969749 + 2478460245, "src": SRC_MHD},
-        {"variant": "tx32_ty4_s8_b3", "zmode": 1, "bytes": 2714474155 + 2446828459, "src": SRC_MHD},
+        {"variant": "tx32_ty8_s8_b2", "zmode": 0, "bytes": 3357410816 + 2579594581, "src": SRC_MHD},
+        {"variant": "tx32_ty4_s8_b3", "zmode": 0, "bytes": 2717305941 + 2478621611, "src": SRC_MHD},
+        {"variant": "tx32_ty4_s8_b3", "zmode": 1, "bytes": 2715124395 + 2447102379, "src": SRC_MHD},
     ],
 }
 
