@@ -4,12 +4,13 @@
   output is the input's augmented array, for every kind.
 * The minimum periodic extent 2r + 1 = 7 on every axis (the halo then wraps almost the whole
   interior): 3D heat for every kernel variant, and the 8-field MHD system (Eqs. A1-A4, RK3).
-* A field beyond 4 GiB (heat 1024^3 FP32, the padded field 4.4 GB), so every 32-bit element or
-  byte offset would overflow.  The input is a product of three 1D sines, an exact eigenfunction
+* Arrays beyond 4 GiB, where a 32-bit byte offset would overflow: a heat field of 1024^3 FP32
+  (4.4 GB padded), and the MHD RK register and Kahan terms at 512^3 FP32 (4.3 GB each).  The input is a product of three 1D sines, an exact eigenfunction
   of the discrete operator of Eq. 7.  It is built on the device as the product of three FP32
   vectors that the host computed.  The host forms the same FP32 products for the boxes around
   sampled cells, and the oracle steps them (box evaluation).  The discrete closed form is a
-  second, independent check.
+  second, independent check.  The MHD fields are products of 1D factors too, advanced by the
+  oracle's box RK3 around sampled cells.
 """
 import numpy as np
 import pytest
@@ -132,3 +133,40 @@ def test_heat_1024_fp32_beyond_4_gib(cuda_lib):
         assert abs(got - ref[1, 1, 1]) <= TOL[L.STENCIL_F32], (cell, got, ref[1, 1, 1])
         exact = amp * float(vz[z]) * float(vy[y]) * float(vx[x])
         assert abs(got - exact) <= 2 * TOL[L.STENCIL_F32], (cell, got, exact)
+
+
+@pytest.mark.slow
+def test_mhd_512_fp32_rk_scratch_beyond_4_gib(cuda_lib):
+    # 512^3 with FP32 storage: the RK register and the Kahan terms (8 values per cell, one array
+    # each) are 4.3 GB, so their offsets 8 cell + q pass 2^32.  Every field is a product of three
+    # 1D factors built on the device; the oracle advances boxes around sampled cells (three RK3
+    # substeps shrink a 21^3 box to its central 3^3).
+    n = 512
+    p, par = mhd_plan((n, n, n), L.STENCIL_F32)
+    h = par.dx[0]
+    i = np.arange(n)
+    # (offset, amplitude) per field: lnrho and s near 1, velocity ~ 0.2^3, vector potential ~ 0.1^3
+    scale = [(1.0, 0.05), (0.2, 0.06), (0.2, 0.06), (0.2, 0.06), (0.1, 0.03), (0.1, 0.03), (0.1, 0.03),
+             (1.0, 0.05)]
+    fac = [[(c + s * np.sin((q + ax + 1) * h * i + 0.1 * (q + 3 * ax))).astype(np.float32) for ax in range(3)]
+           for q, (c, s) in enumerate(scale)]  # fac[q] = [x factor, y factor, z factor]
+    a, b = p.alloc(), p.alloc()
+    ox, oy, oz = p.origin
+    for q in range(8):
+        fx, fy, fz = [torch.from_numpy(v).cuda() for v in fac[q]]
+        p.view3(a[q])[oz:oz + n, oy:oy + n, ox:ox + n] = (fz[:, None, None] * fy[None, :, None]) * fx[None, None, :]
+        del fx, fy, fz
+    p.step(a, b, 1)
+    p.sync()
+    opar = oracle_mhd_params(par)
+    half = 3 * 3 + 1
+    for cell in sample_cells((n, n, n), extra=[(n - 1, 255, 256), (300, n - 2, 1)]):
+        z, y, x = cell
+        iz, iy, ix = [np.arange(c - half, c + half + 1) % n for c in cell]
+        box8 = np.stack([((fz[iz][:, None, None] * fy[iy][None, :, None]) * fx[ix][None, None, :]).astype(np.float64)
+                         for fx, fy, fz in fac])
+        ref = oracle.mhd_rk3_box(box8, opar, par.dt, 3)[:, half, half, half]
+        for q in range(8):
+            got = float(p.view3(b[q])[oz + z, oy + y, ox + x])
+            tol = TOL[L.STENCIL_F32] * np.abs(box8[q]).max()
+            assert abs(got - ref[q]) <= tol, (cell, q, got, ref[q])
