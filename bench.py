@@ -50,24 +50,24 @@ def _peaks():
 
 # DRAM traffic per launch of the dominant kernel from one ncu capture (profiles/), valid only
 # while the kernel source is unchanged (first 16 hex digits of sha256 of each file).
-SRC_MHD = {"mhd.cu": "e859a4f254b7f575", "mhd_rhs.cuh": "be5b445fecd5703b", "common.cuh": "3f7458d1c75ca5f9"}
+SRC_MHD = {"mhd.cu": "6e984cab7c19f38c", "mhd_rhs.cuh": "be5b445fecd5703b", "common.cuh": "3f7458d1c75ca5f9"}
 NCU_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum per launch, mean of 3 launches of a 1-pass capture at
     # the bench sizes (profiles/dram_traffic_full_size.md); MHD: the mean over the 3 RK substeps
-    "heat_f64": {"variant": "vx2_by4_ry1_zb2_s8", "zmode": 0, "bytes": 145201408 + 110754816,
-                "src": {"diffusion.cu": "c4007754501811fa", "common.cuh": "3f7458d1c75ca5f9"}},
+    "heat_f64": {"variant": "vx2_by4_ry1_zb2_s8", "zmode": 0, "bytes": 145087573 + 110741333,
+                "src": {"diffusion.cu": "d40407d5c36ea5d1", "common.cuh": "3f7458d1c75ca5f9"}},
     "heat_f32": {"variant": "f32_by4_ry2_zb2_s8_m3", "zmode": 0, "bytes": 82116779 + 25702827,
                 "src": {"diffusion_f32.cu": "e7b76b56f8dd9baa", "common.cuh": "3f7458d1c75ca5f9"}},
     "heat_f32_512": {"variant": "f32_by8_ry2_zb2_s8_m2", "zmode": 0, "bytes": 586106795 + 523721984,
                 "src": {"diffusion_f32.cu": "e7b76b56f8dd9baa", "common.cuh": "3f7458d1c75ca5f9"}},
     "mhd_f32": [
-        {"variant": "tx32_ty12_s8_b1", "zmode": 0, "bytes": 5635756032 + 4938529792, "src": SRC_MHD},
-        {"variant": "tx32_ty12_s8_b1", "zmode": 1, "bytes": 5371785643 + 4896083285, "src": SRC_MHD},
+        {"variant": "tx32_ty12_s8_b1", "zmode": 0, "bytes": 5640849579 + 4939133781, "src": SRC_MHD},
+        {"variant": "tx32_ty12_s8_b1", "zmode": 1, "bytes": 5373433771 + 4896226048, "src": SRC_MHD},
     ],
     "mhd_bf16": [
-        {"variant": "tx32_ty8_s8_b2", "zmode": 0, "bytes": 3357410816 + 2579594581, "src": SRC_MHD},
-        {"variant": "tx32_ty4_s8_b3", "zmode": 0, "bytes": 2717305941 + 2478621611, "src": SRC_MHD},
-        {"variant": "tx32_ty4_s8_b3", "zmode": 1, "bytes": 2715124395 + 2447102379, "src": SRC_MHD},
+        {"variant": "tx32_ty8_s8_b2", "zmode": 0, "bytes": 3364593493 + 2579704661, "src": SRC_MHD},
+        {"variant": "tx32_ty4_s8_b3", "zmode": 0, "bytes": 2717112917 + 2478695851, "src": SRC_MHD},
+        {"variant": "tx32_ty4_s8_b3", "zmode": 1, "bytes": 2715888555 + 2447137536, "src": SRC_MHD},
     ],
 }
 

@@ -164,13 +164,16 @@ __device__ __forceinline__ bool diffusion_tile(const CUtensorMap *map, T *__rest
     // element offset of (row 0 of this thread, first cell) inside a slot
     const int own = (wy * RY + R) * Cfg::TXP + Cfg::HX + lane * VX;
 
-    // weights as pairs, in registers
-    const P G0 = O::make(wsm[0], wsm[0]);
+    // weights as pairs, in registers up to R = 3; at R = 4 the 8-warp tile would pass 128
+    // registers and lose its second CTA per SM (measured 0.94 against 0.82 ms per step), so
+    // there they stay kernel parameters
+    auto wt = [&](int i) -> T { return R <= 3 ? wsm[i] : (i == 0 ? c.g0 : c.ga[(i - 1) / R][(i - 1) % R]); };
+    const P G0 = O::make(wt(0), wt(0));
     P GA[3][R];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int b = 0; b < R; ++b) GA[a][b] = O::make(wsm[1 + a * R + b], wsm[1 + a * R + b]);
+        for (int b = 0; b < R; ++b) GA[a][b] = O::make(wt(1 + a * R + b), wt(1 + a * R + b));
 
     // z queue: Q[k] holds plane z-R+k of the iteration's first output plane z (k < ZB + 2R)
     P Q[ZB + 2 * R][RY][VP];

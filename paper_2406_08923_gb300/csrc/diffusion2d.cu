@@ -71,12 +71,25 @@ heat2d_kernel(const __grid_constant__ CUtensorMap map_in, T *__restrict__ out, G
     const int nx = (int)g.n[0], ny = (int)g.n[1];
     const int x = x0 + VX * lane, yb = y0 + RY * wy;
 
+    // FP64: the weights go through shared memory into registers, so that the FP64 multiply-adds
+    // take register operands rather than (slower) constant-bank ones
+    __shared__ T wsm[9];
+    if (sizeof(T) == 8 && threadIdx.x < 9)
+        wsm[threadIdx.x] = threadIdx.x == 0 ? w.g0 : (threadIdx.x < 5 ? w.gx[threadIdx.x - 1] : w.gy[threadIdx.x - 5]);
     if (threadIdx.x == 0) {
         tma_prefetch_desc(&map_in);
         mbar_init(&full, 1);
         mbar_fence_init();
     }
     __syncthreads();
+    if (sizeof(T) == 8) {
+        w.g0 = wsm[0];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            w.gx[a] = wsm[1 + a];
+            w.gy[a] = wsm[5 + a];
+        }
+    }
     pdl_launch_dependents();
     pdl_wait();  // the input is the previous step's output
     if (threadIdx.x == 0) {

@@ -230,8 +230,22 @@ mhd_kernel(const __grid_constant__ MhdMaps maps, Ptrs8 fout, S *wbuf, S *kbuf, P
     S *ring = reinterpret_cast<S *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     __shared__ __align__(8) uint64_t full[NSLOT];
     (void)Cfg::SMEM;
-    mhd_tile<S, C, KAHAN, MODE, TX, TY, NSLOT, CONDUCT>(maps.m, fout, wbuf, kbuf, rbuf, g, k, blockIdx.x, blockIdx.y,
-                                                        blockIdx.z, zc, first, last, images, err, ring, full);
+    if constexpr (sizeof(C) == 8) {
+        // FP64: the constants are read from shared memory, so that the FP64 multiply-adds take
+        // register operands rather than constant-bank ones (2 % faster at 256^3; the 255-register
+        // budget has no room to keep all of them in registers)
+        __shared__ MK<C> ks;
+        constexpr int KW = (int)(sizeof(MK<C>) / sizeof(C));
+        for (int i = threadIdx.x; i < KW; i += blockDim.x) reinterpret_cast<C *>(&ks)[i] = reinterpret_cast<const C *>(&k)[i];
+        __syncthreads();
+        mhd_tile<S, C, KAHAN, MODE, TX, TY, NSLOT, CONDUCT>(maps.m, fout, wbuf, kbuf, rbuf, g, ks, blockIdx.x,
+                                                            blockIdx.y, blockIdx.z, zc, first, last, images, err,
+                                                            ring, full);
+    } else {
+        mhd_tile<S, C, KAHAN, MODE, TX, TY, NSLOT, CONDUCT>(maps.m, fout, wbuf, kbuf, rbuf, g, k, blockIdx.x,
+                                                            blockIdx.y, blockIdx.z, zc, first, last, images, err,
+                                                            ring, full);
+    }
 }
 
 // ------------------------------------------------------------------ host side
