@@ -21,6 +21,10 @@
 namespace stn {
 
 constexpr int XC_THREADS = 256;
+// FP64 CTAs: 512 threads, two per SM (below).
+constexpr int XC_T64 = 512;
+template <typename T> constexpr int xc_threads() { return sizeof(T) == 8 ? XC_T64 : XC_THREADS; }
+template <typename T> constexpr int xc_minb() { return sizeof(T) == 8 ? 2 : 1; }
 // Consecutive outputs per thread and sweep (register blocking).  Odd, so that lanes XC_V cells
 // apart read and write distinct shared-memory banks.
 constexpr int XC_V = 9;
@@ -29,11 +33,14 @@ constexpr int XC_MAX_SWEEPS = 16;
 // in the 256 x 9 outputs one pass of the threads computes.
 constexpr int XC_CHUNK = XC_THREADS * XC_V - 2 * (XC_MAX_SWEEPS - 1) * 4;  // 2184
 // FP64 sweeps one output per thread and iteration (below), so its chunk is a runtime length
-// (even, 256..2048).  A grid too small for several waves of 2048-cell chunks gets chunks that
-// put exactly 4 CTAs on every SM (the 2^20-cell benchmark: 1726 cells, 150 us per 10 sweeps).
-// Measured there: 2048 cells (3.4 CTAs per SM, unbalanced) 176 us; 1024 158 us; 864 (8 per
-// SM) 168 us; 1380 (5 per SM) 154 us.
-template <typename T> constexpr int xc_chunk() { return sizeof(T) == 8 ? 2048 : XC_CHUNK; }
+// (even, 256..4096), chosen so that the grid fills whole waves of two CTAs per SM: the
+// 2^20-cell benchmark takes 3450-cell chunks, one wave.  The FP64 pipe retires one warp
+// instruction per 16 SM cycles, so what a sweep costs is the warp instructions of the busiest
+// SM sub-partition, and whole warps count even where lanes idle.  Per sweep a CTA evaluates
+// its chunk plus the halo of the sweeps still to come, in rows of 32 cells; with 3450-cell
+// chunks and the rows spread evenly over the sub-partitions (below), 98.7 % of the issued
+// lanes are outputs, against 96.2 % with four 1726-cell CTAs of 256 threads per SM.
+template <typename T> constexpr int xc_chunk() { return sizeof(T) == 8 ? 4096 : XC_CHUNK; }
 constexpr int XC_PAD = 4;  // buffer elements before logical cell 0
 // elements per shared-memory buffer: a sweep starting at cell s r <= 96 (the halo of the
 // sweeps one launch runs, at most 3 x 30 cells) reads up to 256 x 9 + 40 cells past its start
@@ -70,6 +77,7 @@ __device__ __forceinline__ void xcorr_chunk(const T *__restrict__ in, T *__restr
                                             const XCoef<T> &cf, int sweeps, int periodic, int images, int chunk,
                                             unsigned char *smem_raw, int chunk_len = 0) {
     using A = typename XAcc<T>::type;
+    constexpr int NT = xc_threads<T>();
     const int CHUNK = sizeof(A) == 8 ? chunk_len : xc_chunk<T>();
     const int H = sweeps * R;
     const int W = CHUNK + 2 * H;
@@ -86,14 +94,14 @@ __device__ __forceinline__ void xcorr_chunk(const T *__restrict__ in, T *__restr
     const bool full = c0 + CHUNK <= n;
     if (full) {
         const VT *src = reinterpret_cast<const VT *>(inx + c0);
-        for (int v = threadIdx.x; v < CHUNK / V; v += XC_THREADS) {
+        for (int v = threadIdx.x; v < CHUNK / V; v += NT) {
             VT x = src[v];
             const T *e = reinterpret_cast<const T *>(&x);
 #pragma unroll
             for (int u = 0; u < V; ++u) buf0[XC_PAD + H + v * V + u] = (A)e[u];
         }
     }
-    for (int e = threadIdx.x; e < W; e += XC_THREADS) {
+    for (int e = threadIdx.x; e < W; e += NT) {
         const bool body = e >= H && e < H + CHUNK;
         if (full && body) continue;
         int64_t gi = c0 - H + e;
@@ -123,12 +131,20 @@ __device__ __forceinline__ void xcorr_chunk(const T *__restrict__ in, T *__restr
     // times per sweep instead of 2r + 1 times.  Outputs past the valid span [s r, W - s r) are
     // computed from stale cells and never read by a valid output.
     // FP64 is bound by the FP64 pipe rather than by shared memory, and keeps one output per
-    // thread and iteration (measured 9 % faster there).
+    // thread and iteration (measured 9 % faster there).  Its sweep takes the span in rows of 32
+    // cells, row k to warp (k + rot) mod (warps), with rot advancing by one per sweep and per
+    // CTA: a span of rows that is not a multiple of the warp count leaves its extra rows to
+    // other warps, and so to other SM sub-partitions, from sweep to sweep.  Each output is the
+    // same multiply-add chain whichever warp computes it.
     A *src = buf0, *dst = buf1;
     for (int s = 1; s <= sweeps; ++s) {
         if constexpr (sizeof(A) == 8) {
             const int lo = s * R, hi = W - s * R;
-            for (int p = lo + threadIdx.x; p < hi; p += XC_THREADS) {
+            constexpr int NW = NT / 32;
+            const int rot = (s + (int)blockIdx.x) % NW;
+            int k0 = (int)(threadIdx.x >> 5) - rot;
+            if (k0 < 0) k0 += NW;
+            for (int p = lo + 32 * k0 + (int)(threadIdx.x & 31); p < hi; p += NT) {
                 A acc = A(0);
 #pragma unroll
                 for (int j = -R; j <= R; ++j) acc = mac<A>(acc, wr[j + R], src[XC_PAD + p + j]);
@@ -163,7 +179,7 @@ __device__ __forceinline__ void xcorr_chunk(const T *__restrict__ in, T *__restr
     const A *res = src + XC_PAD + H;
     if (full) {
         VT *d = reinterpret_cast<VT *>(outx + c0);
-        for (int v = threadIdx.x; v < CHUNK / V; v += XC_THREADS) {
+        for (int v = threadIdx.x; v < CHUNK / V; v += NT) {
             VT x;
             T *e = reinterpret_cast<T *>(&x);
 #pragma unroll
@@ -171,11 +187,11 @@ __device__ __forceinline__ void xcorr_chunk(const T *__restrict__ in, T *__restr
             d[v] = x;
         }
     } else {
-        for (int p = threadIdx.x; p < CHUNK && c0 + p < n; p += XC_THREADS)
+        for (int p = threadIdx.x; p < CHUNK && c0 + p < n; p += NT)
             outx[c0 + p] = (T)res[p];
     }
     if (images) {
-        for (int p = threadIdx.x; p < CHUNK; p += XC_THREADS) {
+        for (int p = threadIdx.x; p < CHUNK; p += NT) {
             const int64_t gi = c0 + p;
             if (gi >= n) break;
             if (gi < R) outx[gi + n] = (T)res[p];
@@ -184,11 +200,16 @@ __device__ __forceinline__ void xcorr_chunk(const T *__restrict__ in, T *__restr
     }
 }
 
+// Launched with programmatic dependent launch: the next launch in the stream (the next sweeps
+// of a call, or the next call) is dispatched while this grid runs, and waits in pdl_wait for
+// this grid's completion before its first global-memory access.
 template <typename T, int R>
-__global__ void __launch_bounds__(XC_THREADS)
+__global__ void __launch_bounds__(xc_threads<T>(), xc_minb<T>())
 xcorr_kernel(const T *__restrict__ in, T *__restrict__ out, Geom geo, XCoef<T> cf, int sweeps, int periodic,
              int images, int chunk_len) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_launch_dependents();
+    pdl_wait();
     xcorr_chunk<T, R>(in, out, geo, cf, sweeps, periodic, images, blockIdx.x, smem_raw, chunk_len);
 }
 
@@ -200,8 +221,10 @@ static cudaError_t run(const void *in, void *out, const Geom &g, const void *coe
     for (int j = 0; j < 2 * R + 1; ++j) cf.g[j] = static_cast<const T *>(coeffs)[j];
     int chunk_len = xc_chunk<T>();
     if (sizeof(T) == 8) {
-        const int64_t wave = 4 * (int64_t)device_sms();  // exactly 4 CTAs on every SM
-        const int64_t per = (g.n[0] + wave - 1) / wave;
+        // whole waves of two CTAs on every SM, each chunk at most xc_chunk<double>()
+        const int64_t wave = 2 * (int64_t)device_sms();
+        const int64_t waves = std::max<int64_t>(1, (g.n[0] + wave * chunk_len - 1) / (wave * chunk_len));
+        const int64_t per = (g.n[0] + wave * waves - 1) / (wave * waves);
         chunk_len = (int)std::min<int64_t>(chunk_len, std::max<int64_t>(256, (per + 1) & ~int64_t(1)));
     }
     const size_t smem = sizeof(A) == 8 ? 2 * sizeof(A) * xc_f64_stride(chunk_len, sweeps * R)
@@ -212,9 +235,8 @@ static cudaError_t run(const void *in, void *out, const Geom &g, const void *coe
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k<<<blocks, XC_THREADS, smem, s>>>(static_cast<const T *>(in), static_cast<T *>(out), g, cf,
-                                       sweeps, periodic ? 1 : 0, images ? 1 : 0, chunk_len);
-    return cudaGetLastError();
+    return launch_pdl(k, dim3(blocks), dim3(xc_threads<T>()), smem, s, static_cast<const T *>(in),
+                      static_cast<T *>(out), g, cf, sweeps, periodic ? 1 : 0, images ? 1 : 0, chunk_len);
 }
 
 template <typename T>

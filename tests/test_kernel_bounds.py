@@ -73,11 +73,15 @@ def test_window_kernel_stays_in_its_buffers():
             assert PAD + H + CHUNK - 1 < BUF
 
 
+T64, F64_CAP = _const("XC_T64"), 4096
+
+
 def f64_chunk(n, sms):
-    # run<double>: exactly 4 CTAs per SM on small grids, 2048 otherwise, even, >= 256
-    wave = 4 * sms
-    per = (n + wave - 1) // wave
-    return min(2048, max(256, (per + 1) & ~1))
+    # run<double>: whole waves of 2 CTAs per SM, chunks at most 4096 cells, even, >= 256
+    wave = 2 * sms
+    waves = max(1, (n + wave * F64_CAP - 1) // (wave * F64_CAP))
+    per = (n + wave * waves - 1) // (wave * waves)
+    return min(F64_CAP, max(256, (per + 1) & ~1))
 
 
 def f64_stride(chunk, halo):
@@ -87,16 +91,21 @@ def f64_stride(chunk, halo):
 
 def test_f64_chunks_and_buffers():
     assert "chunk_len = (int)std::min<int64_t>(chunk_len, std::max<int64_t>(256, (per + 1) & ~int64_t(1)));" in SRC
+    assert "const int64_t waves = std::max<int64_t>(1, (g.n[0] + wave * chunk_len - 1) / (wave * chunk_len));" in SRC
+    assert "return sizeof(T) == 8 ? 4096 : XC_CHUNK;" in SRC
     assert "return (XC_PAD + chunk + 2 * halo + 1) & ~1;" in SRC
-    sizes = [1, 7, 255, 256, 4099, 5003, 65536, 2 ** 20, 2 ** 20 + 1, 2 ** 21 + 5, 2 ** 24, 2 ** 26 + 3]
+    assert T64 == 512
+    sizes = [1, 7, 255, 256, 4099, 5003, 65536, 2 ** 20, 2 ** 20 + 1, 2 ** 21 + 5, 2 ** 22, 2 ** 24, 2 ** 26 + 3]
     for sms in (132, 148, 152, 160):
         for n in sizes:
             c = f64_chunk(n, sms)
-            assert c % 2 == 0 and 256 <= c <= 2048, (n, sms, c)
+            assert c % 2 == 0 and 256 <= c <= F64_CAP, (n, sms, c)
             blocks = (n + c - 1) // c
             assert blocks * c >= n and (blocks - 1) * c < n
-            if n <= 4 * sms * 2048 and n >= 4 * sms * 256:
-                assert blocks <= 4 * sms
+            if 2 * sms * 256 <= n:
+                # whole waves: never more than one CTA per SM short of the last wave's end
+                waves = -(-blocks // (2 * sms))
+                assert blocks > (waves - 1) * 2 * sms
             for r in range(0, 5):
                 for sweeps in range(1, max_sweeps(r) + 1):
                     H = sweeps * r
@@ -106,9 +115,30 @@ def test_f64_chunks_and_buffers():
                     for s in range(1, sweeps + 1):
                         # p in [s r, W - s r), reads p + j for |j| <= r
                         assert PAD + (s - 1) * r >= 0 and PAD + W - (s - 1) * r <= S
-                    assert 2 * 8 * S <= SMEM_MAX
-    # the 2^20-cell benchmark on 152 SMs: 1726-cell chunks, 608 CTAs
-    assert f64_chunk(2 ** 20, 152) == 1726 and (2 ** 20 + 1725) // 1726 == 608
+                    assert 2 * 2 * 8 * S <= SMEM_MAX  # two CTAs per SM
+    # the 2^20-cell benchmark on 152 SMs: 3450-cell chunks, 304 CTAs, one wave
+    assert f64_chunk(2 ** 20, 152) == 3450 and (2 ** 20 + 3449) // 3450 == 304
+
+
+def test_f64_rotated_rows_cover_the_span_once():
+    # warp w starts at row k0 = (w - rot) mod NW and strides by NT cells: every cell of
+    # [lo, hi) is computed by exactly one thread, for every rotation
+    assert "int k0 = (int)(threadIdx.x >> 5) - rot;" in SRC
+    assert "for (int p = lo + 32 * k0 + (int)(threadIdx.x & 31); p < hi; p += NT) {" in SRC
+    assert "const int rot = (s + (int)blockIdx.x) % NW;" in SRC
+    NW = T64 // 32
+    for span in (1, 31, 32, 33, 511, 512, 513, 1726, 3450, 3510, 4096 + 128):
+        for rot in range(NW):
+            seen = [0] * span
+            for t in range(T64):
+                k0 = (t >> 5) - rot
+                if k0 < 0:
+                    k0 += NW
+                p = 32 * k0 + (t & 31)
+                while p < span:
+                    seen[p] += 1
+                    p += T64
+            assert all(x == 1 for x in seen), (span, rot)
 
 
 # ---------------------------------------------------------------------------------------------
