@@ -21,10 +21,10 @@
 namespace stn {
 
 constexpr int XC_THREADS = 256;
-// FP64 CTAs: 512 threads, two per SM (below).
+// FP64 CTAs: 512 threads, two per SM, when one wave of them covers the input; else 256
+// threads, four per SM (below).  Either way 1024 threads per SM at 64 registers.
 constexpr int XC_T64 = 512;
-template <typename T> constexpr int xc_threads() { return sizeof(T) == 8 ? XC_T64 : XC_THREADS; }
-template <typename T> constexpr int xc_minb() { return sizeof(T) == 8 ? 2 : 1; }
+template <typename T, int NT> constexpr int xc_minb() { return sizeof(T) == 8 ? 1024 / NT : 1; }
 // Consecutive outputs per thread and sweep (register blocking).  Odd, so that lanes XC_V cells
 // apart read and write distinct shared-memory banks.
 constexpr int XC_V = 9;
@@ -33,14 +33,34 @@ constexpr int XC_MAX_SWEEPS = 16;
 // in the 256 x 9 outputs one pass of the threads computes.
 constexpr int XC_CHUNK = XC_THREADS * XC_V - 2 * (XC_MAX_SWEEPS - 1) * 4;  // 2184
 // FP64 sweeps one output per thread and iteration (below), so its chunk is a runtime length
-// (even, 256..4096), chosen so that the grid fills whole waves of two CTAs per SM: the
-// 2^20-cell benchmark takes 3450-cell chunks, one wave.  The FP64 pipe retires one warp
-// instruction per 16 SM cycles, so what a sweep costs is the warp instructions of the busiest
-// SM sub-partition, and whole warps count even where lanes idle.  Per sweep a CTA evaluates
-// its chunk plus the halo of the sweeps still to come, in rows of 32 cells; with 3450-cell
-// chunks and the rows spread evenly over the sub-partitions (below), 98.7 % of the issued
-// lanes are outputs, against 96.2 % with four 1726-cell CTAs of 256 threads per SM.
+// (even, 256..4096), chosen so that the grid fills whole waves.  The FP64 pipe retires one
+// warp instruction per 16 SM cycles, so what a sweep costs is the warp instructions of the
+// busiest SM sub-partition, and whole warps count even where lanes idle.  Per sweep a CTA
+// evaluates its chunk plus the halo of the sweeps still to come, in rows of 32 cells.
+//   * Inputs whose input and output arrays fill at most 7/8 of L2 together run as whole
+//     waves of two 512-thread CTAs per SM (chunks up to 4096 cells): the 2^20-cell benchmark
+//     is one wave of 3450-cell chunks.  With the rows spread evenly over the sub-partitions
+//     (below), 98.7 % of the issued lanes are outputs, against 96.2 % with four 1726-cell
+//     CTAs of 256 threads per SM.  Measured with 16 sweeps per launch, r = 3: 2^22 cells
+//     794 us in 4 waves (835 us in 3.4 waves of 2048-cell chunks), 3 x 2^21 cells 1189 us in
+//     6 waves (1248 us).
+//   * Larger inputs run 2048-cell chunks in CTAs of 256 threads, four per SM, scheduled as
+//     SMs free up; there each CTA's staging reads DRAM, and four CTAs per SM keep more of them
+//     sweeping meanwhile.  2^23 cells: 1602 us (1648 us in 7 whole waves of 512-thread CTAs);
+//     2^24 cells: 3192 us (3278 us in whole waves of 512-thread CTAs, 3314 us in 14 whole
+//     waves of 1972-cell chunks of 256 threads).  Rotating the rows changed nothing there, nor
+//     did PDL, nor 128-byte aligned chunks.
 template <typename T> constexpr int xc_chunk() { return sizeof(T) == 8 ? 4096 : XC_CHUNK; }
+constexpr int XC_F64_MULTI_CHUNK = 2048;
+
+// L2 capacity in bytes of the current device (cached per device).
+static int64_t device_l2_bytes() {
+    static int l2[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (!l2[dev] && cudaDeviceGetAttribute(&l2[dev], cudaDevAttrL2CacheSize, dev) != cudaSuccess) l2[dev] = -1;
+    return l2[dev] > 0 ? l2[dev] : 0;
+}
 constexpr int XC_PAD = 4;  // buffer elements before logical cell 0
 // elements per shared-memory buffer: a sweep starting at cell s r <= 96 (the halo of the
 // sweeps one launch runs, at most 3 x 30 cells) reads up to 256 x 9 + 40 cells past its start
@@ -72,12 +92,12 @@ template <typename T> struct XCoef { T g[2 * XC_MAX_R + 1]; };
 
 // One chunk of outputs (xc_chunk<T>(); FP64: chunk_len) : stage, sweep in shared memory, write
 // (+ images).
-template <typename T, int R>
+template <typename T, int R, int NT = XC_THREADS>
 __device__ __forceinline__ void xcorr_chunk(const T *__restrict__ in, T *__restrict__ out, const Geom &geo,
                                             const XCoef<T> &cf, int sweeps, int periodic, int images, int chunk,
                                             unsigned char *smem_raw, int chunk_len = 0) {
     using A = typename XAcc<T>::type;
-    constexpr int NT = xc_threads<T>();
+    static_assert(sizeof(A) == 8 || NT == XC_THREADS, "the register-window sweep assumes XC_THREADS threads");
     const int CHUNK = sizeof(A) == 8 ? chunk_len : xc_chunk<T>();
     const int H = sweeps * R;
     const int W = CHUNK + 2 * H;
@@ -203,14 +223,14 @@ __device__ __forceinline__ void xcorr_chunk(const T *__restrict__ in, T *__restr
 // Launched with programmatic dependent launch: the next launch in the stream (the next sweeps
 // of a call, or the next call) is dispatched while this grid runs, and waits in pdl_wait for
 // this grid's completion before its first global-memory access.
-template <typename T, int R>
-__global__ void __launch_bounds__(xc_threads<T>(), xc_minb<T>())
+template <typename T, int R, int NT>
+__global__ void __launch_bounds__(NT, xc_minb<T, NT>())
 xcorr_kernel(const T *__restrict__ in, T *__restrict__ out, Geom geo, XCoef<T> cf, int sweeps, int periodic,
              int images, int chunk_len) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     pdl_launch_dependents();
     pdl_wait();
-    xcorr_chunk<T, R>(in, out, geo, cf, sweeps, periodic, images, blockIdx.x, smem_raw, chunk_len);
+    xcorr_chunk<T, R, NT>(in, out, geo, cf, sweeps, periodic, images, blockIdx.x, smem_raw, chunk_len);
 }
 
 template <typename T, int R>
@@ -220,22 +240,35 @@ static cudaError_t run(const void *in, void *out, const Geom &g, const void *coe
     XCoef<T> cf{};
     for (int j = 0; j < 2 * R + 1; ++j) cf.g[j] = static_cast<const T *>(coeffs)[j];
     int chunk_len = xc_chunk<T>();
+    bool wide = false;  // FP64: whole waves of 512-thread CTAs
     if (sizeof(T) == 8) {
-        // whole waves of two CTAs on every SM, each chunk at most xc_chunk<double>()
+        // whole waves of two 512-thread CTAs per SM (chunks of at most 4096 cells) while the
+        // input and output fill at most 7/8 of L2 together, else 2048-cell chunks in
+        // 256-thread CTAs (at 2^23 cells the two arrays are 134 MB, just under GB300's L2
+        // capacity, and the 256-thread CTAs were 2.7 % faster)
         const int64_t wave = 2 * (int64_t)device_sms();
-        const int64_t waves = std::max<int64_t>(1, (g.n[0] + wave * chunk_len - 1) / (wave * chunk_len));
-        const int64_t per = (g.n[0] + wave * waves - 1) / (wave * waves);
-        chunk_len = (int)std::min<int64_t>(chunk_len, std::max<int64_t>(256, (per + 1) & ~int64_t(1)));
+        const int64_t l2 = device_l2_bytes();
+        wide = 2 * (int64_t)sizeof(T) * g.n[0] <= l2 - l2 / 8;
+        if (wide) {
+            const int64_t waves = std::max<int64_t>(1, (g.n[0] + wave * chunk_len - 1) / (wave * chunk_len));
+            const int64_t per = (g.n[0] + wave * waves - 1) / (wave * waves);
+            chunk_len = (int)std::min<int64_t>(chunk_len, std::max<int64_t>(256, (per + 1) & ~int64_t(1)));
+        } else {
+            chunk_len = XC_F64_MULTI_CHUNK;
+        }
     }
     const size_t smem = sizeof(A) == 8 ? 2 * sizeof(A) * xc_f64_stride(chunk_len, sweeps * R)
                                        : 2 * sizeof(A) * XC_BUF;
     const unsigned blocks = (unsigned)((g.n[0] + chunk_len - 1) / chunk_len);
-    auto k = xcorr_kernel<T, R>;
+    auto k = xcorr_kernel<T, R, XC_THREADS>;
+    if constexpr (sizeof(T) == 8) {
+        if (wide) k = xcorr_kernel<T, R, XC_T64>;
+    }
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    return launch_pdl(k, dim3(blocks), dim3(xc_threads<T>()), smem, s, static_cast<const T *>(in),
+    return launch_pdl(k, dim3(blocks), dim3(wide ? XC_T64 : XC_THREADS), smem, s, static_cast<const T *>(in),
                       static_cast<T *>(out), g, cf, sweeps, periodic ? 1 : 0, images ? 1 : 0, chunk_len);
 }
 

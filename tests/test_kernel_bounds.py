@@ -73,15 +73,23 @@ def test_window_kernel_stays_in_its_buffers():
             assert PAD + H + CHUNK - 1 < BUF
 
 
-T64, F64_CAP = _const("XC_T64"), 4096
+T64, F64_CAP, F64_MULTI = _const("XC_T64"), 4096, _const("XC_F64_MULTI_CHUNK")
+
+
+def f64_launch(n, sms, l2=129 << 20):
+    # run<double>: (chunk, threads).  Whole waves of 2 x 512-thread CTAs per SM (chunks up to
+    # 4096, even, >= 256) while input and output fill at most 7/8 of L2, else 2048-cell
+    # chunks in 256-thread CTAs
+    wave = 2 * sms
+    if 16 * n > l2 - l2 // 8:
+        return F64_MULTI, T
+    waves = max(1, (n + wave * F64_CAP - 1) // (wave * F64_CAP))
+    per = (n + wave * waves - 1) // (wave * waves)
+    return min(F64_CAP, max(256, (per + 1) & ~1)), T64
 
 
 def f64_chunk(n, sms):
-    # run<double>: whole waves of 2 CTAs per SM, chunks at most 4096 cells, even, >= 256
-    wave = 2 * sms
-    waves = max(1, (n + wave * F64_CAP - 1) // (wave * F64_CAP))
-    per = (n + wave * waves - 1) // (wave * waves)
-    return min(F64_CAP, max(256, (per + 1) & ~1))
+    return f64_launch(n, sms)[0]
 
 
 def f64_stride(chunk, halo):
@@ -92,20 +100,27 @@ def f64_stride(chunk, halo):
 def test_f64_chunks_and_buffers():
     assert "chunk_len = (int)std::min<int64_t>(chunk_len, std::max<int64_t>(256, (per + 1) & ~int64_t(1)));" in SRC
     assert "const int64_t waves = std::max<int64_t>(1, (g.n[0] + wave * chunk_len - 1) / (wave * chunk_len));" in SRC
+    assert "wide = 2 * (int64_t)sizeof(T) * g.n[0] <= l2 - l2 / 8;" in SRC
+    assert "const int64_t wave = 2 * (int64_t)device_sms();" in SRC
+    assert "chunk_len = XC_F64_MULTI_CHUNK;" in SRC
     assert "return sizeof(T) == 8 ? 4096 : XC_CHUNK;" in SRC
+    assert F64_MULTI == 2048
     assert "return (XC_PAD + chunk + 2 * halo + 1) & ~1;" in SRC
     assert T64 == 512
-    sizes = [1, 7, 255, 256, 4099, 5003, 65536, 2 ** 20, 2 ** 20 + 1, 2 ** 21 + 5, 2 ** 22, 2 ** 24, 2 ** 26 + 3]
-    for sms in (132, 148, 152, 160):
+    sizes = [1, 7, 255, 256, 4099, 5003, 65536, 2 ** 20, 2 ** 20 + 1, 2 ** 21 + 5, 2 ** 22, 3 << 21, 2 ** 23,
+             2 ** 24, 2 ** 26 + 3]
+    for sms, l2 in ((132, 50 << 20), (148, 126 << 20), (152, 129 << 20), (152, 135 << 20), (160, 256 << 20),
+                    (152, 0)):
         for n in sizes:
-            c = f64_chunk(n, sms)
+            c, nt = f64_launch(n, sms, l2)
             assert c % 2 == 0 and 256 <= c <= F64_CAP, (n, sms, c)
+            per_sm = 1024 // nt
             blocks = (n + c - 1) // c
             assert blocks * c >= n and (blocks - 1) * c < n
-            if 2 * sms * 256 <= n:
-                # whole waves: never more than one CTA per SM short of the last wave's end
-                waves = -(-blocks // (2 * sms))
-                assert blocks > (waves - 1) * 2 * sms
+            if nt == T64 and per_sm * sms * 256 <= n:
+                # whole waves: the last wave is not more than one CTA per SM short
+                waves = -(-blocks // (per_sm * sms))
+                assert blocks > waves * per_sm * sms - sms, (n, sms, blocks, waves)
             for r in range(0, 5):
                 for sweeps in range(1, max_sweeps(r) + 1):
                     H = sweeps * r
@@ -115,9 +130,15 @@ def test_f64_chunks_and_buffers():
                     for s in range(1, sweeps + 1):
                         # p in [s r, W - s r), reads p + j for |j| <= r
                         assert PAD + (s - 1) * r >= 0 and PAD + W - (s - 1) * r <= S
-                    assert 2 * 2 * 8 * S <= SMEM_MAX  # two CTAs per SM
-    # the 2^20-cell benchmark on 152 SMs: 3450-cell chunks, 304 CTAs, one wave
-    assert f64_chunk(2 ** 20, 152) == 3450 and (2 ** 20 + 3449) // 3450 == 304
+                    assert per_sm * 2 * 8 * S <= SMEM_MAX  # CTAs per SM x two buffers
+    # the 2^20-cell benchmark on 152 SMs: 3450-cell chunks, 304 CTAs of 512 threads, one wave;
+    # 2^22 cells: 4 waves of 3450-cell chunks; 2^23 and 2^24 cells (more than L2 holds):
+    # 2048-cell chunks of 256 threads
+    assert f64_launch(2 ** 20, 152) == (3450, 512) and (2 ** 20 + 3449) // 3450 == 304
+    assert f64_launch(2 ** 22, 152) == (3450, 512) and -(-2 ** 22 // 3450) == 1216
+    assert f64_launch(3 << 21, 152) == (3450, 512)
+    assert f64_launch(2 ** 23, 152) == (2048, 256) and f64_launch(2 ** 24, 152) == (2048, 256)
+    assert f64_launch(2 ** 23, 152, 135 << 20) == (2048, 256)
 
 
 def test_f64_rotated_rows_cover_the_span_once():
