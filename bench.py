@@ -891,6 +891,8 @@ CASES = {
     "xcorr1d_f64": ("xcorr_r", 1, 1 << 24, 1),
     "maxfilter_f32": ("maxfilter", 2, 1 << 24, 1),
     "heat2d_f32": ("heat2d", 2, 4096, 4),
+    # the norms of the 8-field state (with the mass), through the allocation-free entry point
+    "norms_f64": ("norms", 1, MHD_N, 1),
 }
 
 
@@ -904,11 +906,20 @@ def run_case(args):
     n = args.n or n0
     steps = args.job_steps or steps
     stream = torch.cuda.current_stream()
+    job = None
     if kind == "heat":
         par = L.heat_params(n)
         p = L.Plan(3, (n, n, n), 3, 1, L.STENCIL_BC_PERIODIC, L.STENCIL_DIFFUSION, storage, storage, params=par)
         a, b = p.alloc(), p.alloc()
         p.upload(a, [synth.heat_field(n)])
+    elif kind == "norms":
+        par = L.mhd_params(n)
+        p = L.Plan(3, (n, n, n), 3, 8, L.STENCIL_BC_PERIODIC, L.STENCIL_MHD8, storage, storage, params=par)
+        a = p.alloc()
+        p.upload(a, synth.mhd_fields(n))
+        nout = torch.empty(3 * 8 + 1, dtype=torch.float64, device="cuda")
+        vol = par.dx[0] * par.dx[1] * par.dx[2]
+        job = lambda: L.stencil_field_norms_noalloc(a, p.storage, p.dims, p.padded, p.origin, vol, nout, stream)
     elif kind == "mhd":
         par = L.mhd_params(n)
         compute = L.STENCIL_F64 if storage == L.STENCIL_F64 else L.STENCIL_F32
@@ -937,12 +948,14 @@ def run_case(args):
         p = L.Plan(1, (n,), 3, 1, L.STENCIL_BC_PERIODIC, L.STENCIL_XCORR, storage, storage, coeffs=g)
         a, b = p.alloc(), p.alloc()
         p.upload(a, [data])
-    p.set_variant(args.variant)
-    if args.zmode:
-        p.set_zmode(args.zmode)
+    if job is None:
+        p.set_variant(args.variant)
+        if args.zmode:
+            p.set_zmode(args.zmode)
+        job = lambda: p.step(a, b, steps, stream)
     for _ in range(args.warmup):
-        p.step(a, b, steps, stream)
-    ms = _timed(lambda: p.step(a, b, steps, stream), args.steps, stream)
+        job()
+    ms = _timed(job, args.steps, stream)
     p.sync()
     print(json.dumps({"case": args.case, "n": n, "radius": args.radius, "steps_per_job": steps,
                       "variant": p.variant()[2], "zmode": args.zmode, "ms_per_job": round(ms, 4)}), flush=True)

@@ -3,9 +3,16 @@
 // (Sec. 5.1 verification; Eq. A1 for the mass).
 //
 // Two passes with a fixed reduction tree, so results are bit-reproducible run to run:
-// pass 1: NB blocks stride over (row, segment) pieces of the interior (coalesced along x)
-// and write NB x nfields x 4 partials; pass 2: one warp per (field, quantity) reduces the
-// partials in a fixed order.
+// pass 1: the NB blocks' warps stride over (row, segment) pieces of the interior, one warp per
+// piece (coalesced along x, NORM_U loads in flight per lane), and each block writes
+// nfields x 4 partials; pass 2: one warp per (field, quantity) reduces the NB partials in a
+// fixed order.
+//
+// Each value costs two FP64 instructions (the add to sum f and the fused multiply-add to
+// sum f^2) and, for the mass, an FP64 exp; FP64 runs at 2 instructions per cycle per SM on
+// GB300, so the pass is bound by the FP64 pipe, not by HBM.  A piece is a whole row of up to
+// NORM_SEG cells (a 256-cell row of a 256^3 grid fills one piece), so the index arithmetic of
+// a row is paid once per 256 or more values.
 #include <mutex>
 
 #include "internal.h"
@@ -13,9 +20,10 @@
 namespace stn {
 
 constexpr int NORM_THREADS = 256;
+constexpr int NORM_WARPS = NORM_THREADS / 32;
 constexpr int NORM_BLOCKS = 2 * 152;
-constexpr int NORM_SEG = 4096;
-constexpr int NORM_U = 8;  // loads in flight per thread in pass 1
+constexpr int NORM_U = 8;                     // loads in flight per lane (no mass)
+constexpr int NORM_SEG = 32 * NORM_U * 8;     // cells per piece: 2048
 
 int norms_blocks() { return NORM_BLOCKS; }
 
@@ -38,50 +46,100 @@ __device__ __forceinline__ void warp_reduce(double &s, double &s2, double &mx, d
     }
 }
 
+// Accumulates one field's pieces for this warp: sum f, sum f^2, max |f| as a bit pattern and,
+// with MASS, sum exp(f).  MASS is a template parameter so that the other fields carry no mass
+// accumulation at all: with a runtime flag the compiler kept the add to the mass sum, with a
+// zero operand, on every value (2.1 FP64 adds per value instead of 1, counted by ncu).
+// The pieces of warp gw: gw, gw + nw, ..., each a segment sg of row (y, z).  The division of
+// the first index is done once; each stride of nw pieces then advances (sg, y, z) by constant
+// steps with carries, so the loop runs no 64-bit division (which this GPU emulates, partly
+// with FP64 instructions that compete with the accumulation).
+struct PieceWalk {
+    int64_t segs, n1, pieces;
+    int64_t sg, y, z;     // current piece
+    int64_t dsg, dy, dz;  // the stride nw in (segment, y, z) units
+    __device__ PieceWalk(const Geom &g, int64_t gw, int64_t nw) {
+        segs = (g.n[0] + NORM_SEG - 1) / NORM_SEG;
+        n1 = g.n[1];
+        pieces = segs * g.n[1] * g.n[2];
+        const int64_t row = gw / segs, drow = nw / segs;
+        sg = gw - row * segs;
+        y = row % n1;
+        z = row / n1;
+        dsg = nw - drow * segs;
+        dy = drow % n1;
+        dz = drow / n1;
+    }
+    __device__ __forceinline__ void next() {
+        sg += dsg;
+        int64_t carry = 0;
+        if (sg >= segs) { sg -= segs; carry = 1; }
+        y += dy + carry;  // dy < n1 and carry <= 1: at most one wrap
+        z += dz;
+        if (y >= n1) { y -= n1; z += 1; }
+    }
+};
+
+template <typename S, bool MASS>
+__device__ __forceinline__ void norms_field(const S *__restrict__ base, const Geom &g, int64_t gw, int64_t nw,
+                                            double &s, double &s2, unsigned &mhi, unsigned &mlo, double &ms) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nx = g.n[0];
+    PieceWalk pw(g, gw, nw);
+    // max |f| as the bit pattern of |f|: for non-negative doubles the unsigned order of the
+    // patterns is the numeric order, and every NaN pattern lies above +inf (so a NaN wins).  The
+    // pattern is kept as two 32-bit words (mhi, mlo) updated with 32-bit integer operations:
+    // a 64-bit compare-and-select here cost one more FP64-pipe instruction per value (ncu), as
+    // many as the sum itself.
+    auto add = [&](double v) {
+        s = __dadd_rn(s, v);
+        s2 = __fma_rn(v, v, s2);
+        const unsigned hi = (unsigned)__double2hiint(v) & 0x7fffffffu, lo = (unsigned)__double2loint(v);
+        const unsigned cand = hi == mhi ? max(mlo, lo) : lo;  // mlo if hi is, or becomes, the max
+        mlo = hi >= mhi ? cand : mlo;
+        mhi = max(mhi, hi);
+        if constexpr (MASS) ms = __dadd_rn(ms, exp(v));
+    };
+    // warp gw takes pieces gw, gw + nw, ...; within a piece, lane l the cells l, l + 32, ...
+    for (int64_t piece = gw; piece < pw.pieces; piece += nw, pw.next()) {
+        const S *p = base + g.idx(0, pw.y, pw.z);
+        const int64_t xe = min(nx, (pw.sg + 1) * NORM_SEG);
+        int64_t x = pw.sg * NORM_SEG + lane;
+        // U independent loads in flight per lane, then the same accumulation order (x, x + 32,
+        // ...) as one element at a time.  The mass path keeps fewer: its exp calls are what
+        // bound it, and values live across them spill.
+        constexpr int U = MASS ? 2 : NORM_U;
+        for (; x + 32 * (U - 1) < xe; x += 32 * U) {
+            S v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) v[u] = p[x + 32 * u];
+#pragma unroll
+            for (int u = 0; u < U; ++u) add(to_d(v[u]));
+        }
+        for (; x < xe; x += 32) add(to_d(p[x]));
+    }
+}
+
 template <typename S>
 __global__ void __launch_bounds__(NORM_THREADS)
 norms_pass1(Ptrs8 f, int nfields, Geom g, int mass0, double *partials) {
-    __shared__ double red[4][NORM_THREADS / 32];
-    const int64_t nx = g.n[0], rows = g.n[1] * g.n[2];
-    const int64_t segs = (nx + NORM_SEG - 1) / NORM_SEG;
+    __shared__ double red[4][NORM_WARPS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t gw = (int64_t)blockIdx.x * NORM_WARPS + warp, nw = (int64_t)gridDim.x * NORM_WARPS;
     for (int q = 0; q < nfields; ++q) {
         const S *base = static_cast<const S *>(f.p[q]);
-        const bool do_mass = mass0 && q == 0;
         double s = 0.0, s2 = 0.0, ms = 0.0;
-        // max |f| as the bit pattern of |f|: for non-negative doubles the unsigned order of the
-        // patterns is the numeric order, every NaN pattern lies above +inf (so a NaN wins), and
-        // no FP64 compare (a slow-pipe instruction on this GPU) is needed
-        unsigned long long mxb = 0ull;
-        auto add = [&](double v) {
-            s += v;
-            s2 += v * v;
-            mxb = max(mxb, (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull);
-            if (do_mass) ms += exp(v);
-        };
-        for (int64_t piece = blockIdx.x; piece < rows * segs; piece += gridDim.x) {
-            const int64_t row = piece / segs, sg = piece - row * segs;
-            const int64_t y = row % g.n[1], z = row / g.n[1];
-            const S *p = base + g.idx(0, y, z);
-            const int64_t xe = min(nx, (sg + 1) * NORM_SEG);
-            int64_t x = sg * NORM_SEG + threadIdx.x;
-            // NORM_U independent loads in flight per thread, then the same accumulation order
-            // (x, x + NORM_THREADS, ...) as one element at a time
-            for (; x + (NORM_U - 1) * NORM_THREADS < xe; x += NORM_U * NORM_THREADS) {
-                S v[NORM_U];
-#pragma unroll
-                for (int u = 0; u < NORM_U; ++u) v[u] = p[x + u * NORM_THREADS];
-#pragma unroll
-                for (int u = 0; u < NORM_U; ++u) add(to_d(v[u]));
-            }
-            for (; x < xe; x += NORM_THREADS) add(to_d(p[x]));
-        }
-        double mx = __longlong_as_double((long long)mxb);
+        unsigned mhi = 0u, mlo = 0u;
+        if (mass0 && q == 0)
+            norms_field<S, true>(base, g, gw, nw, s, s2, mhi, mlo, ms);
+        else
+            norms_field<S, false>(base, g, gw, nw, s, s2, mhi, mlo, ms);
+        double mx = __hiloint2double((int)mhi, (int)mlo);
         warp_reduce(s, s2, mx, ms);
         if (lane == 0) { red[0][warp] = s; red[1][warp] = s2; red[2][warp] = mx; red[3][warp] = ms; }
         __syncthreads();
         if (warp == 0) {
-            const bool in = lane < NORM_THREADS / 32;
+            const bool in = lane < NORM_WARPS;
             s = in ? red[0][lane] : 0.0;
             s2 = in ? red[1][lane] : 0.0;
             mx = in ? red[2][lane] : 0.0;

@@ -323,3 +323,44 @@ def test_mhd_variants_fit_shared_memory_and_registers():
             threads = tx * ty
             assert threads <= 1024 and threads % 32 == 0
             assert 65536 // (threads * minb) >= 64, (macro, tx, ty)  # registers per thread
+
+
+# ---------------------------------------------------------------------------------------------
+# Norms pass 1 (csrc/norms.cu): each warp walks its pieces with carried (segment, y, z) steps
+# instead of dividing every piece index; the walk must visit exactly the pieces a division gives.
+
+NORM_SRC = open(os.path.join(ROOT, "paper_2406_08923_gb300", "csrc", "norms.cu")).read()
+
+
+def test_norms_piece_walk_matches_division():
+    for text in ("const int64_t row = gw / segs, drow = nw / segs;", "sg = gw - row * segs;",
+                 "dsg = nw - drow * segs;", "if (sg >= segs) { sg -= segs; carry = 1; }",
+                 "y += dy + carry;  // dy < n1 and carry <= 1: at most one wrap",
+                 "if (y >= n1) { y -= n1; z += 1; }",
+                 "for (int64_t piece = gw; piece < pw.pieces; piece += nw, pw.next()) {"):
+        assert text in NORM_SRC, text
+    seg = 32 * 8 * 8
+    assert "constexpr int NORM_SEG = 32 * NORM_U * 8;" in NORM_SRC
+    for nx, ny, nz in ((256, 256, 4), (1, 1, 1), (2 ** 20, 1, 1), (5000, 3, 7), (2049, 17, 2), (13, 11, 9)):
+        segs = -(-nx // seg)
+        pieces = segs * ny * nz
+        for nw in (1, 7, 2432, 4864):
+            for gw in sorted({0, 1, nw // 2, nw - 1}):
+                if gw >= nw:
+                    continue
+                row, drow = gw // segs, nw // segs
+                sg, y, z = gw - row * segs, row % ny, row // ny
+                dsg, dy, dz = nw - drow * segs, drow % ny, drow // ny
+                piece = gw
+                while piece < pieces:
+                    r = piece // segs
+                    assert (sg, y, z) == (piece - r * segs, r % ny, r // ny), (nx, ny, nz, nw, gw, piece)
+                    piece += nw
+                    sg += dsg
+                    carry = 0
+                    if sg >= segs:
+                        sg, carry = sg - segs, 1
+                    y += dy + carry
+                    z += dz
+                    if y >= ny:
+                        y, z = y - ny, z + 1
