@@ -96,8 +96,8 @@ def test_minimum_extent_wraps_several_times(cuda_lib):
 
 @pytest.mark.parametrize("dtype", [L.STENCIL_I32, L.STENCIL_F32, L.STENCIL_F64])
 def test_large_grid_full_blocks(cuda_lib, dtype):
-    # 2^21 + 5 cells: enough chunks for FP64's 2048-cell chunks (smaller grids run 1024-cell
-    # chunks), many chunks and a ragged tail.  16 + 3 sweeps: two launches.
+    # 2^21 + 5 cells: many chunks and a ragged tail (FP64: two whole waves of 512-thread CTAs
+    # with 3450-cell chunks).  16 + 3 sweeps: two launches.
     n = (1 << 21) + 5
     if dtype == L.STENCIL_I32:
         data, g = synth.xcorr_int32(n)
@@ -113,6 +113,20 @@ def test_large_grid_full_blocks(cuda_lib, dtype):
         assert np.array_equal(out, ref)
     else:
         assert_close(out, ref, 1e-12 if dtype == L.STENCIL_F64 else 1e-5, "2^21 + 5")
+    ox = p.origin[0]
+    np.testing.assert_array_equal(whole[ox - 3:ox], whole[ox + n - 3:ox + n])
+    np.testing.assert_array_equal(whole[ox + n:ox + n + 3], whole[ox:ox + 3])
+    p.close()
+
+
+def test_f64_past_l2_runs_the_256_thread_chunks(cuda_lib):
+    # 2^23 + 3 FP64 cells: input and output (134 MB) exceed 7/8 of L2, so the launches take
+    # 2048-cell chunks in 256-thread CTAs instead of whole waves of 512-thread CTAs.  Ragged
+    # tail, 16 + 3 sweeps in two launches, and the periodic images of both ends.
+    n = (1 << 23) + 3
+    data = synth.uniform(2406089233, 9, n, -1.0, 1.0)
+    out, whole, p, _ = _run(data, D2, 19, L.STENCIL_F64)
+    assert_close(out, oracle.xcorr1d(data, D2, 19), 1e-12, "2^23 + 3")
     ox = p.origin[0]
     np.testing.assert_array_equal(whole[ox - 3:ox], whole[ox + n - 3:ox + n])
     np.testing.assert_array_equal(whole[ox + n:ox + n + 3], whole[ox:ox + 3])
