@@ -79,3 +79,18 @@ def test_a_nan_cell_makes_the_max_nan(cuda_lib, storage):
             assert np.isnan(s) and np.isnan(s2) and np.isnan(mx), got[9:12]
         else:
             assert np.isfinite([s, s2, mx]).all(), (q, got[3 * q:3 * q + 3])
+
+
+@pytest.mark.parametrize("shape", [(40, 70, 33), (7, 7, (1 << 17) + 5)])
+def test_norms_when_warps_take_several_pieces(cuda_lib, shape):
+    # More pieces than the pass's warps (304 x 8), so each warp walks on from its first piece:
+    # (40, 70, 33) has 2800 one-segment rows; (7, 7, 2^17 + 5) has 49 rows of 65 segments each
+    # (3185 pieces), whose walk carries from segment to row and from row to plane.
+    nz, ny, nx = shape
+    f = synth.uniform(2406089241, 3, nz * ny * nx, -1.0, 1.0).reshape(shape)
+    p = L.Plan(3, (nx, ny, nz), 3, 1, L.STENCIL_BC_PERIODIC, L.STENCIL_DIFFUSION, L.STENCIL_F64, L.STENCIL_F64,
+               params=L.heat_params(shape))
+    a = p.alloc(fill=1e6)
+    p.upload(a, [f])
+    np.testing.assert_allclose(p.norms(a), _ref(f), rtol=1e-12, atol=1e-12)
+    p.close()
