@@ -778,7 +778,7 @@ def run_zslab(args):
 def run_extras(L, synth, stream, hbm_peak, args):
     out = {}
     w, r = 1, 3
-    # config 1: 1D cross-correlation, 2^20 cells, 10 sweeps (L2-resident: no HBM claim)
+    # 1D cross-correlation, 2^20 cells, 10 sweeps (L2-resident: no HBM claim)
     for name, dt in (("xcorr1d_int32_2^20_10sweeps", L.STENCIL_I32), ("xcorr1d_fp64_2^20_10sweeps", L.STENCIL_F64)):
         res = xcorr_job(L, synth, dt, w, 20, stream)
         out[name] = {"ms_per_job": round(res["ms_job"], 4), "ms_per_job_eager": round(res["ms_job_eager"], 4),
@@ -791,7 +791,7 @@ def run_extras(L, synth, stream, hbm_peak, args):
             out[name]["bound"] = "FP64 pipe (4 MiB working set, L2-resident)"
             out[name]["roofline"] = _roof("alu", tf, FP64_PEAK_TFLOPS, "TFLOP/s",
                                           note="14 flop per cell-sweep; FP64 nominal 1.25 TFLOP/s")
-    # config 2, FP32 variant
+    # 3D heat, 256^3, 100 steps, FP32
     res = heat_job(L, synth, L.STENCIL_F32, HEAT_N, HEAT_STEPS, w, r, stream)
     cells = HEAT_N ** 3
     gbs = cells * 8.0 / (res["ms_kernel"] / 1e3) / 1e9
@@ -804,7 +804,7 @@ def run_extras(L, synth, stream, hbm_peak, args):
                           traffic=_traffic("heat_f32", res["variant"], res["plan"].autotune_status()[1]),
                           note="8 B/cell-update algorithmic; traffic = ncu dram bytes/launch")}
     res["plan"].close()
-    # config 2 FP32 at 512^3: the two 540 MB fields far exceed the 126 MB L2
+    # 3D heat FP32 at 512^3: the two 540 MB fields far exceed the 126 MB L2
     n5 = 2 * HEAT_N
     res = heat_job(L, synth, L.STENCIL_F32, n5, HEAT_STEPS // 4, w, r, stream)
     cells5 = n5 ** 3
@@ -818,7 +818,7 @@ def run_extras(L, synth, stream, hbm_peak, args):
                           traffic=_traffic("heat_f32_512", res["variant"], res["plan"].autotune_status()[1]),
                           note="8 B/cell-update algorithmic; traffic = ncu dram bytes/launch")}
     res["plan"].close()
-    # config 3: fused 8-field MHD, 256^3 FP64, 20 RK3 steps
+    # fused 8-field MHD, 256^3 FP64, 20 RK3 steps
     cells = MHD_N ** 3
     res = mhd_job(L, synth, L.STENCIL_F64, MHD_N, MHD_STEPS, w, 1, stream)
     # algorithmic flops per cell-substep (Eqs. A1-A4 + RK3) against the FP64 FMA peak; the
@@ -855,7 +855,7 @@ def run_extras(L, synth, stream, hbm_peak, args):
                           note="one read of 8 fields x 256^3 interior cells x 8 B per call (sum, sum f^2, "
                                "max |f|, mass sum exp(lnrho)); 2 launches")}
     res["plan"].close()
-    # config 4: 384^3 FP32 / BF16 storage, Kahan-compensated RK
+    # fused 8-field MHD, 384^3 FP32 / BF16 storage, Kahan-compensated RK
     cells = MHD_N_LOWP ** 3
     for name, st, bpc in (("mhd8_384_fp32_20steps", L.STENCIL_F32, 4), ("mhd8_384_bf16_20steps", L.STENCIL_BF16, 2)):
         res = mhd_job(L, synth, st, MHD_N_LOWP, MHD_STEPS, w, 1, stream)
@@ -873,7 +873,7 @@ def run_extras(L, synth, stream, hbm_peak, args):
                                             "RK substeps); traffic = ncu dram bytes per launch, mean of the 3 "
                                             "substeps")}
         res["plan"].close()
-    # config 4 accuracy: FP32 / BF16 storage against the FP64 path, every step of 20
+    # MHD 384^3 accuracy: FP32 / BF16 storage against the FP64 path, every step of 20
     out["mhd8_384_accuracy_20steps"] = run_accuracy_leg(L, synth, stream)
     return out
 
