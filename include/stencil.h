@@ -53,7 +53,7 @@ typedef enum stencil_status {
     STENCIL_EINVAL = 1,       /* an argument is out of range, inconsistent or misaligned */
     STENCIL_ENOMEM = 2,       /* a device or host allocation failed */
     STENCIL_ECUDA = 3,        /* a CUDA call failed (detail string names it) */
-    STENCIL_EUNSUPPORTED = 4, /* a valid combination this build does not implement */
+    STENCIL_EUNSUPPORTED = 4, /* a valid combination the library does not implement */
     STENCIL_ETIMEOUT = 5      /* a bounded device-side wait expired; the kernel gave up */
 } stencil_status;
 
